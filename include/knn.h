@@ -1,0 +1,177 @@
+/*
+ * knn.h -- C ABI of the GB300 (sm_103a) brute-force k-nearest-neighbour library.
+ *
+ * The operation is the one of Sec. 2.1 ("Problem definition") of Garcia,
+ * Debreuve and Barlaud, "Fast k Nearest Neighbor Search using GPU": given m
+ * reference points R = {r_1..r_m} and n query points Q = {q_1..q_n} in R^d,
+ * return for every query the k reference points nearest to it under a given
+ * distance.  The brute-force method of the same section (compute all m
+ * distances, sort, keep the k smallest, for every query) fixes the result;
+ * this library reaches the same result without writing the n x m distance
+ * matrix to memory: each distance tile is consumed on chip by a per-query
+ * top-k selection.
+ *
+ * Conventions (the paper fixes none of them):
+ *   - points are rows: R is m x d and Q is n x d, row-major, contiguous,
+ *     IEEE float32;
+ *   - indices are 0-based (the paper writes r_1..r_m);
+ *   - every output row i holds k pairs (dist, idx) ascending by distance,
+ *     equal distances ordered by the smaller index;
+ *   - Euclidean results are true distances ||q - r||_2 (not squared);
+ *     Manhattan results are sum_t |q_t - r_t|;
+ *   - non-finite coordinates are a precondition violation: results are
+ *     unspecified (they are not checked on the hot path).
+ *
+ * Every entry point returns a knn_status.  On any error status nothing has
+ * been written to the caller's output buffers.  A handle is not thread-safe:
+ * use one handle per host thread or serialise calls externally.
+ */
+#ifndef KNN_GB300_H
+#define KNN_GB300_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct knn_ctx* knn_handle; /* opaque; owned by the library */
+
+/* Distances named in Sec. 2.1 ("the Euclidean or the Manhattan distance"). */
+typedef enum { KNN_L2 = 0, KNN_L1 = 1 } knn_metric;
+
+/*
+ * Arithmetic of the distance stage.
+ *   KNN_FP32: float32 on CUDA cores, distances formed from coordinate
+ *             differences (sum (q-r)^2 or sum |q-r|).
+ *   KNN_BF16 / KNN_TF32: Euclidean only.  The cross term q.r runs on the
+ *             tensor cores (tcgen05) in bf16 or tf32 with float32
+ *             accumulation, the norms are added in the epilogue
+ *             (||q||^2 + ||r||^2 - 2 q.r), the best rerank_factor * k
+ *             candidates per query are re-ranked with exact float32
+ *             differences.  Manhattan distance ignores this setting and
+ *             runs in KNN_FP32.
+ * In every mode, candidates whose float32 distances lie within the float32
+ * rounding bound of each other around the returned list are re-checked in
+ * float64 on the GPU, so ties are resolved by the exact distance.
+ */
+typedef enum { KNN_FP32 = 0, KNN_TF32 = 1, KNN_BF16 = 2 } knn_precision;
+
+typedef enum {
+    KNN_OK = 0,
+    KNN_ERR_INVALID = 1,     /* bad argument: null pointer, k<1, k>m, d mismatch, ... */
+    KNN_ERR_OOM = 2,         /* device memory could not be obtained (or is over the limit) */
+    KNN_ERR_CUDA = 3,        /* a CUDA call failed; see knn_last_error() */
+    KNN_ERR_TIMEOUT = 4,     /* a bounded device-side wait gave up */
+    KNN_ERR_NOREF = 5,       /* knn_search before knn_set_reference */
+    KNN_ERR_BUSY = 6,        /* the handle is in use */
+    KNN_ERR_UNSUPPORTED = 7  /* valid request outside this build's limits (see KNN_K_MAX) */
+} knn_status;
+
+/* Largest k accepted by knn_search. */
+#define KNN_K_MAX 1024
+
+typedef struct {
+    int32_t precision;       /* knn_precision; default KNN_FP32 */
+    int32_t rerank_factor;   /* low-precision forms keep rerank_factor*k candidates; default 4 */
+    int64_t workspace_limit; /* max bytes of device scratch the handle may hold; 0 = no limit */
+} knn_options;
+
+/* Fill *opt with the defaults above. */
+void knn_options_default(knn_options* opt);
+
+/*
+ * Create a handle bound to CUDA device `device`.  opt may be NULL
+ * (defaults).  The handle owns a CUDA stream, the device copy of the
+ * reference set and a scratch workspace.
+ * Errors: KNN_ERR_INVALID (out == NULL, bad option), KNN_ERR_CUDA (no such
+ * device / no driver).
+ */
+knn_status knn_create(knn_handle* out, int device, const knn_options* opt);
+
+/*
+ * Set the reference set R (m x d, row-major float32) -- the set R of
+ * Sec. 2.1.  The library COPIES R into device memory it owns (the caller
+ * keeps ownership of its buffer and may free it on return) and precomputes
+ * what later searches need (squared norms, the bf16/tf32 copy when the
+ * handle's precision asks for one).  r_on_device = 1: R is a device
+ * pointer on the handle's device; 0: a host pointer.  The call is
+ * synchronous.  Replaces any previous reference set.
+ * Errors: KNN_ERR_INVALID (R NULL, m < 1, d < 1), KNN_ERR_OOM, KNN_ERR_CUDA.
+ */
+knn_status knn_set_reference(knn_handle h, const float* R, int64_t m, int32_t d,
+                             int r_on_device);
+
+/*
+ * k nearest neighbours of each of the n queries Q (n x d, row-major
+ * float32) among the current reference set, under `metric` -- the search
+ * of Sec. 2.1.  Writes dist_out[i*k + s] (float32) and idx_out[i*k + s]
+ * (int32, 0-based), s = 0..k-1 ascending.
+ *   io_on_device = 1: Q, dist_out and idx_out are device pointers valid on
+ *     `cuda_stream`; the call only enqueues work and returns (asynchronous).
+ *   io_on_device = 0: host pointers; the call copies Q in, searches, copies
+ *     the results out and returns when they are in place (synchronous).
+ *     Pinned host memory makes the copies faster; pageable works too.
+ * cuda_stream: a cudaStream_t, or NULL for the handle's own stream.
+ * n = 0 is a no-op returning KNN_OK.
+ * Errors: KNN_ERR_INVALID (null pointer with n > 0, n < 0, k < 1, k > m,
+ * d != the reference dimension, bad metric), KNN_ERR_UNSUPPORTED
+ * (k > KNN_K_MAX), KNN_ERR_NOREF, KNN_ERR_OOM, KNN_ERR_CUDA.
+ */
+knn_status knn_search(knn_handle h, const float* Q, int64_t n, int32_t d, int32_t k,
+                      knn_metric metric, float* dist_out, int32_t* idx_out,
+                      int io_on_device, void* cuda_stream);
+
+/*
+ * Wait for all work the library enqueued on this handle's device and report
+ * a bounded device-side wait that gave up during it (KNN_ERR_TIMEOUT, after
+ * which the flag is cleared).  The asynchronous form of knn_search reports
+ * such a failure only here or in a later synchronous call.
+ */
+knn_status knn_sync(knn_handle h);
+
+/*
+ * Change the handle's precision (knn_precision).  Builds the bf16/tf32
+ * copy of the current reference set if one is needed.  Synchronous.
+ * Errors: KNN_ERR_INVALID, KNN_ERR_OOM, KNN_ERR_CUDA.
+ */
+knn_status knn_set_precision(knn_handle h, int32_t precision);
+
+/* Counters since knn_create (reading them synchronises the handle's work). */
+typedef struct {
+    int64_t searches;          /* knn_search calls that did work */
+    int64_t kernel_launches;   /* this library's kernels launched */
+    int64_t recheck_entries;   /* candidates re-checked in float64 */
+    int64_t fallback_queries;  /* queries finished by the exact float64 pass */
+    int64_t workspace_bytes;   /* device scratch currently held */
+} knn_stats;
+
+knn_status knn_get_stats(knn_handle h, knn_stats* out);
+
+/*
+ * Per-stage device times of the next searches.  knn_set_profiling(h, 1)
+ * makes knn_search record CUDA events around each of its stages on the
+ * stream it runs on; knn_get_profile() synchronises and returns, for the
+ * most recent search, the milliseconds of up to `cap` stages in `ms` and
+ * their names in `names` (static strings), and the number of stages in
+ * *count.  Profiling adds event records only; it changes no result.
+ */
+knn_status knn_set_profiling(knn_handle h, int on);
+knn_status knn_get_profile(knn_handle h, float* ms, const char** names, int32_t cap,
+                           int32_t* count);
+
+/* Release the handle and everything it owns.  NULL is accepted. */
+knn_status knn_destroy(knn_handle h);
+
+/* Static description of a status code. */
+const char* knn_status_string(knn_status s);
+
+/* Text of the last CUDA error seen by this handle ("" if none). */
+const char* knn_last_error(knn_handle h);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* KNN_GB300_H */

@@ -1,0 +1,473 @@
+// knn_capi.cu -- the C ABI declared in include/knn.h: handle, reference set,
+// workspace and the orchestration of one search (select -> finalize ->
+// fallback), all enqueued on one CUDA stream.
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <new>
+#include <string>
+
+#include "../../include/knn.h"
+#include "knn_internal.cuh"
+
+using namespace knn;
+
+namespace {
+
+constexpr int kMaxStages = 8;
+
+// Device counters owned by a handle.
+struct Counters {
+    int32_t fallback_count;                 // queued queries of the current search
+    int32_t error_flag;                     // set by a kernel whose bounded wait gave up
+    unsigned long long recheck_total;       // float64 re-checked candidates
+    unsigned long long fallback_total;      // queries finished by the fallback
+};
+
+}  // namespace
+
+struct knn_ctx {
+    int device = 0;
+    int num_sms = 0;
+    cudaStream_t stream = nullptr;
+    knn_options opt{};
+
+    // reference set (owned)
+    float* R = nullptr;
+    int64_t m = 0;
+    int32_t d = 0;
+    float* r_norms = nullptr;     // ||r||^2 in float32
+    void* R_lp = nullptr;         // bf16 / tf32 operand copy
+    int32_t kp = 0;               // padded row length of R_lp
+    int lp_prec = 0;              // 0: none, kTF32, kBF16
+
+    // workspace (grown on demand)
+    unsigned char* ws = nullptr;
+    size_t ws_bytes = 0;
+
+    Counters* counters = nullptr;  // device
+    int64_t searches = 0;
+    int64_t launches = 0;
+
+    bool profiling = false;
+    cudaEvent_t ev[kMaxStages + 1] = {};
+    const char* stage_names[kMaxStages] = {};
+    int nstages = 0;
+
+    std::string last_error;
+};
+
+namespace {
+
+knn_status cuda_fail(knn_ctx* h, cudaError_t err, const char* what) {
+    if (h) {
+        h->last_error = std::string(what) + ": " + cudaGetErrorString(err);
+    }
+    (void)cudaGetLastError();  // clear a sticky launch error if recoverable
+    return (err == cudaErrorMemoryAllocation) ? KNN_ERR_OOM : KNN_ERR_CUDA;
+}
+
+#define KNN_CUDA(h, call)                                          \
+    do {                                                           \
+        cudaError_t err__ = (call);                                \
+        if (err__ != cudaSuccess) return cuda_fail((h), err__, #call); \
+    } while (0)
+
+bool fault_inject_oom() {
+    const char* v = std::getenv("KNN_FAULT_INJECT_OOM");
+    return v && v[0] == '1';
+}
+
+// Make sure the handle's workspace holds at least `bytes`.
+knn_status ensure_workspace(knn_ctx* h, size_t bytes) {
+    if (bytes <= h->ws_bytes) return KNN_OK;
+    if (fault_inject_oom()) {
+        h->last_error = "workspace allocation refused (KNN_FAULT_INJECT_OOM=1)";
+        return KNN_ERR_OOM;
+    }
+    if (h->opt.workspace_limit > 0 && bytes > static_cast<size_t>(h->opt.workspace_limit)) {
+        h->last_error = "workspace over the handle's limit";
+        return KNN_ERR_OOM;
+    }
+    KNN_CUDA(h, cudaStreamSynchronize(h->stream));
+    if (h->ws) KNN_CUDA(h, cudaFree(h->ws));
+    h->ws = nullptr;
+    h->ws_bytes = 0;
+    const size_t grow = bytes + bytes / 4;
+    cudaError_t err = cudaMalloc(&h->ws, grow);
+    if (err != cudaSuccess) {
+        err = cudaMalloc(&h->ws, bytes);
+        if (err != cudaSuccess) return cuda_fail(h, err, "cudaMalloc(workspace)");
+        h->ws_bytes = bytes;
+    } else {
+        h->ws_bytes = grow;
+    }
+    return KNN_OK;
+}
+
+// Bump allocator over the workspace (256-byte aligned slices).
+struct Carve {
+    size_t off = 0;
+    size_t take(size_t bytes) {
+        const size_t at = off;
+        off += (bytes + 255) & ~static_cast<size_t>(255);
+        return at;
+    }
+};
+
+void free_reference(knn_ctx* h) {
+    if (h->R) cudaFree(h->R);
+    if (h->r_norms) cudaFree(h->r_norms);
+    if (h->R_lp) cudaFree(h->R_lp);
+    h->R = nullptr;
+    h->r_norms = nullptr;
+    h->R_lp = nullptr;
+    h->m = 0;
+    h->d = 0;
+    h->kp = 0;
+    h->lp_prec = 0;
+}
+
+knn_status build_lowp(knn_ctx* h, int prec) {
+    if (h->lp_prec == prec && h->R_lp) return KNN_OK;
+    if (h->R_lp) {
+        KNN_CUDA(h, cudaFree(h->R_lp));
+        h->R_lp = nullptr;
+        h->lp_prec = 0;
+    }
+    const int kp = tc_padded_dim(h->d, prec);
+    const size_t elt = (prec == kBF16) ? 2 : 4;
+    KNN_CUDA(h, cudaMalloc(&h->R_lp, static_cast<size_t>(h->m) * kp * elt));
+    int l = 0;
+    KNN_CUDA(h, launch_prepare_lowp(h->R, h->m, h->d, kp, prec, h->R_lp, h->r_norms, h->stream, &l));
+    h->launches += l;
+    KNN_CUDA(h, cudaStreamSynchronize(h->stream));
+    h->kp = kp;
+    h->lp_prec = prec;
+    return KNN_OK;
+}
+
+int ceil_div(int64_t a, int64_t b) { return static_cast<int>((a + b - 1) / b); }
+
+void stage(knn_ctx* h, cudaStream_t st, const char* name) {
+    if (!h->profiling || h->nstages >= kMaxStages) return;
+    h->stage_names[h->nstages] = name;
+    cudaEventRecord(h->ev[h->nstages + 1], st);
+    ++h->nstages;
+}
+
+}  // namespace
+
+extern "C" {
+
+void knn_options_default(knn_options* opt) {
+    if (!opt) return;
+    opt->precision = KNN_FP32;
+    opt->rerank_factor = 4;
+    opt->workspace_limit = 0;
+}
+
+knn_status knn_create(knn_handle* out, int device, const knn_options* opt) {
+    if (!out) return KNN_ERR_INVALID;
+    *out = nullptr;
+    knn_options o;
+    knn_options_default(&o);
+    if (opt) o = *opt;
+    if (o.precision < KNN_FP32 || o.precision > KNN_BF16 || o.rerank_factor < 1 ||
+        o.rerank_factor > 64 || o.workspace_limit < 0)
+        return KNN_ERR_INVALID;
+    int count = 0;
+    if (cudaGetDeviceCount(&count) != cudaSuccess || device < 0 || device >= count) {
+        (void)cudaGetLastError();
+        return KNN_ERR_CUDA;
+    }
+    knn_ctx* h = new (std::nothrow) knn_ctx();
+    if (!h) return KNN_ERR_OOM;
+    h->device = device;
+    h->opt = o;
+    cudaError_t err = cudaSetDevice(device);
+    if (err == cudaSuccess)
+        err = cudaDeviceGetAttribute(&h->num_sms, cudaDevAttrMultiProcessorCount, device);
+    if (err == cudaSuccess) err = cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking);
+    if (err == cudaSuccess) err = cudaMalloc(&h->counters, sizeof(Counters));
+    if (err == cudaSuccess) err = cudaMemset(h->counters, 0, sizeof(Counters));
+    for (int i = 0; err == cudaSuccess && i <= kMaxStages; ++i) err = cudaEventCreate(&h->ev[i]);
+    if (err != cudaSuccess) {
+        knn_destroy(h);
+        (void)cudaGetLastError();
+        return err == cudaErrorMemoryAllocation ? KNN_ERR_OOM : KNN_ERR_CUDA;
+    }
+    *out = h;
+    return KNN_OK;
+}
+
+knn_status knn_destroy(knn_handle h) {
+    if (!h) return KNN_OK;
+    cudaSetDevice(h->device);
+    if (h->stream) cudaStreamSynchronize(h->stream);
+    free_reference(h);
+    if (h->ws) cudaFree(h->ws);
+    if (h->counters) cudaFree(h->counters);
+    for (int i = 0; i <= kMaxStages; ++i)
+        if (h->ev[i]) cudaEventDestroy(h->ev[i]);
+    if (h->stream) cudaStreamDestroy(h->stream);
+    delete h;
+    return KNN_OK;
+}
+
+knn_status knn_set_reference(knn_handle h, const float* R, int64_t m, int32_t d, int r_on_device) {
+    if (!h || !R || m < 1 || d < 1 || m > 0x7fffffffLL) return KNN_ERR_INVALID;
+    KNN_CUDA(h, cudaSetDevice(h->device));
+    KNN_CUDA(h, cudaStreamSynchronize(h->stream));
+    free_reference(h);
+    const size_t bytes = static_cast<size_t>(m) * d * sizeof(float);
+    KNN_CUDA(h, cudaMalloc(&h->R, bytes));
+    // norms padded to whole 128-reference tiles (zero beyond m): the tensor-core
+    // epilogue reads them in aligned groups without a bounds check
+    const size_t mpad = static_cast<size_t>((m + 127) / 128 * 128);
+    KNN_CUDA(h, cudaMalloc(&h->r_norms, mpad * sizeof(float)));
+    KNN_CUDA(h, cudaMemsetAsync(h->r_norms, 0, mpad * sizeof(float), h->stream));
+    KNN_CUDA(h, cudaMemcpyAsync(h->R, R, bytes,
+                                r_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
+                                h->stream));
+    KNN_CUDA(h, cudaStreamSynchronize(h->stream));
+    h->m = m;
+    h->d = d;
+    if (h->opt.precision != KNN_FP32) {
+        knn_status s = build_lowp(h, h->opt.precision == KNN_BF16 ? kBF16 : kTF32);
+        if (s != KNN_OK) {
+            free_reference(h);
+            return s;
+        }
+    }
+    return KNN_OK;
+}
+
+knn_status knn_set_precision(knn_handle h, int32_t precision) {
+    if (!h || precision < KNN_FP32 || precision > KNN_BF16) return KNN_ERR_INVALID;
+    KNN_CUDA(h, cudaSetDevice(h->device));
+    h->opt.precision = precision;
+    if (precision != KNN_FP32 && h->R) return build_lowp(h, precision == KNN_BF16 ? kBF16 : kTF32);
+    return KNN_OK;
+}
+
+knn_status knn_search(knn_handle h, const float* Q, int64_t n, int32_t d, int32_t k,
+                      knn_metric metric, float* dist_out, int32_t* idx_out, int io_on_device,
+                      void* cuda_stream) {
+    if (!h) return KNN_ERR_INVALID;
+    if (n < 0 || k < 1 || (metric != KNN_L2 && metric != KNN_L1)) return KNN_ERR_INVALID;
+    if (n > 0 && (!Q || !dist_out || !idx_out)) return KNN_ERR_INVALID;
+    if (!h->R) return KNN_ERR_NOREF;
+    if (d != h->d || k > h->m) return KNN_ERR_INVALID;
+    if (k > KNN_K_MAX) return KNN_ERR_UNSUPPORTED;
+    if (n == 0) return KNN_OK;
+    if (n > 0x7fffffffLL) return KNN_ERR_UNSUPPORTED;
+    KNN_CUDA(h, cudaSetDevice(h->device));
+    cudaStream_t st = cuda_stream ? static_cast<cudaStream_t>(cuda_stream) : h->stream;
+
+    const int64_t m = h->m;
+    const bool tensor = (metric == KNN_L2) && h->opt.precision != KNN_FP32;
+    const int prec = tensor ? (h->opt.precision == KNN_BF16 ? kBF16 : kTF32) : 0;
+    if (tensor) {
+        knn_status s = build_lowp(h, prec);
+        if (s != KNN_OK) return s;
+    }
+
+    // candidates per (query, split)
+    int c;
+    if (tensor) {
+        c = h->opt.rerank_factor * k;
+        const int cmax = tc_max_candidates(h->kp, prec);
+        if (c > cmax) c = cmax;
+    } else {
+        const int margin = k / 4 > 8 ? k / 4 : 8;
+        c = k + margin;
+        if (c > cc_max_candidates()) c = cc_max_candidates();
+    }
+    if (c > m) c = static_cast<int>(m);
+    if (c < k) return KNN_ERR_UNSUPPORTED;
+
+    // reference splits: enough CTAs to fill the GPU, each split much larger
+    // than c, and all splits' candidates within one finalize pool
+    int S = 1;
+    if (!tensor) {
+        const int64_t tiles = (n + 63) / 64;
+        const int64_t want = 2LL * h->num_sms;
+        if (tiles < want) S = ceil_div(want, tiles);
+        const int64_t max_by_size = m / (8LL * c);
+        if (S > max_by_size) S = static_cast<int>(max_by_size);
+        if (S < 1) S = 1;
+        while (S > 1 && static_cast<int64_t>(S) * c > finalize_max_pool()) --S;
+    }
+    int64_t chunk = (m + S - 1) / S;
+    chunk = (chunk + 127) / 128 * 128;
+    S = ceil_div(m, chunk);
+    if (static_cast<int64_t>(S) * c > finalize_max_pool()) return KNN_ERR_UNSUPPORTED;
+
+    // fallback grid: scratch of grid * m doubles, at most 64 MiB
+    int64_t fb_grid = (64LL << 20) / (8 * m);
+    if (fb_grid > 64) fb_grid = 64;
+    if (fb_grid < 1) fb_grid = 1;
+
+    // workspace layout
+    Carve cv;
+    const size_t off_cand = cv.take(static_cast<size_t>(n) * S * c * sizeof(uint64_t));
+    const size_t off_list = cv.take(static_cast<size_t>(n) * sizeof(int32_t));
+    const size_t off_scr = cv.take(static_cast<size_t>(fb_grid) * m * sizeof(double));
+    size_t off_q = 0, off_ql = 0, off_dist = 0, off_idx = 0;
+    if (!io_on_device) {
+        off_q = cv.take(static_cast<size_t>(n) * d * sizeof(float));
+        off_dist = cv.take(static_cast<size_t>(n) * k * sizeof(float));
+        off_idx = cv.take(static_cast<size_t>(n) * k * sizeof(int32_t));
+    }
+    if (tensor) off_ql = cv.take(static_cast<size_t>(n) * h->kp * (prec == kBF16 ? 2 : 4));
+    knn_status s = ensure_workspace(h, cv.off);
+    if (s != KNN_OK) return s;
+    unsigned char* ws = h->ws;
+
+    const float* Qd = Q;
+    float* dd = dist_out;
+    int32_t* id = idx_out;
+    h->nstages = 0;
+    if (h->profiling) cudaEventRecord(h->ev[0], st);
+    if (!io_on_device) {
+        Qd = reinterpret_cast<float*>(ws + off_q);
+        dd = reinterpret_cast<float*>(ws + off_dist);
+        id = reinterpret_cast<int32_t*>(ws + off_idx);
+        KNN_CUDA(h, cudaMemcpyAsync(const_cast<float*>(Qd), Q, static_cast<size_t>(n) * d * 4,
+                                    cudaMemcpyHostToDevice, st));
+        stage(h, st, "h2d");
+    }
+
+    CandidateSet cs;
+    cs.keys = reinterpret_cast<uint64_t*>(ws + off_cand);
+    cs.n = n;
+    cs.S = S;
+    cs.c = c;
+    cs.chunk = chunk;
+    cs.exact = tensor ? 0 : 1;
+
+    Counters* ctr = h->counters;
+    KNN_CUDA(h, cudaMemsetAsync(&ctr->fallback_count, 0, sizeof(int32_t), st));
+    int l = 0;
+    if (tensor) {
+        void* Ql = ws + off_ql;
+        KNN_CUDA(h, launch_prepare_lowp(Qd, n, d, h->kp, prec, Ql, nullptr, st, &l));
+        stage(h, st, "prepare_q");
+        KNN_CUDA(h, launch_tc_select(Ql, n, h->R_lp, h->r_norms, m, h->kp, prec, cs,
+                                     &ctr->error_flag, st, &l));
+        stage(h, st, "tc_select");
+    } else {
+        KNN_CUDA(h, launch_cc_select(Qd, n, h->R, m, d, metric, cs, st, &l));
+        stage(h, st, "cc_select");
+    }
+
+    FinalizeArgs fa;
+    fa.Q = Qd;
+    fa.R = h->R;
+    fa.n = n;
+    fa.m = m;
+    fa.d = d;
+    fa.k = k;
+    fa.metric = metric;
+    fa.cand = cs;
+    fa.dist_out = dd;
+    fa.idx_out = id;
+    fa.fallback_count = &ctr->fallback_count;
+    fa.fallback_list = reinterpret_cast<int32_t*>(ws + off_list);
+    fa.recheck_counter = &ctr->recheck_total;
+    fa.fallback_total = &ctr->fallback_total;
+    KNN_CUDA(h, launch_finalize(fa, st, &l));
+    stage(h, st, "finalize");
+    KNN_CUDA(h, launch_fallback(fa, reinterpret_cast<double*>(ws + off_scr),
+                                static_cast<int32_t>(fb_grid), st, &l));
+    stage(h, st, "fallback");
+    h->launches += l;
+    h->searches += 1;
+
+    if (!io_on_device) {
+        KNN_CUDA(h, cudaMemcpyAsync(dist_out, dd, static_cast<size_t>(n) * k * 4,
+                                    cudaMemcpyDeviceToHost, st));
+        KNN_CUDA(h, cudaMemcpyAsync(idx_out, id, static_cast<size_t>(n) * k * 4,
+                                    cudaMemcpyDeviceToHost, st));
+        stage(h, st, "d2h");
+        KNN_CUDA(h, cudaStreamSynchronize(st));
+        int32_t flag = 0;
+        KNN_CUDA(h, cudaMemcpy(&flag, &ctr->error_flag, sizeof(flag), cudaMemcpyDeviceToHost));
+        if (flag) {
+            KNN_CUDA(h, cudaMemset(&ctr->error_flag, 0, sizeof(flag)));
+            h->last_error = "a bounded device-side wait gave up";
+            return KNN_ERR_TIMEOUT;
+        }
+    }
+    return KNN_OK;
+}
+
+knn_status knn_sync(knn_handle h) {
+    if (!h) return KNN_ERR_INVALID;
+    KNN_CUDA(h, cudaSetDevice(h->device));
+    KNN_CUDA(h, cudaDeviceSynchronize());
+    int32_t flag = 0;
+    KNN_CUDA(h, cudaMemcpy(&flag, &h->counters->error_flag, sizeof(flag), cudaMemcpyDeviceToHost));
+    if (flag) {
+        KNN_CUDA(h, cudaMemset(&h->counters->error_flag, 0, sizeof(flag)));
+        h->last_error = "a bounded device-side wait gave up";
+        return KNN_ERR_TIMEOUT;
+    }
+    return KNN_OK;
+}
+
+knn_status knn_get_stats(knn_handle h, knn_stats* out) {
+    if (!h || !out) return KNN_ERR_INVALID;
+    KNN_CUDA(h, cudaSetDevice(h->device));
+    KNN_CUDA(h, cudaDeviceSynchronize());
+    Counters c{};
+    KNN_CUDA(h, cudaMemcpy(&c, h->counters, sizeof(c), cudaMemcpyDeviceToHost));
+    out->searches = h->searches;
+    out->kernel_launches = h->launches;
+    out->recheck_entries = static_cast<int64_t>(c.recheck_total);
+    out->fallback_queries = static_cast<int64_t>(c.fallback_total);
+    out->workspace_bytes = static_cast<int64_t>(h->ws_bytes);
+    return KNN_OK;
+}
+
+knn_status knn_set_profiling(knn_handle h, int on) {
+    if (!h) return KNN_ERR_INVALID;
+    h->profiling = on != 0;
+    h->nstages = 0;
+    return KNN_OK;
+}
+
+knn_status knn_get_profile(knn_handle h, float* ms, const char** names, int32_t cap,
+                           int32_t* count) {
+    if (!h || !count || cap < 0 || (cap > 0 && (!ms || !names))) return KNN_ERR_INVALID;
+    KNN_CUDA(h, cudaSetDevice(h->device));
+    const int ns = h->nstages;
+    if (ns > 0) KNN_CUDA(h, cudaEventSynchronize(h->ev[ns]));
+    for (int i = 0; i < ns && i < cap; ++i) {
+        float t = 0.f;
+        KNN_CUDA(h, cudaEventElapsedTime(&t, h->ev[i], h->ev[i + 1]));
+        ms[i] = t;
+        names[i] = h->stage_names[i];
+    }
+    *count = ns;
+    return KNN_OK;
+}
+
+const char* knn_status_string(knn_status s) {
+    switch (s) {
+        case KNN_OK: return "ok";
+        case KNN_ERR_INVALID: return "invalid argument";
+        case KNN_ERR_OOM: return "out of device memory";
+        case KNN_ERR_CUDA: return "CUDA error";
+        case KNN_ERR_TIMEOUT: return "device wait timed out";
+        case KNN_ERR_NOREF: return "no reference set";
+        case KNN_ERR_BUSY: return "handle busy";
+        case KNN_ERR_UNSUPPORTED: return "unsupported by this build";
+    }
+    return "unknown status";
+}
+
+const char* knn_last_error(knn_handle h) { return h ? h->last_error.c_str() : ""; }
+
+}  // extern "C"

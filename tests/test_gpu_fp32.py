@@ -1,0 +1,182 @@
+"""Parity of the float32 CUDA-core path with the oracle (needs a GB300).
+
+Every case calls the C ABI through the ctypes binding and compares with the
+oracle element by element under the rule of tests/parity.py.  Shapes span
+several tiles with ragged tails (queries per CTA 64, references per tile 128,
+coordinates per stage 16), k = 1 and k = m, duplicates, lattices full of
+exact ties (which exercise the float64 re-check and the exact fallback), and
+the full n = m = 38400, d = 96 workload checked on sampled queries.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_0804_1448_gb300 import inputs
+from tests import parity
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def knn():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_0804_1448_gb300 import knn as mod
+    return mod
+
+
+def run_case(knn, R, Q, k, metric, device_io=True):
+    import torch
+    idx_ = knn.Index(0, "fp32")
+    if device_io:
+        idx_.set_reference(torch.from_numpy(R).cuda())
+        dist, ind = idx_.search(torch.from_numpy(Q).cuda(), k, metric)
+        torch.cuda.synchronize()
+        out = dist.cpu().numpy(), ind.cpu().numpy()
+    else:
+        idx_.set_reference(R)
+        out = idx_.search(Q, k, metric)
+    st = idx_.stats()
+    idx_.close()
+    return out[0], out[1], st
+
+
+def check(knn, R, Q, k, metric, device_io=True):
+    m = R.shape[0]
+    g_dist, g_idx, st = run_case(knn, R, Q, k, metric, device_io)
+    ko = parity.oracle_k(k, m)
+    o_dist, o_idx = oracle.knn(R, Q, ko, metric)
+    rows, exact = parity.compare(g_dist, g_idx, o_dist, o_idx, k, m)
+    return rows, exact, st
+
+
+@pytest.mark.parametrize("metric", ["l2", "l1"])
+def test_uniform_n1200_d8_k20(knn, metric):
+    R, Q, k = inputs.workload("uniform_n1200_d8_k20")
+    rows, exact, _ = check(knn, R, Q, k, metric)
+    assert rows == 1200
+
+
+@pytest.mark.parametrize("metric", ["l2", "l1"])
+@pytest.mark.parametrize("n,m,d,k", [
+    (1, 1, 1, 1),            # single point
+    (7, 300, 3, 5),          # n below one query tile
+    (130, 1000, 33, 20),     # ragged in every dimension
+    (257, 129, 16, 129),     # k = m, m one past a tile
+    (65, 4099, 7, 1),        # k = 1, many splits
+    (100, 2000, 96, 64),
+    (50, 700, 200, 100),     # d over several stages, large k
+])
+def test_ragged_shapes(knn, metric, n, m, d, k):
+    R = inputs.uniform(m, d, seed=1000 + m)
+    Q = inputs.uniform(n, d, seed=2000 + n)
+    check(knn, R, Q, k, metric)
+
+
+def test_host_and_device_io_agree(knn):
+    R = inputs.uniform(3000, 24, seed=5)
+    Q = inputs.uniform(333, 24, seed=6)
+    d1, i1, _ = run_case(knn, R, Q, 17, "l2", device_io=True)
+    d2, i2, _ = run_case(knn, R, Q, 17, "l2", device_io=False)
+    np.testing.assert_array_equal(i1, i2)
+    np.testing.assert_array_equal(d1, d2)
+
+
+def test_queries_drawn_from_reference(knn):
+    R = inputs.uniform(5000, 12, seed=15)
+    Q = R[::37].copy()
+    for metric in ("l2", "l1"):
+        g_dist, g_idx, _ = run_case(knn, R, Q, 10, metric)
+        assert np.all(g_dist[:, 0] == 0.0)
+        np.testing.assert_array_equal(g_idx[:, 0], np.arange(0, 5000, 37))
+        check(knn, R, Q, 10, metric)
+
+
+def test_lattice_ties(knn):
+    """Integer lattice: distances tie in large groups; indices must follow
+    the smaller-index rule exactly."""
+    R = inputs.lattice(9, 3)            # 729 points
+    Q = inputs.lattice(9, 3)[::5] + np.float32(0.5) * (np.arange(3) == 0)
+    for metric in ("l2", "l1"):
+        for k in (1, 6, 27, 100):
+            m = R.shape[0]
+            g_dist, g_idx, _ = run_case(knn, R, Q, k, metric)
+            o_dist, o_idx = oracle.knn(R, Q, k, metric)
+            np.testing.assert_array_equal(g_idx, o_idx)
+            np.testing.assert_allclose(g_dist, o_dist, rtol=1e-6, atol=0)
+
+
+def test_all_identical_points_use_exact_fallback(knn):
+    R = np.full((2000, 5), 0.125, dtype=np.float32)
+    Q = np.array([[0.125] * 5, [0.5] * 5], dtype=np.float32)
+    g_dist, g_idx, st = run_case(knn, R, Q, 40, "l2")
+    assert g_idx.tolist() == [list(range(40))] * 2
+    assert st["fallback_queries"] == 2
+    np.testing.assert_allclose(g_dist[1], np.full(40, np.sqrt(5 * 0.375 ** 2)), rtol=1e-7)
+
+
+def test_duplicates_across_splits(knn):
+    base = inputs.uniform(300, 8, seed=77)
+    R = np.concatenate([base] * 20)      # every point 20 times, spread over the range
+    Q = base[:40].copy()
+    for metric in ("l2", "l1"):
+        rows, exact, st = check(knn, R, Q, 30, metric)
+        g_dist, g_idx, _ = run_case(knn, R, Q, 30, metric)
+        o_dist, o_idx = oracle.knn(R, Q, 30, metric)
+        np.testing.assert_array_equal(g_idx, o_idx)
+
+
+def test_prefix_property(knn):
+    R = inputs.uniform(6000, 20, seed=88)
+    Q = inputs.uniform(200, 20, seed=89)
+    d_big, i_big, _ = run_case(knn, R, Q, 50, "l2")
+    for k in (1, 10, 49):
+        d_k, i_k, _ = run_case(knn, R, Q, k, "l2")
+        np.testing.assert_array_equal(i_k, i_big[:, :k])
+        np.testing.assert_array_equal(d_k, d_big[:, :k])
+
+
+@pytest.mark.parametrize("metric", ["l2", "l1"])
+def test_uniform_n38400_d96_k20_sampled(knn, metric):
+    """Full-size Table-1 shape (N = 38400, D = 96, k = 20): all queries run on
+    the GPU in one call; 96 sampled rows are checked against the oracle."""
+    R, Q, k = inputs.workload("uniform_n38400_d96_k20")
+    g_dist, g_idx, st = run_case(knn, R, Q, k, metric)
+    sel = np.random.default_rng(123).choice(Q.shape[0], 96, replace=False)
+    sel[0], sel[1] = 0, Q.shape[0] - 1
+    o_dist, o_idx = oracle.knn_subset(R, Q, sel, parity.oracle_k(k, R.shape[0]), metric)
+    parity.compare(g_dist[sel], g_idx[sel], o_dist, o_idx, k, R.shape[0])
+    # properties that hold for every row
+    assert np.all(np.diff(g_dist, axis=1) >= 0)
+    assert np.all((g_idx >= 0) & (g_idx < R.shape[0]))
+
+
+def test_invalid_arguments(knn):
+    import torch
+    ix = knn.Index(0, "fp32")
+    Q = torch.zeros((4, 3), device="cuda")
+    with pytest.raises(knn.KnnError) as e:
+        ix.search(Q, 1)
+    assert e.value.status == 5            # KNN_ERR_NOREF
+    ix.set_reference(torch.rand((10, 3), device="cuda"))
+    for bad_k in (0, 11):
+        with pytest.raises(knn.KnnError) as e:
+            ix.search(Q, bad_k)
+        assert e.value.status == 1
+    with pytest.raises(knn.KnnError) as e:
+        ix.search(torch.zeros((4, 5), device="cuda"), 1)
+    assert e.value.status == 1
+    d, i = ix.search(torch.zeros((0, 3), device="cuda"), 3)
+    assert d.shape == (0, 3)
+    ix.close()
+
+
+def test_workspace_limit_reports_oom(knn):
+    import torch
+    ix = knn.Index(0, "fp32", workspace_limit=1024)
+    ix.set_reference(torch.rand((5000, 16), device="cuda"))
+    with pytest.raises(knn.KnnError) as e:
+        ix.search(torch.rand((1000, 16), device="cuda"), 10)
+    assert e.value.status == 2
+    ix.close()

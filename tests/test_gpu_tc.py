@@ -1,0 +1,103 @@
+"""Tensor-core form (bf16 / tf32 tcgen05 contraction, float32 re-rank of
+rerank_factor*k candidates, float64 near-tie re-check) against the oracle.
+
+The candidates are ranked with low-precision products, so a true neighbour can
+in principle fall outside them; what is checked is (a) recall@k against the
+float64 oracle, stated per case, and (b) for every returned entry, that its
+distance is the exact distance of that reference (float32 re-rank), i.e. rows
+whose indices were all recalled match the oracle under the parity rule.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_0804_1448_gb300 import inputs
+from tests import parity
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def knn():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_0804_1448_gb300 import knn as mod
+    return mod
+
+
+def run(knn, R, Q, k, precision, rerank=4):
+    import torch
+    ix = knn.Index(0, precision, rerank_factor=rerank)
+    ix.set_reference(torch.from_numpy(R).cuda())
+    dist, idx = ix.search(torch.from_numpy(Q).cuda(), k, "l2")
+    ix.sync()
+    out = dist.cpu().numpy(), idx.cpu().numpy()
+    ix.close()
+    return out
+
+
+def check_recalled_rows(R, Q, g_dist, g_idx, o_dist, o_idx, k):
+    """Rows that recalled every true neighbour must match the oracle exactly
+    (parity rule); every returned distance must be that reference's exact
+    distance within 1e-5 relative."""
+    m = R.shape[0]
+    full = [i for i in range(Q.shape[0])
+            if set(g_idx[i, :k].tolist()) == set(o_idx[i, :k].tolist())]
+    if full:
+        parity.compare(g_dist[full], g_idx[full], o_dist[full], o_idx[full], k, m)
+    qi = np.repeat(np.arange(Q.shape[0]), k)
+    keys = oracle.key_pairs(R, Q, qi, g_idx.reshape(-1), "l2")
+    exact = np.sqrt(keys).reshape(g_dist.shape)
+    np.testing.assert_allclose(g_dist, exact, rtol=1e-5, atol=0)
+    return len(full)
+
+
+@pytest.mark.parametrize("precision", ["bf16", "tf32"])
+@pytest.mark.parametrize("n,m,d,k", [
+    (1, 1, 1, 1),
+    (7, 300, 3, 5),           # less than one tile of queries and references
+    (130, 1000, 33, 20),      # ragged: queries, references and coordinates
+    (300, 4099, 96, 10),      # references one past a multiple of 128... plus 3
+    (256, 2048, 128, 16),
+    (129, 5000, 8, 20),
+])
+def test_uniform_shapes(knn, precision, n, m, d, k):
+    R = inputs.uniform(m, d, seed=3000 + m)
+    Q = inputs.uniform(n, d, seed=4000 + n)
+    g_dist, g_idx = run(knn, R, Q, k, precision)
+    o_dist, o_idx = oracle.knn(R, Q, parity.oracle_k(k, m), "l2")
+    rec = parity.recall(g_idx, o_idx, k)
+    assert rec >= 0.999, f"recall@{k} = {rec}"
+    check_recalled_rows(R, Q, g_dist, g_idx, o_dist, o_idx, k)
+
+
+@pytest.mark.parametrize("precision", ["bf16", "tf32"])
+def test_uniform_n1200_d8_k20(knn, precision):
+    R, Q, k = inputs.workload("uniform_n1200_d8_k20")
+    g_dist, g_idx = run(knn, R, Q, k, precision)
+    o_dist, o_idx = oracle.knn(R, Q, parity.oracle_k(k, R.shape[0]), "l2")
+    assert parity.recall(g_idx, o_idx, k) == 1.0
+    check_recalled_rows(R, Q, g_dist, g_idx, o_dist, o_idx, k)
+
+
+@pytest.mark.parametrize("precision", ["bf16", "tf32"])
+def test_uniform_n38400_d96_k20_sampled(knn, precision):
+    """Full-size Table-1 shape in one launch; 128 sampled rows against the oracle."""
+    R, Q, k = inputs.workload("uniform_n38400_d96_k20")
+    g_dist, g_idx = run(knn, R, Q, k, precision)
+    sel = np.random.default_rng(7).choice(Q.shape[0], 128, replace=False)
+    sel[0], sel[1] = 0, Q.shape[0] - 1
+    o_dist, o_idx = oracle.knn_subset(R, Q, sel, parity.oracle_k(k, R.shape[0]), "l2")
+    assert parity.recall(g_idx[sel], o_idx, k) == 1.0
+    check_recalled_rows(R, Q[sel], g_dist[sel], g_idx[sel], o_dist, o_idx, k)
+    assert np.all(np.diff(g_dist, axis=1) >= 0)
+
+
+def test_self_neighbours(knn):
+    R = inputs.uniform(4000, 40, seed=99)
+    Q = R[::13].copy()
+    for precision in ("bf16", "tf32"):
+        g_dist, g_idx = run(knn, R, Q, 5, precision)
+        np.testing.assert_array_equal(g_idx[:, 0], np.arange(0, 4000, 13))
+        assert np.all(g_dist[:, 0] == 0.0)
