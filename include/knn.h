@@ -145,6 +145,13 @@ typedef struct {
     int64_t recheck_entries;   /* candidates re-checked in float64 */
     int64_t fallback_queries;  /* queries finished by the exact float64 pass */
     int64_t workspace_bytes;   /* device scratch currently held */
+    /* why queries went to the exact float64 pass (tensor-core forms: the
+       filtered list was shorter than the candidates wanted, overflowed, or
+       its cut kept too many; float32 form: completeness not certified) */
+    int64_t fallback_short_list;
+    int64_t fallback_overflow;
+    int64_t fallback_wide_cut;
+    int64_t fallback_uncertified;
 } knn_stats;
 
 knn_status knn_get_stats(knn_handle h, knn_stats* out);

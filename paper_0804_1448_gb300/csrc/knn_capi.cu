@@ -22,6 +22,7 @@ struct Counters {
     int32_t error_flag;                     // set by a kernel whose bounded wait gave up
     unsigned long long recheck_total;       // float64 re-checked candidates
     unsigned long long fallback_total;      // queries finished by the fallback
+    unsigned long long fallback_reason[4];  // short list, overflow, wide cut, uncertified
 };
 
 }  // namespace
@@ -139,7 +140,7 @@ knn_status build_lowp(knn_ctx* h, int prec) {
     const size_t elt = (prec == kBF16) ? 2 : 4;
     KNN_CUDA(h, cudaMalloc(&h->R_lp, static_cast<size_t>(h->m) * kp * elt));
     int l = 0;
-    KNN_CUDA(h, launch_prepare_lowp(h->R, h->m, h->d, kp, prec, h->R_lp, h->r_norms, h->stream, &l));
+    KNN_CUDA(h, launch_prepare_ref(h->R, h->m, h->d, kp, prec, h->R_lp, h->r_norms, h->stream, &l));
     h->launches += l;
     KNN_CUDA(h, cudaStreamSynchronize(h->stream));
     h->kp = kp;
@@ -273,24 +274,31 @@ knn_status knn_search(knn_handle h, const float* Q, int64_t n, int32_t d, int32_
         if (s != KNN_OK) return s;
     }
 
-    // candidates per (query, split)
+    // candidates per query: k plus a margin (float32), rerank_factor * k (tensor cores)
     int c;
     if (tensor) {
         c = h->opt.rerank_factor * k;
-        const int cmax = tc_max_candidates(h->kp, prec);
-        if (c > cmax) c = cmax;
+        if (c > (finalize_max_pool() - 32) / 2) c = (finalize_max_pool() - 32) / 2;
+        if (c < k) return KNN_ERR_UNSUPPORTED;
     } else {
         const int margin = k / 4 > 8 ? k / 4 : 8;
         c = k + margin;
         if (c > cc_max_candidates()) c = cc_max_candidates();
+        if (c > m) c = static_cast<int>(m);
+        if (c < k) return KNN_ERR_UNSUPPORTED;
     }
-    if (c > m) c = static_cast<int>(m);
-    if (c < k) return KNN_ERR_UNSUPPORTED;
 
-    // reference splits: enough CTAs to fill the GPU, each split much larger
-    // than c, and all splits' candidates within one finalize pool
+    // float32 path: reference splits so that enough CTAs fill the GPU, each
+    // split much larger than c, all splits' candidates within one finalize pool
     int S = 1;
-    if (!tensor) {
+    int64_t chunk = m;
+    TcPlan plan{};
+    if (tensor) {
+        plan = tc_plan(n, m, h->kp, prec, c, h->num_sms);
+        if (plan.stages == 0) return KNN_ERR_UNSUPPORTED;
+        S = plan.S;
+        chunk = plan.chunk;
+    } else {
         const int64_t tiles = (n + 63) / 64;
         const int64_t want = 2LL * h->num_sms;
         if (tiles < want) S = ceil_div(want, tiles);
@@ -298,11 +306,11 @@ knn_status knn_search(knn_handle h, const float* Q, int64_t n, int32_t d, int32_
         if (S > max_by_size) S = static_cast<int>(max_by_size);
         if (S < 1) S = 1;
         while (S > 1 && static_cast<int64_t>(S) * c > finalize_max_pool()) --S;
+        chunk = (m + S - 1) / S;
+        chunk = (chunk + 127) / 128 * 128;
+        S = ceil_div(m, chunk);
+        if (static_cast<int64_t>(S) * c > finalize_max_pool()) return KNN_ERR_UNSUPPORTED;
     }
-    int64_t chunk = (m + S - 1) / S;
-    chunk = (chunk + 127) / 128 * 128;
-    S = ceil_div(m, chunk);
-    if (static_cast<int64_t>(S) * c > finalize_max_pool()) return KNN_ERR_UNSUPPORTED;
 
     // fallback grid: scratch of grid * m doubles, at most 64 MiB
     int64_t fb_grid = (64LL << 20) / (8 * m);
@@ -311,16 +319,23 @@ knn_status knn_search(knn_handle h, const float* Q, int64_t n, int32_t d, int32_
 
     // workspace layout
     Carve cv;
-    const size_t off_cand = cv.take(static_cast<size_t>(n) * S * c * sizeof(uint64_t));
+    size_t off_cand = 0, off_ql = 0, off_gmax = 0, off_lists = 0, off_counts = 0;
+    if (tensor) {
+        off_ql = cv.take(static_cast<size_t>(n) * h->kp * (prec == kBF16 ? 2 : 4));
+        if (plan.pilot) off_gmax = cv.take(static_cast<size_t>(n) * plan.G * 4);
+        off_lists = cv.take(static_cast<size_t>(n) * S * plan.cap * sizeof(uint64_t));
+        off_counts = cv.take(static_cast<size_t>(n) * S * sizeof(int32_t));
+    } else {
+        off_cand = cv.take(static_cast<size_t>(n) * S * c * sizeof(uint64_t));
+    }
     const size_t off_list = cv.take(static_cast<size_t>(n) * sizeof(int32_t));
     const size_t off_scr = cv.take(static_cast<size_t>(fb_grid) * m * sizeof(double));
-    size_t off_q = 0, off_ql = 0, off_dist = 0, off_idx = 0;
+    size_t off_q = 0, off_dist = 0, off_idx = 0;
     if (!io_on_device) {
         off_q = cv.take(static_cast<size_t>(n) * d * sizeof(float));
         off_dist = cv.take(static_cast<size_t>(n) * k * sizeof(float));
         off_idx = cv.take(static_cast<size_t>(n) * k * sizeof(int32_t));
     }
-    if (tensor) off_ql = cv.take(static_cast<size_t>(n) * h->kp * (prec == kBF16 ? 2 : 4));
     knn_status s = ensure_workspace(h, cv.off);
     if (s != KNN_OK) return s;
     unsigned char* ws = h->ws;
@@ -339,30 +354,49 @@ knn_status knn_search(knn_handle h, const float* Q, int64_t n, int32_t d, int32_
         stage(h, st, "h2d");
     }
 
-    CandidateSet cs;
-    cs.keys = reinterpret_cast<uint64_t*>(ws + off_cand);
-    cs.n = n;
-    cs.S = S;
-    cs.c = c;
-    cs.chunk = chunk;
-    cs.exact = tensor ? 0 : 1;
-
     Counters* ctr = h->counters;
     KNN_CUDA(h, cudaMemsetAsync(&ctr->fallback_count, 0, sizeof(int32_t), st));
     int l = 0;
+    FinalizeArgs fa{};
     if (tensor) {
         void* Ql = ws + off_ql;
-        KNN_CUDA(h, launch_prepare_lowp(Qd, n, d, h->kp, prec, Ql, nullptr, st, &l));
+        uint64_t* lists = reinterpret_cast<uint64_t*>(ws + off_lists);
+        int32_t* counts = reinterpret_cast<int32_t*>(ws + off_counts);
+        KNN_CUDA(h, launch_prepare_query(Qd, n, d, h->kp, prec, Ql, st, &l));
         stage(h, st, "prepare_q");
-        KNN_CUDA(h, launch_tc_select(Ql, n, h->R_lp, h->r_norms, m, h->kp, prec, cs,
+        if (plan.pilot) {
+            uint32_t* gmax = reinterpret_cast<uint32_t*>(ws + off_gmax);
+            KNN_CUDA(h, launch_tc_pilot(plan, Ql, n, h->R_lp, m, h->kp, prec, gmax, &ctr->error_flag,
+                                        st, &l));
+            stage(h, st, "tc_pilot");
+            KNN_CUDA(h, launch_tc_threshold(plan, gmax, n, d, h->kp, prec, Ql, st, &l));
+            stage(h, st, "tc_threshold");
+        }
+        KNN_CUDA(h, launch_tc_filter(plan, Ql, n, h->R_lp, m, h->kp, prec, lists, counts,
                                      &ctr->error_flag, st, &l));
-        stage(h, st, "tc_select");
+        stage(h, st, "tc_filter");
+        fa.use_hits = 1;
+        fa.hits.keys = lists;
+        fa.hits.counts = counts;
+        fa.hits.S = S;
+        fa.hits.cap = plan.cap;
+        fa.hits.c = c;
+        fa.cand.exact = 0;
+        fa.cand.S = 1;
+        fa.cand.c = c;
     } else {
+        CandidateSet cs;
+        cs.keys = reinterpret_cast<uint64_t*>(ws + off_cand);
+        cs.n = n;
+        cs.S = S;
+        cs.c = c;
+        cs.chunk = chunk;
+        cs.exact = 1;
         KNN_CUDA(h, launch_cc_select(Qd, n, h->R, m, d, metric, cs, st, &l));
         stage(h, st, "cc_select");
+        fa.use_hits = 0;
+        fa.cand = cs;
     }
-
-    FinalizeArgs fa;
     fa.Q = Qd;
     fa.R = h->R;
     fa.n = n;
@@ -370,13 +404,13 @@ knn_status knn_search(knn_handle h, const float* Q, int64_t n, int32_t d, int32_
     fa.d = d;
     fa.k = k;
     fa.metric = metric;
-    fa.cand = cs;
     fa.dist_out = dd;
     fa.idx_out = id;
     fa.fallback_count = &ctr->fallback_count;
     fa.fallback_list = reinterpret_cast<int32_t*>(ws + off_list);
     fa.recheck_counter = &ctr->recheck_total;
     fa.fallback_total = &ctr->fallback_total;
+    fa.fallback_reason = ctr->fallback_reason;
     KNN_CUDA(h, launch_finalize(fa, st, &l));
     stage(h, st, "finalize");
     KNN_CUDA(h, launch_fallback(fa, reinterpret_cast<double*>(ws + off_scr),
@@ -428,6 +462,10 @@ knn_status knn_get_stats(knn_handle h, knn_stats* out) {
     out->recheck_entries = static_cast<int64_t>(c.recheck_total);
     out->fallback_queries = static_cast<int64_t>(c.fallback_total);
     out->workspace_bytes = static_cast<int64_t>(h->ws_bytes);
+    out->fallback_short_list = static_cast<int64_t>(c.fallback_reason[0]);
+    out->fallback_overflow = static_cast<int64_t>(c.fallback_reason[1]);
+    out->fallback_wide_cut = static_cast<int64_t>(c.fallback_reason[2]);
+    out->fallback_uncertified = static_cast<int64_t>(c.fallback_reason[3]);
     return KNN_OK;
 }
 

@@ -39,6 +39,22 @@ __device__ __forceinline__ double f32_rel_bound(int d) {
 template <int METRIC>
 __device__ __forceinline__ float dist_f32(const float* q, const float* __restrict__ r, int d) {
     float acc = 0.f;
+    if ((d & 3) == 0) {   // rows are 16-byte aligned: vector loads, same order of operations
+        const float4* r4 = reinterpret_cast<const float4*>(r);
+        const float4* q4 = reinterpret_cast<const float4*>(q);
+        for (int t = 0; t < d / 4; ++t) {
+            const float4 x = __ldg(r4 + t);
+            const float4 y = q4[t];
+            const float e0 = y.x - x.x, e1 = y.y - x.y, e2 = y.z - x.z, e3 = y.w - x.w;
+            if (METRIC == kL2) {
+                acc = fmaf(e0, e0, acc); acc = fmaf(e1, e1, acc);
+                acc = fmaf(e2, e2, acc); acc = fmaf(e3, e3, acc);
+            } else {
+                acc += fabsf(e0); acc += fabsf(e1); acc += fabsf(e2); acc += fabsf(e3);
+            }
+        }
+        return acc;
+    }
     for (int t = 0; t < d; ++t) {
         const float diff = q[t] - __ldg(r + t);
         if (METRIC == kL2) acc = fmaf(diff, diff, acc);
@@ -80,13 +96,107 @@ struct WarpScratch {
     int32_t* re;     // [P] run end (inclusive)
     int32_t* perm;   // [P] output position -> source position inside re-checked runs
     uint64_t* smax;  // [S] largest original key per split
-    float* qrow;     // [d]
+    int32_t* hist;   // [kBins] histogram of hit-list keys; hist[kBins] = fill counter
+    float* qrow;     // [d], 16-byte aligned
 };
 
+constexpr int kBins = 64;
+
 __host__ __device__ inline size_t warp_scratch_bytes(int P, int S, int d) {
-    const size_t b = static_cast<size_t>(P) * (8 + 8 + 4 + 4 + 4) + static_cast<size_t>(S) * 8 +
-                     static_cast<size_t>(d) * 4;
+    const size_t b = static_cast<size_t>(P) * (8 + 8 + 4 + 4 + 4) + static_cast<size_t>((S + 1) & ~1) * 8 +
+                     (kBins + 4) * 4 + (static_cast<size_t>(d) + 4) * 4;
     return (b + 15) & ~static_cast<size_t>(15);
+}
+
+// Hit-list front end: keep every listed reference whose low-precision key
+// falls in the histogram bins up to the one holding rank c (so at least the
+// best c), compute their exact float32 distances into w.keys, and return how
+// many there are; -1 sends the query to the exact fallback.
+template <int METRIC>
+__device__ int gather_hits(const FinalizeArgs& a, int64_t q, int P, WarpScratch& w, int lane) {
+    const HitLists& hl = a.hits;
+    const int S = hl.S, cap = hl.cap;
+    const int d = a.d;
+    const uint64_t* base = hl.keys + q * static_cast<int64_t>(S) * cap;
+    const int32_t* cnts = hl.counts + q * static_cast<int64_t>(S);
+    int total = 0, over = 0;
+    for (int s = lane; s < S; s += 32) {
+        const int cs = cnts[s];
+        over |= cs > cap;
+        total += min(cs, cap);
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        total += __shfl_xor_sync(0xffffffffu, total, o);
+        over |= __shfl_xor_sync(0xffffffffu, over, o);
+    }
+    if (over) return -2;
+    if (total < hl.c && total < a.m) return -1;
+    // range of the order-mapped scores
+    uint32_t omin = 0xffffffffu, omax = 0;
+    for (int s = 0; s < S; ++s) {
+        const int cs = min(cnts[s], cap);
+        for (int e = lane; e < cs; e += 32) {
+            const uint32_t o = static_cast<uint32_t>(base[static_cast<int64_t>(s) * cap + e] >> 32);
+            omin = min(omin, o);
+            omax = max(omax, o);
+        }
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        omin = min(omin, __shfl_xor_sync(0xffffffffu, omin, o));
+        omax = max(omax, __shfl_xor_sync(0xffffffffu, omax, o));
+    }
+    const uint64_t span = static_cast<uint64_t>(omax) - omin + 1;
+    int cut = kBins - 1;            // keep bins 0..cut
+    if (total > hl.c) {
+        for (int b = lane; b < kBins + 4; b += 32) w.hist[b] = 0;
+        __syncwarp();
+        for (int s = 0; s < S; ++s) {
+            const int cs = min(cnts[s], cap);
+            for (int e = lane; e < cs; e += 32) {
+                const uint32_t o = static_cast<uint32_t>(base[static_cast<int64_t>(s) * cap + e] >> 32);
+                atomicAdd(&w.hist[static_cast<int>((static_cast<uint64_t>(o - omin) * kBins) / span)], 1);
+            }
+        }
+        __syncwarp();
+        // smallest bin whose cumulative count reaches c (two bins per lane)
+        const int h0 = w.hist[2 * lane], h1 = w.hist[2 * lane + 1];
+        int incl = h0 + h1;
+        for (int o = 1; o < 32; o <<= 1) {
+            const int v = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += v;
+        }
+        const int excl = incl - h0 - h1;
+        int mine = kBins;
+        if (excl + h0 >= hl.c) mine = 2 * lane;
+        else if (incl >= hl.c) mine = 2 * lane + 1;
+        for (int o = 16; o > 0; o >>= 1) mine = min(mine, __shfl_xor_sync(0xffffffffu, mine, o));
+        cut = mine;
+    }
+    // keep, re-rank in float32
+    if (lane == 0) w.hist[kBins] = 0;
+    __syncwarp();
+    int kept = 0;
+    for (int s = 0; s < S; ++s) {
+        const int cs = min(cnts[s], cap);
+        for (int e0 = 0; e0 < cs; e0 += 32) {
+            const int e = e0 + lane;
+            bool take = false;
+            uint32_t j = 0;
+            if (e < cs) {
+                const uint64_t key = base[static_cast<int64_t>(s) * cap + e];
+                const uint32_t o = static_cast<uint32_t>(key >> 32);
+                take = static_cast<int>((static_cast<uint64_t>(o - omin) * kBins) / span) <= cut;
+                j = key_idx(key);
+            }
+            const unsigned bal = __ballot_sync(0xffffffffu, take);
+            const int pos = kept + __popc(bal & ((1u << lane) - 1u));
+            if (take && pos < P)
+                w.keys[pos] = make_key(dist_f32<METRIC>(w.qrow, a.R + static_cast<int64_t>(j) * d, d), j);
+            kept += __popc(bal);
+        }
+    }
+    __syncwarp();
+    return kept <= P ? kept : -3;
 }
 
 template <int METRIC>
@@ -97,7 +207,7 @@ __global__ void finalize_kernel(FinalizeArgs a, int P, int warps_per_block) {
     if (q >= a.n) return;   // warp-uniform: no block-level sync below
 
     const CandidateSet& cs = a.cand;
-    const int S = cs.S, c = cs.c, Sc = S * c;
+    const int S = a.use_hits ? 1 : cs.S, c = cs.c, Sc = a.use_hits ? 0 : S * c;
     const int d = a.d;
     const size_t per_warp = warp_scratch_bytes(P, S, d);
     unsigned char* base = smem_raw + per_warp * warp;
@@ -105,33 +215,47 @@ __global__ void finalize_kernel(FinalizeArgs a, int P, int warps_per_block) {
     w.keys = reinterpret_cast<uint64_t*>(base);
     w.d64 = w.keys + P;
     w.smax = w.d64 + P;
-    w.rs = reinterpret_cast<int32_t*>(w.smax + S);
+    w.rs = reinterpret_cast<int32_t*>(w.smax + ((S + 1) & ~1));
     w.re = w.rs + P;
     w.perm = w.re + P;
-    w.qrow = reinterpret_cast<float*>(w.perm + P);
+    w.hist = w.perm + P;
+    w.qrow = reinterpret_cast<float*>(w.hist + kBins + 4);
 
     for (int t = lane; t < d; t += 32) w.qrow[t] = a.Q[q * d + t];
     for (int s = lane; s < S; s += 32) w.smax[s] = 0;
+    for (int e = lane; e < P; e += 32) { w.keys[e] = kEmptyKey; w.rs[e] = -1; }
     __syncwarp();
 
     // 1. exact float32 distances of the candidates
     int cnt = 0;
-    const uint64_t* src = cs.keys + q * static_cast<int64_t>(Sc);
-    for (int e0 = 0; e0 < P; e0 += 32) {
-        const int e = e0 + lane;
-        uint64_t nk = kEmptyKey;
-        if (e < Sc) {
-            const uint64_t key = src[e];
-            if (key != kEmptyKey) {
-                const uint32_t j = key_idx(key);
-                nk = make_key(dist_f32<METRIC>(w.qrow, a.R + static_cast<int64_t>(j) * d, d), j);
-                atomicMax(reinterpret_cast<unsigned long long*>(&w.smax[e / c]),
-                          static_cast<unsigned long long>(key));
+    if (!a.use_hits) {
+        const uint64_t* src = cs.keys + q * static_cast<int64_t>(Sc);
+        for (int e0 = 0; e0 < Sc; e0 += 32) {
+            const int e = e0 + lane;
+            uint64_t nk = kEmptyKey;
+            if (e < Sc) {
+                const uint64_t key = src[e];
+                if (key != kEmptyKey) {
+                    const uint32_t j = key_idx(key);
+                    nk = make_key(dist_f32<METRIC>(w.qrow, a.R + static_cast<int64_t>(j) * d, d), j);
+                    atomicMax(reinterpret_cast<unsigned long long*>(&w.smax[e / c]),
+                              static_cast<unsigned long long>(key));
+                }
+                w.keys[e] = nk;
             }
+            cnt += __popc(__ballot_sync(0xffffffffu, nk != kEmptyKey));
         }
-        w.keys[e] = nk;
-        w.rs[e] = -1;
-        cnt += __popc(__ballot_sync(0xffffffffu, nk != kEmptyKey));
+    } else {
+        cnt = gather_hits<METRIC>(a, q, P, w, lane);
+        if (cnt < 0) {   // -1 short list, -2 overflow, -3 the cut kept too many
+            if (lane == 0) {
+                const int pos = atomicAdd(a.fallback_count, 1);
+                a.fallback_list[pos] = static_cast<int32_t>(q);
+                if (a.fallback_total) atomicAdd(a.fallback_total, 1ull);
+                if (a.fallback_reason) atomicAdd(&a.fallback_reason[-cnt - 1], 1ull);
+            }
+            return;
+        }
     }
     __syncwarp();
 
@@ -203,7 +327,7 @@ __global__ void finalize_kernel(FinalizeArgs a, int P, int warps_per_block) {
     auto source_of = [&](int s) { return (w.rs[s] >= 0) ? w.perm[s] : s; };
 
     // 4. completeness of a float32 candidate set
-    if (cs.exact && kk > 0) {
+    if (!a.use_hits && cs.exact && kk > 0) {
         bool have = false;
         double lower = 0.0;
         for (int s = 0; s < S; ++s) {
@@ -225,6 +349,7 @@ __global__ void finalize_kernel(FinalizeArgs a, int P, int warps_per_block) {
                     const int pos = atomicAdd(a.fallback_count, 1);
                     a.fallback_list[pos] = static_cast<int32_t>(q);
                     if (a.fallback_total) atomicAdd(a.fallback_total, 1ull);
+                    if (a.fallback_reason) atomicAdd(&a.fallback_reason[3], 1ull);
                 }
                 return;
             }
@@ -380,11 +505,11 @@ fallback_kernel(FinalizeArgs a, double* __restrict__ scratch) {
 int finalize_max_pool() { return kMaxPool; }
 
 cudaError_t launch_finalize(const FinalizeArgs& a, cudaStream_t st, int* launches) {
-    const int Sc = a.cand.S * a.cand.c;
+    const int want = a.use_hits ? 2 * a.hits.c + 32 : a.cand.S * a.cand.c;
     int P = 32;
-    while (P < Sc) P <<= 1;
+    while (P < want) P <<= 1;
     if (P > kMaxPool) return cudaErrorInvalidValue;
-    const size_t per_warp = warp_scratch_bytes(P, a.cand.S, a.d);
+    const size_t per_warp = warp_scratch_bytes(P, a.use_hits ? 1 : a.cand.S, a.d);
     int wpb = static_cast<int>((48 * 1024) / per_warp);
     wpb = wpb < 1 ? 1 : (wpb > 8 ? 8 : wpb);
     const size_t smem = per_warp * wpb;

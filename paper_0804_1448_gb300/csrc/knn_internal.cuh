@@ -74,7 +74,20 @@ struct CandidateSet {
                       //    (completeness can be certified); 0: ranking scores
 };
 
+// Per-(query, split) lists of references that passed the tensor-core filter;
+// keys rank by the low-precision score (smaller key = nearer).  counts may
+// exceed cap, meaning the list overflowed.
+struct HitLists {
+    const uint64_t* keys;   // [n][S][cap]
+    const int32_t* counts;  // [n][S]
+    int32_t S;
+    int32_t cap;
+    int32_t c;              // keep (at least) the best c before the exact re-rank
+};
+
 struct FinalizeArgs {
+    int32_t use_hits;       // 0: candidates come from `cand`; 1: from `hits`
+    HitLists hits;
     const float* Q;
     const float* R;
     int64_t n, m;
@@ -87,6 +100,7 @@ struct FinalizeArgs {
     int32_t* fallback_list;    // [n] query ids
     unsigned long long* recheck_counter;
     unsigned long long* fallback_total;
+    unsigned long long* fallback_reason;   // [4]: short list, overflow, wide cut, uncertified
 };
 
 // ---- launchers (return cudaSuccess or the launch error) -------------------
@@ -111,17 +125,42 @@ cudaError_t launch_fallback(const FinalizeArgs& a, double* scratch, int32_t grid
 
 enum LowPrecision : int { kTF32 = 1, kBF16 = 2 };
 
-// Build the low-precision operand copy of a point set: rows of `kp` elements
-// (bf16 or tf32-in-fp32), zero padded beyond d, plus the float32 squared
-// norms of the float32 rows (norms may be NULL).
-cudaError_t launch_prepare_lowp(const float* X, int64_t rows, int32_t d, int32_t kp, int prec,
-                                void* X_lp, float* norms, cudaStream_t st, int* launches);
+// Row length (elements) of the low-precision operand copies: d coordinates,
+// four augmentation words (norm halves, threshold halves), zero padded to a
+// whole 32-byte MMA K step.
 int tc_padded_dim(int32_t d, int prec);
-// Largest candidate count per query the tensor-core kernel holds on chip.
-int tc_max_candidates(int32_t kp, int prec);
-// Tensor-core fused q.r + top-c.  Writes cand (exact = 0).
-cudaError_t launch_tc_select(const void* Q_lp, int64_t n, const void* R_lp, const float* r_norms,
-                             int64_t m, int32_t kp, int prec, const CandidateSet& cand,
+
+// Launch plan of the pilot and filter passes for one search.
+struct TcPlan {
+    int32_t mt;          // 128-query tiles per CTA (1 or 2)
+    int32_t kb;          // 128-byte K blocks per operand row
+    int32_t ksteps;      // MMA instructions per tile pair
+    int32_t stages;      // reference-tile ring depth
+    int32_t S;           // reference splits
+    int64_t chunk;       // references per split (multiple of 128)
+    int32_t stride;      // pilot samples every stride-th tile
+    int32_t spt;         // pilot tile slots per split
+    int32_t G;           // pilot group maxima per query
+    int32_t cprime;      // order statistic of the group maxima used as threshold
+    int32_t pilot;       // 0: no pilot, every reference is appended
+    int32_t cap;         // list capacity per (query, split)
+    size_t smem_filter;
+};
+TcPlan tc_plan(int64_t n, int64_t m, int32_t kp, int prec, int32_t c, int num_sms);
+
+// Reference copy [r, -||r||^2/2 (hi, lo), 1, 1, 0..] and float32 norms.
+cudaError_t launch_prepare_ref(const float* R, int64_t m, int32_t d, int32_t kp, int prec,
+                               void* R_lp, float* norms, cudaStream_t st, int* launches);
+// Query copy [q, 1, 1, 0, 0, 0..] (threshold words filled by the threshold pass).
+cudaError_t launch_prepare_query(const float* Q, int64_t n, int32_t d, int32_t kp, int prec,
+                                 void* Q_lp, cudaStream_t st, int* launches);
+cudaError_t launch_tc_pilot(const TcPlan& p, const void* Q_lp, int64_t n, const void* R_lp,
+                            int64_t m, int32_t kp, int prec, uint32_t* gmax, int32_t* error_flag,
+                            cudaStream_t st, int* launches);
+cudaError_t launch_tc_threshold(const TcPlan& p, const uint32_t* gmax, int64_t n, int32_t d,
+                                int32_t kp, int prec, void* Q_lp, cudaStream_t st, int* launches);
+cudaError_t launch_tc_filter(const TcPlan& p, const void* Q_lp, int64_t n, const void* R_lp,
+                             int64_t m, int32_t kp, int prec, uint64_t* lists, int32_t* counts,
                              int32_t* error_flag, cudaStream_t st, int* launches);
 
 }  // namespace knn

@@ -42,7 +42,9 @@ class knn_options(ctypes.Structure):
 class knn_stats(ctypes.Structure):
     _fields_ = [("searches", ctypes.c_int64), ("kernel_launches", ctypes.c_int64),
                 ("recheck_entries", ctypes.c_int64), ("fallback_queries", ctypes.c_int64),
-                ("workspace_bytes", ctypes.c_int64)]
+                ("workspace_bytes", ctypes.c_int64), ("fallback_short_list", ctypes.c_int64),
+                ("fallback_overflow", ctypes.c_int64), ("fallback_wide_cut", ctypes.c_int64),
+                ("fallback_uncertified", ctypes.c_int64)]
 
 
 _H = ctypes.c_void_p
