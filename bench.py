@@ -1,0 +1,302 @@
+#!/usr/bin/env python
+"""Benchmark of the brute-force k-nearest-neighbour search on GB300.
+
+Workload: the largest shape of Table 1 of the paper, N = n = m = 38400 points,
+D = d = 96, k = 20, points uniform in [0,1) (seeded synthetic data; the paper
+does not state its distribution).  One step is one complete search of all
+38400 queries against the 38400 references through the C ABI: the tensor-core
+(bf16) distance + threshold filter, the float32 re-rank, the float64 near-tie
+re-check and the output.  Inputs are resident in HBM when a step starts; L2 is
+flushed (256 MiB write) before every step, outside the timed window.
+
+Also reported: the float32 CUDA-core form on the same workload, the same
+search end to end through the C ABI with pinned host buffers (host<->device
+copies timed), the roofline fraction of the dominant kernel, and the oracle
+timed on the host cores on a bounded sample.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+Under torchrun with N > 1 every rank runs the full workload on its own GPU
+(independent problems, weak scaling); rank 0 prints the line.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = ("queries/s & %roofline at n=m=38400,d=96,k=20 (BF16+rerank vs FP32); "
+          "serve p50/p99")
+WORKLOAD = "uniform_n38400_d96_k20"
+PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
+FALLBACK_PEAKS = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}
+
+
+def parse_args():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=30)
+    p.add_argument("--warmup", type=int, default=5)
+    p.add_argument("--impl", choices=["gb300", "reference"], default="gb300")
+    p.add_argument("--precision", choices=["bf16", "tf32"], default="bf16")
+    p.add_argument("--cpu-seconds", type=float, default=10.0)
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    return p.parse_args()
+
+
+def dist_env():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+class Clocks:
+    """nvidia-smi sampled while the timed region runs."""
+
+    def __init__(self, device: int):
+        self.path = os.path.join(tempfile.gettempdir(), f"knn_clocks_{os.getpid()}.csv")
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        self.proc = None
+        try:
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={device}", f"--query-gpu={q}", "--format=csv,noheader,nounits",
+                 "-lms", "50"], stdout=self.f, stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.f.close()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        with open(self.path) as f:
+            for line in f:
+                parts = [x.strip() for x in line.split(",")]
+                if len(parts) < 9:
+                    continue
+                try:
+                    sm.append(float(parts[1]))
+                    smax.append(float(parts[2]))
+                except ValueError:
+                    continue
+                for nm, v in zip(names, parts[5:9]):
+                    if v.lower() == "active":
+                        reasons.add(nm)
+        os.unlink(self.path)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def load_peaks():
+    try:
+        with open(PEAKS_FILE) as f:
+            return json.load(f), "measured"
+    except (OSError, ValueError):
+        return FALLBACK_PEAKS, "fallback"
+
+
+def cpu_baseline(R, Q, k, seconds):
+    """The oracle, as it stands, on a bounded sample of the workload's queries."""
+    import oracle
+    done, t0 = 0, time.perf_counter()
+    batch = 512
+    while done < Q.shape[0] and time.perf_counter() - t0 < seconds:
+        oracle.knn(R, Q[done:done + batch], k, "l2")
+        done += min(batch, Q.shape[0] - done)
+    dt = time.perf_counter() - t0
+    return {"value": done / dt, "unit": "queries/s", "cores": oracle.max_threads(),
+            "kind": "oracle",
+            "sample": f"{done} of {Q.shape[0]} queries x {R.shape[0]} references, d={R.shape[1]}, "
+                      f"k={k}, float64 with a full sort per query ({dt:.1f} s)"}
+
+
+def run_reference(args):
+    """--impl reference: the oracle timed on the host cores, per step a bounded
+    sample of the workload (no GPU work)."""
+    world, rank, _ = dist_env()
+    if rank != 0:
+        return
+    import oracle
+    from paper_0804_1448_gb300 import inputs
+    R, Q, k = inputs.workload(WORKLOAD)
+    per_step = 64
+    for i in range(args.warmup):
+        oracle.knn(R, Q[i * per_step:(i + 1) * per_step], k, "l2")
+    t0 = time.perf_counter()
+    off = args.warmup * per_step
+    for i in range(args.steps):
+        lo = (off + i * per_step) % (Q.shape[0] - per_step)
+        oracle.knn(R, Q[lo:lo + per_step], k, "l2")
+    dt = time.perf_counter() - t0
+    v = per_step * args.steps / dt
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "queries/s",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": dt / args.steps * 1e3, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "n": Q.shape[0], "m": R.shape[0], "d": R.shape[1],
+                       "k": k, "distance": "l2", "queries_per_step": per_step},
+            "cpu_baseline": {"value": v, "unit": "queries/s", "cores": oracle.max_threads(),
+                             "kind": "oracle",
+                             "sample": f"{per_step} queries per step x {args.steps} steps"},
+            "e2e": {"value": v, "unit": "queries/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+        return
+    world, rank, local = dist_env()
+    import numpy as np
+    import torch
+    if not torch.cuda.is_available():
+        raise SystemExit("bench.py needs a CUDA GPU (the library has no CPU path)")
+    torch.cuda.set_device(local)
+    pg = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+        pg = dist
+    from paper_0804_1448_gb300 import inputs, knn
+
+    R, Q, k = inputs.workload(WORKLOAD)
+    n, m, d = Q.shape[0], R.shape[0], R.shape[1]
+    dev = torch.device("cuda", local)
+    Rd = torch.from_numpy(R).to(dev)
+    Qd = torch.from_numpy(Q).to(dev)
+    dist_out = torch.empty((n, k), dtype=torch.float32, device=dev)
+    idx_out = torch.empty((n, k), dtype=torch.int32, device=dev)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream(dev)
+
+    def barrier():
+        torch.cuda.synchronize(dev)
+        if pg is not None:
+            pg.barrier()
+        torch.cuda.synchronize(dev)
+
+    def timed_steps(ix, steps, profile_stage=None):
+        """Device time of `steps` searches, each after an L2 flush."""
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+              for _ in range(steps)]
+        stage_ms = []
+        barrier()
+        l0 = ix.stats()["kernel_launches"]
+        for e0, e1 in ev:
+            flush.fill_(1)
+            e0.record(stream)
+            ix.search_into(Qd, k, dist_out, idx_out, "l2", stream)
+            e1.record(stream)
+            if profile_stage:
+                stage_ms.append(ix.profile().get(profile_stage))
+        barrier()
+        launches = ix.stats()["kernel_launches"] - l0
+        return sum(a.elapsed_time(b) for a, b in ev), stage_ms, launches
+
+    # ---- tensor-core form (the headline)
+    ix = knn.Index(local, args.precision)
+    ix.set_reference(Rd)
+    ix.set_profiling(True)
+    for _ in range(max(3, args.warmup)):
+        ix.search_into(Qd, k, dist_out, idx_out, "l2", stream)
+    ix.sync()
+    clocks = Clocks(local)
+    total_ms, filt_ms, launches = timed_steps(ix, args.steps, "tc_filter")
+    clock_info = clocks.stop()
+    prof = ix.profile()
+    ms_step = total_ms / args.steps
+    if pg is not None:
+        t = torch.tensor([ms_step], device=dev)
+        pg.all_reduce(t, op=pg.ReduceOp.MAX)
+        ms_step = float(t.item())
+    value = world * n / (ms_step / 1e3)
+
+    # ---- roofline of the dominant kernel (the tensor-core filter pass)
+    peaks, peak_src = load_peaks()
+    filt = [x for x in filt_ms if x]
+    filt_avg = sum(filt) / len(filt) if filt else None
+    flops = 2.0 * n * m * d    # algorithmic: 2 m d per query
+    achieved = flops / (filt_avg / 1e3) / 1e12 if filt_avg else None
+    peak = peaks.get("bf16_tflops") if args.precision == "bf16" else peaks.get("bf16_tflops") * 1.1 / 2.25
+    roofline = {"bound": "tensor", "kernel": "tc_filter", "achieved": achieved, "peak": peak,
+                "unit": "TFLOP/s", "frac": (achieved / peak) if achieved else None,
+                "traffic": None, "peak_source": f"{peak_src} "
+                + ("bf16_tflops (burst)" if args.precision == "bf16"
+                   else "bf16_tflops x 1.1/2.25 (nominal tf32:bf16 ratio)"),
+                "kernel_ms": filt_avg, "flops_per_launch": flops}
+
+    # ---- float32 CUDA-core form, same workload (the comparator)
+    ix32 = knn.Index(local, "fp32")
+    ix32.set_reference(Rd)
+    for _ in range(3):
+        ix32.search_into(Qd, k, dist_out, idx_out, "l2", stream)
+    ix32.sync()
+    k32 = max(3, args.steps // 6)
+    fp32_ms, _, _ = timed_steps(ix32, k32)
+    fp32_value = world * n / (fp32_ms / k32 / 1e3)
+    ix32.close()
+
+    # ---- end to end through the C ABI with pinned host buffers
+    Qh = torch.from_numpy(Q).pin_memory()
+    dh = torch.empty((n, k), dtype=torch.float32).pin_memory()
+    ih = torch.empty((n, k), dtype=torch.int32).pin_memory()
+    for _ in range(2):
+        ix.search_into(Qh, k, dh, ih, "l2")
+    barrier()
+    t0 = time.perf_counter()
+    e2e_steps = max(3, args.steps // 3)
+    for _ in range(e2e_steps):
+        ix.search_into(Qh, k, dh, ih, "l2")     # synchronous: copies in, search, copies out
+    barrier()
+    e2e_s = (time.perf_counter() - t0) / e2e_steps
+    e2e = {"value": world * n / e2e_s, "unit": "queries/s",
+           "h2d_bytes_per_step": int(n * d * 4), "d2h_bytes_per_step": int(n * k * 8)}
+    stats = ix.stats()
+    ix.close()
+
+    if rank != 0:
+        if pg is not None:
+            pg.destroy_process_group()
+        return
+    line = {"metric": METRIC, "value": value, "unit": "queries/s", "n_gpus": world,
+            "steps": args.steps, "warmup": max(3, args.warmup), "ms_per_step": ms_step,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": args.precision, "data": "synthetic",
+            "config": {"workload": WORKLOAD, "n": n, "m": m, "d": d, "k": k, "distance": "l2",
+                       "precision": args.precision, "rerank_factor": 4,
+                       "l2": "flushed before every step (256 MiB write), outside the timed window",
+                       "step": "one knn_search of all n queries (filter, re-rank, re-check)"},
+            "fp32_value": fp32_value, "speedup_vs_fp32": value / fp32_value,
+            "stage_ms": prof, "roofline": roofline, "e2e": e2e, "gpu_launches": launches,
+            "fallback_queries_total": stats["fallback_queries"], "clocks": clock_info}
+    if not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(R, Q, k, args.cpu_seconds)
+    print(json.dumps(line), flush=True)
+    if pg is not None:
+        pg.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()
