@@ -89,34 +89,158 @@ __device__ __forceinline__ bool near_tie(float a, float b, double rel) {
            2.0 * rel * static_cast<double>(b) + 1e-37;
 }
 
+// Per-warp shared scratch of the finalize kernel.
 struct WarpScratch {
-    uint64_t* keys;  // [P] (float32 distance, index)
-    uint64_t* d64;   // [P] float64 distance bits of re-checked entries
-    int32_t* rs;     // [P] run start of re-checked entries, -1 otherwise
-    int32_t* re;     // [P] run end (inclusive)
-    int32_t* perm;   // [P] output position -> source position inside re-checked runs
-    uint64_t* smax;  // [S] largest original key per split
-    int32_t* hist;   // [kBins] histogram of hit-list keys; hist[kBins] = fill counter
-    float* qrow;     // [d], 16-byte aligned
+    uint64_t* keys;    // [P] candidates (float32 distance, index); kEmptyKey = none / taken
+    uint64_t* sorted;  // [P] ascending prefix, extracted from keys
+    uint64_t* d64;     // [P] float64 distance bits of re-checked prefix entries
+    int32_t* perm;     // [P] output position -> prefix position inside re-checked runs
+    int32_t* runs;     // [P] run start of a re-checked prefix entry, -1 otherwise
+    int32_t* rend;     // [P] run end (inclusive)
+    uint64_t* smax;    // [S] largest select-stage key per split
+    uint64_t* hbuf;    // [kHitBuf] staged hit list (hit-list front end)
+    int32_t* hist;     // [kBins + 4]
+    float* qrow;       // [d + 4], 16-byte aligned
 };
 
 constexpr int kBins = 64;
 
-__host__ __device__ inline size_t warp_scratch_bytes(int P, int S, int d) {
-    const size_t b = static_cast<size_t>(P) * (8 + 8 + 4 + 4 + 4) + static_cast<size_t>((S + 1) & ~1) * 8 +
-                     (kBins + 4) * 4 + (static_cast<size_t>(d) + 4) * 4;
-    return (b + 15) & ~static_cast<size_t>(15);
+constexpr int kHitBuf = 512;   // hit-list entries staged in shared memory per query
+
+__host__ __device__ constexpr size_t align16(size_t x) { return (x + 15) & ~static_cast<size_t>(15); }
+
+// Layout (every array starts 16-byte aligned): keys, sorted, d64 [P] u64;
+// smax [S] u64; hbuf [H] u64; perm, runs, rend [P] i32; hist [kBins+4] i32;
+// qrow [d+4] f32.  H = kHitBuf for the hit-list front end, 0 otherwise.
+__host__ __device__ inline size_t warp_scratch_bytes(int P, int S, int H, int d) {
+    return align16(static_cast<size_t>(P) * 8) * 3 + align16(static_cast<size_t>(S) * 8) +
+           align16(static_cast<size_t>(H) * 8) + align16(static_cast<size_t>(P) * 4) * 3 +
+           align16((kBins + 4) * 4) + align16((static_cast<size_t>(d) + 4) * 4);
 }
 
-// Hit-list front end: keep every listed reference whose low-precision key
-// falls in the histogram bins up to the one holding rank c (so at least the
-// best c), compute their exact float32 distances into w.keys, and return how
-// many there are; -1 sends the query to the exact fallback.
+__device__ __forceinline__ WarpScratch carve(unsigned char* base, int P, int S, int H) {
+    WarpScratch w;
+    size_t o = 0;
+    w.keys = reinterpret_cast<uint64_t*>(base + o);   o += align16(static_cast<size_t>(P) * 8);
+    w.sorted = reinterpret_cast<uint64_t*>(base + o); o += align16(static_cast<size_t>(P) * 8);
+    w.d64 = reinterpret_cast<uint64_t*>(base + o);    o += align16(static_cast<size_t>(P) * 8);
+    w.smax = reinterpret_cast<uint64_t*>(base + o);   o += align16(static_cast<size_t>(S) * 8);
+    w.hbuf = reinterpret_cast<uint64_t*>(base + o);   o += align16(static_cast<size_t>(H) * 8);
+    w.perm = reinterpret_cast<int32_t*>(base + o);    o += align16(static_cast<size_t>(P) * 4);
+    w.runs = reinterpret_cast<int32_t*>(base + o);    o += align16(static_cast<size_t>(P) * 4);
+    w.rend = reinterpret_cast<int32_t*>(base + o);    o += align16(static_cast<size_t>(P) * 4);
+    w.hist = reinterpret_cast<int32_t*>(base + o);    o += align16((kBins + 4) * 4);
+    w.qrow = reinterpret_cast<float*>(base + o);
+    return w;
+}
+
+// Replace raw reference indices keys[0..cnt) (kEmptyKey = none) by exact
+// float32 keys.  With d % 4 == 0 eight lanes share one candidate: each loads
+// every eighth float4 of the row (coalesced 128-byte segments) and sums its
+// part; three shuffles finish the sum.  Otherwise one lane per candidate.
+template <int METRIC>
+__device__ void exact_keys(uint64_t* keys, int cnt, const FinalizeArgs& a, const float* qrow,
+                           int lane) {
+    const int d = a.d;
+    if ((d & 3) == 0) {
+        const int g = lane >> 3, sub = lane & 7, d4 = d >> 2;
+        const float4* q4 = reinterpret_cast<const float4*>(qrow);
+        for (int e0 = 0; e0 < cnt; e0 += 4) {
+            const int e = e0 + g;
+            const uint64_t raw = (e < cnt) ? keys[e] : kEmptyKey;
+            float acc = 0.f;
+            if (raw != kEmptyKey) {
+                const float4* r4 =
+                    reinterpret_cast<const float4*>(a.R + static_cast<int64_t>(raw) * d);
+                for (int t = sub; t < d4; t += 8) {
+                    const float4 x = __ldg(r4 + t);
+                    const float4 y = q4[t];
+                    const float e0f = y.x - x.x, e1 = y.y - x.y, e2 = y.z - x.z, e3 = y.w - x.w;
+                    if (METRIC == kL2) {
+                        acc = fmaf(e0f, e0f, acc); acc = fmaf(e1, e1, acc);
+                        acc = fmaf(e2, e2, acc); acc = fmaf(e3, e3, acc);
+                    } else {
+                        acc += fabsf(e0f); acc += fabsf(e1); acc += fabsf(e2); acc += fabsf(e3);
+                    }
+                }
+            }
+            acc += __shfl_xor_sync(0xffffffffu, acc, 4);
+            acc += __shfl_xor_sync(0xffffffffu, acc, 2);
+            acc += __shfl_xor_sync(0xffffffffu, acc, 1);
+            if (sub == 0 && raw != kEmptyKey) keys[e] = make_key(acc, static_cast<uint32_t>(raw));
+        }
+    } else {
+        for (int e = lane; e < cnt; e += 32) {
+            const uint64_t raw = keys[e];
+            if (raw != kEmptyKey)
+                keys[e] = make_key(dist_f32<METRIC>(qrow, a.R + static_cast<int64_t>(raw) * d, d),
+                                   static_cast<uint32_t>(raw));
+        }
+    }
+    __syncwarp();
+}
+
+// Candidate-set front end: exact float32 keys of the S*c entries of query q,
+// and the largest select-stage key of every split.
+template <int METRIC>
+__device__ void gather_cand(const FinalizeArgs& a, int64_t q, WarpScratch& w, int lane) {
+    const CandidateSet& cs = a.cand;
+    const int Sc = cs.S * cs.c, d = a.d;
+    const uint64_t* src = cs.keys + q * static_cast<int64_t>(Sc);
+    for (int e = lane; e < Sc; e += 32) {
+        const uint64_t key = src[e];
+        uint64_t raw = kEmptyKey;
+        if (key != kEmptyKey) {
+            raw = key_idx(key);
+            atomicMax(reinterpret_cast<unsigned long long*>(&w.smax[e / cs.c]),
+                      static_cast<unsigned long long>(key));
+        }
+        w.keys[e] = raw;
+    }
+    __syncwarp();
+    exact_keys<METRIC>(w.keys, Sc, a, w.qrow, lane);
+    (void)d;
+}
+
+// Histogram over [lo, lo + kBins/inv) of the entries of the hit lists that
+// satisfy keep1 (first level: all; second level: those in bin b1 of level 1).
+struct Binning {
+    float lo, inv;
+    __device__ int bin(float v) const {
+        const float x = (v - lo) * inv;
+        return x <= 0.f ? 0 : (x >= kBins - 1 ? kBins - 1 : static_cast<int>(x));
+    }
+};
+
+// Smallest bin whose cumulative count reaches `need` (counts summed with `base`),
+// and the cumulative count before it.  Two bins per lane.
+__device__ void cut_bin(const int32_t* hist, int need, int lane, int* bin, int* before) {
+    const int h0 = hist[2 * lane], h1 = hist[2 * lane + 1];
+    int incl = h0 + h1;
+    for (int o = 1; o < 32; o <<= 1) {
+        const int v = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += v;
+    }
+    const int excl = incl - h0 - h1;
+    int mine = kBins, mb = 0;
+    if (excl + h0 >= need) { mine = 2 * lane; mb = excl; }
+    else if (incl >= need) { mine = 2 * lane + 1; mb = excl + h0; }
+    int best = mine;
+    for (int o = 16; o > 0; o >>= 1) best = min(best, __shfl_xor_sync(0xffffffffu, best, o));
+    const unsigned own = __ballot_sync(0xffffffffu, mine == best && best < kBins);
+    *bin = best;
+    *before = own ? __shfl_sync(0xffffffffu, mb, __ffs(own) - 1) : 0;
+}
+
+// Hit-list front end: keep the listed references whose low-precision key is
+// among the best c, cutting at a histogram bin (refined once), so at least c
+// and usually a few more are kept; their exact float32 keys go to w.keys.
+// Returns the number kept, or -1 (list shorter than c), -2 (overflowed),
+// -3 (the cut kept more than P) to send the query to the exact fallback.
 template <int METRIC>
 __device__ int gather_hits(const FinalizeArgs& a, int64_t q, int P, WarpScratch& w, int lane) {
     const HitLists& hl = a.hits;
-    const int S = hl.S, cap = hl.cap;
-    const int d = a.d;
+    const int S = hl.S, cap = hl.cap, c = hl.c, d = a.d;
     const uint64_t* base = hl.keys + q * static_cast<int64_t>(S) * cap;
     const int32_t* cnts = hl.counts + q * static_cast<int64_t>(S);
     int total = 0, over = 0;
@@ -130,73 +254,125 @@ __device__ int gather_hits(const FinalizeArgs& a, int64_t q, int P, WarpScratch&
         over |= __shfl_xor_sync(0xffffffffu, over, o);
     }
     if (over) return -2;
-    if (total < hl.c && total < a.m) return -1;
-    // range of the order-mapped scores
-    uint32_t omin = 0xffffffffu, omax = 0;
-    for (int s = 0; s < S; ++s) {
-        const int cs = min(cnts[s], cap);
-        for (int e = lane; e < cs; e += 32) {
-            const uint32_t o = static_cast<uint32_t>(base[static_cast<int64_t>(s) * cap + e] >> 32);
-            omin = min(omin, o);
-            omax = max(omax, o);
-        }
-    }
-    for (int o = 16; o > 0; o >>= 1) {
-        omin = min(omin, __shfl_xor_sync(0xffffffffu, omin, o));
-        omax = max(omax, __shfl_xor_sync(0xffffffffu, omax, o));
-    }
-    const uint64_t span = static_cast<uint64_t>(omax) - omin + 1;
-    int cut = kBins - 1;            // keep bins 0..cut
-    if (total > hl.c) {
-        for (int b = lane; b < kBins + 4; b += 32) w.hist[b] = 0;
-        __syncwarp();
+    if (total < c && total < a.m) return -1;
+    // stage the lists in shared memory when they fit: the passes below read them three times
+    const uint64_t* src = base;
+    int64_t sstride = cap;
+    if (total <= kHitBuf) {
+        int o = 0;
         for (int s = 0; s < S; ++s) {
             const int cs = min(cnts[s], cap);
-            for (int e = lane; e < cs; e += 32) {
-                const uint32_t o = static_cast<uint32_t>(base[static_cast<int64_t>(s) * cap + e] >> 32);
-                atomicAdd(&w.hist[static_cast<int>((static_cast<uint64_t>(o - omin) * kBins) / span)], 1);
-            }
+            for (int e = lane; e < cs; e += 32) w.hbuf[o + e] = base[static_cast<int64_t>(s) * cap + e];
+            o += cs;
         }
         __syncwarp();
-        // smallest bin whose cumulative count reaches c (two bins per lane)
-        const int h0 = w.hist[2 * lane], h1 = w.hist[2 * lane + 1];
-        int incl = h0 + h1;
-        for (int o = 1; o < 32; o <<= 1) {
-            const int v = __shfl_up_sync(0xffffffffu, incl, o);
-            if (lane >= o) incl += v;
-        }
-        const int excl = incl - h0 - h1;
-        int mine = kBins;
-        if (excl + h0 >= hl.c) mine = 2 * lane;
-        else if (incl >= hl.c) mine = 2 * lane + 1;
-        for (int o = 16; o > 0; o >>= 1) mine = min(mine, __shfl_xor_sync(0xffffffffu, mine, o));
-        cut = mine;
+        src = w.hbuf;
+        sstride = 0;
     }
-    // keep, re-rank in float32
-    if (lane == 0) w.hist[kBins] = 0;
-    __syncwarp();
-    int kept = 0;
-    for (int s = 0; s < S; ++s) {
+    // entry e of split s lives at src[s * sstride + off(s) + e] with off = running
+    // count when staged (sstride 0), 0 otherwise
+
+    // level-1 range of the ranking values
+    float vmin = __int_as_float(0x7f800000), vmax = -vmin;
+    for (int s = 0, o = 0; s < S; ++s) {
         const int cs = min(cnts[s], cap);
+        const uint64_t* sp = src + (sstride ? static_cast<int64_t>(s) * sstride : o);
+        for (int e = lane; e < cs; e += 32) {
+            const float v = key_dist(sp[e]);
+            vmin = fminf(vmin, v);
+            vmax = fmaxf(vmax, v);
+        }
+        o += cs;
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        vmin = fminf(vmin, __shfl_xor_sync(0xffffffffu, vmin, o));
+        vmax = fmaxf(vmax, __shfl_xor_sync(0xffffffffu, vmax, o));
+    }
+    Binning b1{vmin, vmax > vmin ? kBins / (vmax - vmin) : 0.f};
+    int cut1 = kBins - 1, cut2 = kBins - 1;
+    Binning b2{0.f, 0.f};
+    if (total > c) {
+        for (int b = lane; b < kBins; b += 32) w.hist[b] = 0;
+        __syncwarp();
+        for (int s = 0, o = 0; s < S; ++s) {
+            const int cs = min(cnts[s], cap);
+            const uint64_t* sp = src + (sstride ? static_cast<int64_t>(s) * sstride : o);
+            for (int e = lane; e < cs; e += 32) atomicAdd(&w.hist[b1.bin(key_dist(sp[e]))], 1);
+            o += cs;
+        }
+        __syncwarp();
+        int before;
+        cut_bin(w.hist, c, lane, &cut1, &before);
+        const int in_bin = w.hist[cut1];
+        __syncwarp();
+        if (before + in_bin > P && b1.inv > 0.f) {
+            // refine the cut bin once
+            b2.lo = vmin + cut1 / b1.inv;
+            b2.inv = b1.inv * kBins;
+            for (int b = lane; b < kBins; b += 32) w.hist[b] = 0;
+            __syncwarp();
+            for (int s = 0, o = 0; s < S; ++s) {
+                const int cs = min(cnts[s], cap);
+                const uint64_t* sp = src + (sstride ? static_cast<int64_t>(s) * sstride : o);
+                for (int e = lane; e < cs; e += 32) {
+                    const float v = key_dist(sp[e]);
+                    if (b1.bin(v) == cut1) atomicAdd(&w.hist[b2.bin(v)], 1);
+                }
+                o += cs;
+            }
+            __syncwarp();
+            int before2;
+            cut_bin(w.hist, c - before, lane, &cut2, &before2);
+            __syncwarp();
+        }
+    }
+    // compact the kept indices, then compute their exact keys with all lanes busy
+    int kept = 0;
+    for (int s = 0, o = 0; s < S; ++s) {
+        const int cs = min(cnts[s], cap);
+        const uint64_t* sp = src + (sstride ? static_cast<int64_t>(s) * sstride : o);
+        o += cs;
         for (int e0 = 0; e0 < cs; e0 += 32) {
             const int e = e0 + lane;
             bool take = false;
             uint32_t j = 0;
             if (e < cs) {
-                const uint64_t key = base[static_cast<int64_t>(s) * cap + e];
-                const uint32_t o = static_cast<uint32_t>(key >> 32);
-                take = static_cast<int>((static_cast<uint64_t>(o - omin) * kBins) / span) <= cut;
+                const uint64_t key = sp[e];
+                const float v = key_dist(key);
+                const int bb = b1.bin(v);
+                take = bb < cut1 || (bb == cut1 && (b2.inv == 0.f || b2.bin(v) <= cut2));
                 j = key_idx(key);
             }
             const unsigned bal = __ballot_sync(0xffffffffu, take);
             const int pos = kept + __popc(bal & ((1u << lane) - 1u));
-            if (take && pos < P)
-                w.keys[pos] = make_key(dist_f32<METRIC>(w.qrow, a.R + static_cast<int64_t>(j) * d, d), j);
+            if (take && pos < P) w.keys[pos] = j;
             kept += __popc(bal);
         }
     }
     __syncwarp();
-    return kept <= P ? kept : -3;
+    if (kept > P) return -3;
+    exact_keys<METRIC>(w.keys, kept, a, w.qrow, lane);
+    (void)d;
+    return kept;
+}
+
+__device__ __forceinline__ void local_min(const uint64_t* keys, int pool, int lane, uint64_t* lmin,
+                                          int* lpos) {
+    uint64_t best = kEmptyKey;
+    int at = -1;
+    for (int e = lane; e < pool; e += 32) {
+        const uint64_t v = keys[e];
+        if (v < best) { best = v; at = e; }
+    }
+    *lmin = best;
+    *lpos = at;
+}
+
+__device__ __forceinline__ void queue_fallback(const FinalizeArgs& a, int64_t q, int reason) {
+    const int pos = atomicAdd(a.fallback_count, 1);
+    a.fallback_list[pos] = static_cast<int32_t>(q);
+    if (a.fallback_total) atomicAdd(a.fallback_total, 1ull);
+    if (a.fallback_reason) atomicAdd(&a.fallback_reason[reason], 1ull);
 }
 
 template <int METRIC>
@@ -206,134 +382,114 @@ __global__ void finalize_kernel(FinalizeArgs a, int P, int warps_per_block) {
     const int64_t q = static_cast<int64_t>(blockIdx.x) * warps_per_block + warp;
     if (q >= a.n) return;   // warp-uniform: no block-level sync below
 
-    const CandidateSet& cs = a.cand;
-    const int S = a.use_hits ? 1 : cs.S, c = cs.c, Sc = a.use_hits ? 0 : S * c;
-    const int d = a.d;
-    const size_t per_warp = warp_scratch_bytes(P, S, d);
-    unsigned char* base = smem_raw + per_warp * warp;
-    WarpScratch w;
-    w.keys = reinterpret_cast<uint64_t*>(base);
-    w.d64 = w.keys + P;
-    w.smax = w.d64 + P;
-    w.rs = reinterpret_cast<int32_t*>(w.smax + ((S + 1) & ~1));
-    w.re = w.rs + P;
-    w.perm = w.re + P;
-    w.hist = w.perm + P;
-    w.qrow = reinterpret_cast<float*>(w.hist + kBins + 4);
-
+    const int S = a.use_hits ? 1 : a.cand.S;
+    const int d = a.d, k = a.k;
+    const int H = a.use_hits ? kHitBuf : 0;
+    WarpScratch w = carve(smem_raw + warp_scratch_bytes(P, S, H, d) * warp, P, S, H);
     for (int t = lane; t < d; t += 32) w.qrow[t] = a.Q[q * d + t];
     for (int s = lane; s < S; s += 32) w.smax[s] = 0;
-    for (int e = lane; e < P; e += 32) { w.keys[e] = kEmptyKey; w.rs[e] = -1; }
     __syncwarp();
 
-    // 1. exact float32 distances of the candidates
-    int cnt = 0;
+    // 1. candidates with exact float32 keys
+    int pool;
     if (!a.use_hits) {
-        const uint64_t* src = cs.keys + q * static_cast<int64_t>(Sc);
-        for (int e0 = 0; e0 < Sc; e0 += 32) {
-            const int e = e0 + lane;
-            uint64_t nk = kEmptyKey;
-            if (e < Sc) {
-                const uint64_t key = src[e];
-                if (key != kEmptyKey) {
-                    const uint32_t j = key_idx(key);
-                    nk = make_key(dist_f32<METRIC>(w.qrow, a.R + static_cast<int64_t>(j) * d, d), j);
-                    atomicMax(reinterpret_cast<unsigned long long*>(&w.smax[e / c]),
-                              static_cast<unsigned long long>(key));
-                }
-                w.keys[e] = nk;
-            }
-            cnt += __popc(__ballot_sync(0xffffffffu, nk != kEmptyKey));
-        }
+        pool = a.cand.S * a.cand.c;
+        gather_cand<METRIC>(a, q, w, lane);
     } else {
-        cnt = gather_hits<METRIC>(a, q, P, w, lane);
-        if (cnt < 0) {   // -1 short list, -2 overflow, -3 the cut kept too many
-            if (lane == 0) {
-                const int pos = atomicAdd(a.fallback_count, 1);
-                a.fallback_list[pos] = static_cast<int32_t>(q);
-                if (a.fallback_total) atomicAdd(a.fallback_total, 1ull);
-                if (a.fallback_reason) atomicAdd(&a.fallback_reason[-cnt - 1], 1ull);
-            }
+        pool = gather_hits<METRIC>(a, q, P, w, lane);
+        if (pool < 0) {
+            if (lane == 0) queue_fallback(a, q, -pool - 1);
             return;
         }
     }
     __syncwarp();
 
-    // 2. bitonic sort by (distance, index)
-    for (int size = 2; size <= P; size <<= 1) {
-        for (int stride = size >> 1; stride > 0; stride >>= 1) {
-            for (int i = lane; i < P; i += 32) {
-                const int j = i ^ stride;
-                if (j > i) {
-                    const uint64_t x = w.keys[i], y = w.keys[j];
-                    const bool up = (i & size) == 0;
-                    if ((x > y) == up) { w.keys[i] = y; w.keys[j] = x; }
-                }
-            }
-            __syncwarp();
-        }
-    }
-
-    const int k = a.k;
-    const int kk = min(k, cnt);
+    // 2. ascending prefix by repeated minimum: the first k, continued through
+    //    the near-tie run holding position k-1
     const double rel = f32_rel_bound(d);
+    uint64_t lmin;
+    int lpos;
+    local_min(w.keys, pool, lane, &lmin, &lpos);
+    int L = 0;
+    uint64_t prev = 0;
+    while (L < P) {
+        const uint32_t hi = static_cast<uint32_t>(lmin >> 32);
+        const uint32_t mhi = __reduce_min_sync(0xffffffffu, hi);
+        const uint32_t lo = (hi == mhi) ? static_cast<uint32_t>(lmin) : 0xffffffffu;
+        const uint32_t mlo = __reduce_min_sync(0xffffffffu, lo);
+        const uint64_t win = (static_cast<uint64_t>(mhi) << 32) | mlo;
+        if (win == kEmptyKey) break;
+        if (L >= k && !near_tie(key_dist(prev), key_dist(win), rel)) break;
+        if (lane == 0) w.sorted[L] = win;
+        if (lmin == win) {                 // owner: take it, rescan
+            w.keys[lpos] = kEmptyKey;
+            local_min(w.keys, pool, lane, &lmin, &lpos);
+        }
+        prev = win;
+        ++L;
+    }
+    __syncwarp();
+    const int kk = min(k, L);
 
-    // 3a. find the near-tie runs that reach the first kk positions (lane 0)
-    int scan_end = 0;
-    if (lane == 0 && kk > 0) {
-        int p = 0;
-        while (p < kk) {
-            int e = p;
-            while (e + 1 < cnt && near_tie(key_dist(w.keys[e]), key_dist(w.keys[e + 1]), rel)) ++e;
-            if (e > p) {
-                for (int x = p; x <= e; ++x) { w.rs[x] = p; w.re[x] = e; }
+    // 3. float64 re-check of near-tie runs inside the prefix
+    bool any_tie = false;
+    for (int p = 1 + lane; p < L; p += 32)
+        any_tie |= near_tie(key_dist(w.sorted[p - 1]), key_dist(w.sorted[p]), rel);
+    any_tie = __any_sync(0xffffffffu, any_tie);
+    for (int p = lane; p < L; p += 32) w.runs[p] = -1;
+    __syncwarp();
+    if (any_tie) {
+        if (lane == 0) {
+            int p = 0;
+            while (p < L) {
+                int e = p;
+                while (e + 1 < L && near_tie(key_dist(w.sorted[e]), key_dist(w.sorted[e + 1]), rel)) ++e;
+                if (e > p)
+                    for (int x = p; x <= e; ++x) { w.runs[x] = p; w.rend[x] = e; }
+                p = e + 1;
             }
-            p = e + 1;
         }
-        scan_end = p;   // one past the last position of the run holding kk-1
-    }
-    scan_end = __shfl_sync(0xffffffffu, scan_end, 0);
-    __syncwarp();
-
-    // 3b. float64 distances of re-checked entries, then their rank in the run
-    int nre = 0;
-    for (int p = lane; p < scan_end; p += 32) {
-        if (w.rs[p] >= 0) {
-            const uint32_t j = key_idx(w.keys[p]);
-            w.d64[p] = dbits(dist_f64<METRIC>(w.qrow, a.R + static_cast<int64_t>(j) * d, d));
-            ++nre;
-        }
-    }
-    __syncwarp();
-    for (int p = lane; p < scan_end; p += 32) {
-        const int s0 = w.rs[p];
-        if (s0 >= 0) {
-            const uint64_t mine = w.d64[p];
-            const uint32_t mj = key_idx(w.keys[p]);
-            int rank = 0;
-            for (int x = s0; x <= w.re[p]; ++x) {
-                const uint64_t o = w.d64[x];
-                const uint32_t oj = key_idx(w.keys[x]);
-                rank += (o < mine || (o == mine && oj < mj)) ? 1 : 0;
+        __syncwarp();
+        int nre = 0;
+        for (int p = lane; p < L; p += 32) {
+            if (w.runs[p] >= 0) {
+                const uint32_t j = key_idx(w.sorted[p]);
+                w.d64[p] = dbits(dist_f64<METRIC>(w.qrow, a.R + static_cast<int64_t>(j) * d, d));
+                ++nre;
             }
-            w.perm[s0 + rank] = p;
         }
+        __syncwarp();
+        for (int p = lane; p < L; p += 32) {
+            const int s0 = w.runs[p];
+            if (s0 >= 0) {
+                const uint64_t mine = w.d64[p];
+                const uint32_t mj = key_idx(w.sorted[p]);
+                int rank = 0;
+                for (int x = s0; x <= w.rend[p]; ++x) {
+                    const uint64_t o = w.d64[x];
+                    const uint32_t oj = key_idx(w.sorted[x]);
+                    rank += (o < mine || (o == mine && oj < mj)) ? 1 : 0;
+                }
+                w.perm[s0 + rank] = p;
+            }
+        }
+        __syncwarp();
+        for (int o = 16; o > 0; o >>= 1) nre += __shfl_xor_sync(0xffffffffu, nre, o);
+        if (lane == 0 && nre > 0 && a.recheck_counter)
+            atomicAdd(a.recheck_counter, static_cast<unsigned long long>(nre));
     }
-    __syncwarp();
-    for (int o = 16; o > 0; o >>= 1) nre += __shfl_xor_sync(0xffffffffu, nre, o);
-    if (lane == 0 && nre > 0 && a.recheck_counter)
-        atomicAdd(a.recheck_counter, static_cast<unsigned long long>(nre));
+    auto source_of = [&](int s) { return (w.runs[s] >= 0) ? w.perm[s] : s; };
 
-    auto source_of = [&](int s) { return (w.rs[s] >= 0) ? w.perm[s] : s; };
-
-    // 4. completeness of a float32 candidate set
-    if (!a.use_hits && cs.exact && kk > 0) {
+    // 4. completeness of a float32 candidate set: the references left out by a
+    //    split have keys >= that split's largest kept key
+    if (!a.use_hits && a.cand.exact && kk > 0) {
+        const CandidateSet& cs = a.cand;
         bool have = false;
         double lower = 0.0;
         for (int s = 0; s < S; ++s) {
             const int64_t b = static_cast<int64_t>(s) * cs.chunk;
             const int64_t e = min(a.m, b + cs.chunk);
-            if (e - b > c) {   // this split left references out
+            if (e - b > cs.c) {
                 const double v = static_cast<double>(key_dist(w.smax[s])) * (1.0 - rel);
                 lower = have ? fmin(lower, v) : v;
                 have = true;
@@ -341,16 +497,11 @@ __global__ void finalize_kernel(FinalizeArgs a, int P, int warps_per_block) {
         }
         if (have) {
             const int sk = source_of(kk - 1);
-            const double upper = (w.rs[kk - 1] >= 0)
+            const double upper = (w.runs[kk - 1] >= 0)
                                      ? bitsd(w.d64[sk])
-                                     : static_cast<double>(key_dist(w.keys[sk])) * (1.0 + rel);
+                                     : static_cast<double>(key_dist(w.sorted[sk])) * (1.0 + rel);
             if (!(lower > upper) || kk < k) {
-                if (lane == 0) {
-                    const int pos = atomicAdd(a.fallback_count, 1);
-                    a.fallback_list[pos] = static_cast<int32_t>(q);
-                    if (a.fallback_total) atomicAdd(a.fallback_total, 1ull);
-                    if (a.fallback_reason) atomicAdd(&a.fallback_reason[3], 1ull);
-                }
+                if (lane == 0) queue_fallback(a, q, 3);
                 return;
             }
         }
@@ -362,12 +513,12 @@ __global__ void finalize_kernel(FinalizeArgs a, int P, int warps_per_block) {
         int32_t idx = -1;
         if (s < kk) {
             const int sp = source_of(s);
-            idx = static_cast<int32_t>(key_idx(w.keys[sp]));
-            if (w.rs[s] >= 0) {
+            idx = static_cast<int32_t>(key_idx(w.sorted[sp]));
+            if (w.runs[s] >= 0) {
                 const double v = bitsd(w.d64[sp]);
                 dist = (METRIC == kL2) ? static_cast<float>(__dsqrt_rn(v)) : static_cast<float>(v);
             } else {
-                const float v = key_dist(w.keys[sp]);
+                const float v = key_dist(w.sorted[sp]);
                 dist = (METRIC == kL2) ? sqrtf(v) : v;
             }
         }
@@ -377,24 +528,65 @@ __global__ void finalize_kernel(FinalizeArgs a, int P, int warps_per_block) {
 }
 
 // ---------------------------------------------------------------------------
-// exact float64 fallback
+// exact fallback: float32 distances to every reference, the k-th smallest by
+// radix selection, then float64 distances for every reference whose float32
+// distance could still place it in the answer (float32 <= kth * (1+e)/(1-e)),
+// an exact radix selection on those, a sort, and the outputs.
 // ---------------------------------------------------------------------------
 constexpr int kFbThreads = 256;
 constexpr int kFbMaxK = 1024;
+constexpr uint64_t kInfBits = 0x7ff0000000000000ull;
+
+struct FbShared {
+    int hist[256];
+    uint64_t ck[kFbMaxK];
+    uint32_t ci[kFbMaxK];
+    int digit, rank, less, taken, wsum[kFbThreads / 32];
+};
+
+// k-th smallest of the non-negative doubles keys[0..m) (bit pattern order),
+// returned as bits; *ties = how many entries equal to it belong to the k.
+__device__ uint64_t radix_select(const double* keys, int64_t m, int k, FbShared& sh, int* ties) {
+    const int tid = threadIdx.x;
+    uint64_t prefix = 0, mask = 0;
+    int rank = k;
+    for (int shift = 56; shift >= 0; shift -= 8) {
+        for (int b = tid; b < 256; b += kFbThreads) sh.hist[b] = 0;
+        __syncthreads();
+        for (int64_t j = tid; j < m; j += kFbThreads) {
+            const uint64_t u = dbits(keys[j]);
+            if ((u & mask) == prefix) atomicAdd(&sh.hist[(u >> shift) & 0xff], 1);
+        }
+        __syncthreads();
+        if (tid == 0) {
+            int cum = 0, b = 0;
+            for (; b < 255; ++b) {
+                if (cum + sh.hist[b] >= rank) break;
+                cum += sh.hist[b];
+            }
+            sh.digit = b;
+            sh.rank = rank - cum;
+        }
+        __syncthreads();
+        prefix |= static_cast<uint64_t>(sh.digit) << shift;
+        mask |= 0xffull << shift;
+        rank = sh.rank;
+        __syncthreads();
+    }
+    *ties = rank;
+    return prefix;
+}
 
 template <int METRIC>
 __global__ void __launch_bounds__(kFbThreads)
 fallback_kernel(FinalizeArgs a, double* __restrict__ scratch) {
-    __shared__ int hist[256];
-    __shared__ uint64_t ck[kFbMaxK];
-    __shared__ uint32_t ci[kFbMaxK];
-    __shared__ int s_digit, s_rank, s_less, s_taken, s_wsum[kFbThreads / 32];
-    extern __shared__ float qrow[];
-
+    __shared__ FbShared sh;
+    extern __shared__ __align__(16) float qrow[];
     const int tid = threadIdx.x;
     const int count = *a.fallback_count;
     const int64_t m = a.m;
     const int d = a.d, k = a.k;
+    const double rel = f32_rel_bound(d);
     double* keys = scratch + static_cast<int64_t>(blockIdx.x) * m;
 
     for (int f = blockIdx.x; f < count; f += gridDim.x) {
@@ -402,89 +594,68 @@ fallback_kernel(FinalizeArgs a, double* __restrict__ scratch) {
         __syncthreads();
         for (int t = tid; t < d; t += kFbThreads) qrow[t] = a.Q[q * d + t];
         __syncthreads();
+        // float32 pass and its k-th smallest
         for (int64_t j = tid; j < m; j += kFbThreads)
-            keys[j] = dist_f64<METRIC>(qrow, a.R + j * d, d);
+            keys[j] = static_cast<double>(dist_f32<METRIC>(qrow, a.R + j * d, d));
         __syncthreads();
-
-        // radix selection of the k-th smallest key (non-negative doubles:
-        // the bit pattern orders like the value)
-        uint64_t prefix = 0, mask = 0;
-        int rank = k;
-        for (int shift = 56; shift >= 0; shift -= 8) {
-            for (int b = tid; b < 256; b += kFbThreads) hist[b] = 0;
-            __syncthreads();
-            for (int64_t j = tid; j < m; j += kFbThreads) {
-                const uint64_t u = dbits(keys[j]);
-                if ((u & mask) == prefix) atomicAdd(&hist[(u >> shift) & 0xff], 1);
-            }
-            __syncthreads();
-            if (tid == 0) {
-                int cum = 0, b = 0;
-                for (; b < 256; ++b) {
-                    if (cum + hist[b] >= rank) break;
-                    cum += hist[b];
-                }
-                s_digit = b;
-                s_rank = rank - cum;
-            }
-            __syncthreads();
-            prefix |= static_cast<uint64_t>(s_digit) << shift;
-            mask |= 0xffull << shift;
-            rank = s_rank;
-            __syncthreads();
-        }
-        const uint64_t T = prefix;   // bits of the k-th smallest distance
-        const int n_less = k - rank; // entries strictly below T; then `rank` ties at T
-        if (tid == 0) { s_less = 0; s_taken = 0; }
+        int ties;
+        const double kth32 = bitsd(radix_select(keys, m, k, sh, &ties));
+        const double bound = kth32 * (1.0 + rel) / (1.0 - rel) * (1.0 + 1e-12) + 1e-37;
+        // float64 for every reference that could still be in the answer
+        for (int64_t j = tid; j < m; j += kFbThreads)
+            keys[j] = (keys[j] <= bound) ? dist_f64<METRIC>(qrow, a.R + j * d, d) : bitsd(kInfBits);
+        __syncthreads();
+        const uint64_t T = radix_select(keys, m, k, sh, &ties);
+        const int n_less = k - ties;   // strictly below T; then `ties` entries equal to T
+        if (tid == 0) { sh.less = 0; sh.taken = 0; }
         __syncthreads();
         for (int64_t j = tid; j < m; j += kFbThreads) {
             const uint64_t u = dbits(keys[j]);
             if (u < T) {
-                const int slot = atomicAdd(&s_less, 1);
-                ck[slot] = u;
-                ci[slot] = static_cast<uint32_t>(j);
+                const int slot = atomicAdd(&sh.less, 1);
+                sh.ck[slot] = u;
+                sh.ci[slot] = static_cast<uint32_t>(j);
             }
         }
         __syncthreads();
-        // the `rank` ties at T with the smallest indices, in index order
-        for (int64_t base = 0; base < m; base += kFbThreads) {
-            const int64_t j = base + tid;
+        // the `ties` entries equal to T with the smallest indices, in index order
+        const int lane = tid % 32, wid = tid / 32;
+        for (int64_t b0 = 0; b0 < m; b0 += kFbThreads) {
+            const int64_t j = b0 + tid;
             const bool eq = (j < m) && dbits(keys[j]) == T;
             const unsigned bal = __ballot_sync(0xffffffffu, eq);
-            const int lane = tid % 32, wid = tid / 32;
-            if (lane == 0) s_wsum[wid] = __popc(bal);
+            if (lane == 0) sh.wsum[wid] = __popc(bal);
             __syncthreads();
-            int before = s_taken;
-            for (int x = 0; x < wid; ++x) before += s_wsum[x];
+            int before = sh.taken;
+            for (int x = 0; x < wid; ++x) before += sh.wsum[x];
             before += __popc(bal & ((1u << lane) - 1u));
-            if (eq && before < rank) {
-                ck[n_less + before] = T;
-                ci[n_less + before] = static_cast<uint32_t>(j);
+            if (eq && before < ties) {
+                sh.ck[n_less + before] = T;
+                sh.ci[n_less + before] = static_cast<uint32_t>(j);
             }
             __syncthreads();
             if (tid == 0) {
                 int tot = 0;
-                for (int x = 0; x < kFbThreads / 32; ++x) tot += s_wsum[x];
-                s_taken += tot;
+                for (int x = 0; x < kFbThreads / 32; ++x) tot += sh.wsum[x];
+                sh.taken += tot;
             }
             __syncthreads();
-            if (s_taken >= rank) break;
+            if (sh.taken >= ties) break;
         }
-        // sort the k selected pairs by (distance, index)
+        // sort the k pairs by (distance, index)
         int P2 = 1;
         while (P2 < k) P2 <<= 1;
-        for (int i = k + tid; i < P2; i += kFbThreads) { ck[i] = ~0ull; ci[i] = 0xffffffffu; }
+        for (int i = k + tid; i < P2; i += kFbThreads) { sh.ck[i] = ~0ull; sh.ci[i] = 0xffffffffu; }
         __syncthreads();
         for (int size = 2; size <= P2; size <<= 1) {
             for (int stride = size >> 1; stride > 0; stride >>= 1) {
                 for (int i = tid; i < P2; i += kFbThreads) {
                     const int j = i ^ stride;
                     if (j > i) {
-                        const bool gt = ck[i] > ck[j] || (ck[i] == ck[j] && ci[i] > ci[j]);
-                        const bool up = (i & size) == 0;
-                        if (gt == up) {
-                            const uint64_t tk = ck[i]; ck[i] = ck[j]; ck[j] = tk;
-                            const uint32_t tj = ci[i]; ci[i] = ci[j]; ci[j] = tj;
+                        const bool gt = sh.ck[i] > sh.ck[j] || (sh.ck[i] == sh.ck[j] && sh.ci[i] > sh.ci[j]);
+                        if (gt == ((i & size) == 0)) {
+                            const uint64_t tk = sh.ck[i]; sh.ck[i] = sh.ck[j]; sh.ck[j] = tk;
+                            const uint32_t tj = sh.ci[i]; sh.ci[i] = sh.ci[j]; sh.ci[j] = tj;
                         }
                     }
                 }
@@ -492,10 +663,10 @@ fallback_kernel(FinalizeArgs a, double* __restrict__ scratch) {
             }
         }
         for (int s = tid; s < k; s += kFbThreads) {
-            const double v = bitsd(ck[s]);
+            const double v = bitsd(sh.ck[s]);
             a.dist_out[q * k + s] =
                 (METRIC == kL2) ? static_cast<float>(__dsqrt_rn(v)) : static_cast<float>(v);
-            a.idx_out[q * k + s] = static_cast<int32_t>(ci[s]);
+            a.idx_out[q * k + s] = static_cast<int32_t>(sh.ci[s]);
         }
     }
 }
@@ -505,12 +676,12 @@ fallback_kernel(FinalizeArgs a, double* __restrict__ scratch) {
 int finalize_max_pool() { return kMaxPool; }
 
 cudaError_t launch_finalize(const FinalizeArgs& a, cudaStream_t st, int* launches) {
-    const int want = a.use_hits ? 2 * a.hits.c + 32 : a.cand.S * a.cand.c;
-    int P = 32;
-    while (P < want) P <<= 1;
+    int P = a.use_hits ? 2 * a.hits.c + 32 : a.cand.S * a.cand.c;
+    P = (P + 3) & ~3;
     if (P > kMaxPool) return cudaErrorInvalidValue;
-    const size_t per_warp = warp_scratch_bytes(P, a.use_hits ? 1 : a.cand.S, a.d);
-    int wpb = static_cast<int>((48 * 1024) / per_warp);
+    const size_t per_warp =
+        warp_scratch_bytes(P, a.use_hits ? 1 : a.cand.S, a.use_hits ? kHitBuf : 0, a.d);
+    int wpb = static_cast<int>((96 * 1024) / per_warp);
     wpb = wpb < 1 ? 1 : (wpb > 8 ? 8 : wpb);
     const size_t smem = per_warp * wpb;
     if (smem > 200 * 1024) return cudaErrorInvalidValue;
@@ -535,7 +706,7 @@ cudaError_t launch_finalize(const FinalizeArgs& a, cudaStream_t st, int* launche
 cudaError_t launch_fallback(const FinalizeArgs& a, double* scratch, int32_t grid,
                             cudaStream_t st, int* launches) {
     if (a.k > kFbMaxK) return cudaErrorInvalidValue;
-    const size_t smem = static_cast<size_t>(a.d) * sizeof(float);
+    const size_t smem = (static_cast<size_t>(a.d) + 4) * sizeof(float);
     if (launches) ++*launches;
     if (a.metric == kL2)
         fallback_kernel<kL2><<<grid, kFbThreads, smem, st>>>(a, scratch);
