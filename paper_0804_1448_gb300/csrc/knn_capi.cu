@@ -294,7 +294,7 @@ knn_status knn_search(knn_handle h, const float* Q, int64_t n, int32_t d, int32_
     int64_t chunk = m;
     TcPlan plan{};
     if (tensor) {
-        plan = tc_plan(n, m, h->kp, prec, c, h->num_sms);
+        plan = tc_plan(n, m, d, h->kp, prec, c, h->num_sms);
         if (plan.stages == 0) return KNN_ERR_UNSUPPORTED;
         S = plan.S;
         chunk = plan.chunk;

@@ -98,34 +98,29 @@ struct WarpScratch {
     int32_t* runs;     // [P] run start of a re-checked prefix entry, -1 otherwise
     int32_t* rend;     // [P] run end (inclusive)
     uint64_t* smax;    // [S] largest select-stage key per split
-    uint64_t* hbuf;    // [kHitBuf] staged hit list (hit-list front end)
     int32_t* hist;     // [kBins + 4]
     float* qrow;       // [d + 4], 16-byte aligned
 };
 
 constexpr int kBins = 64;
 
-constexpr int kHitBuf = 512;   // hit-list entries staged in shared memory per query
-
 __host__ __device__ constexpr size_t align16(size_t x) { return (x + 15) & ~static_cast<size_t>(15); }
 
 // Layout (every array starts 16-byte aligned): keys, sorted, d64 [P] u64;
-// smax [S] u64; hbuf [H] u64; perm, runs, rend [P] i32; hist [kBins+4] i32;
-// qrow [d+4] f32.  H = kHitBuf for the hit-list front end, 0 otherwise.
-__host__ __device__ inline size_t warp_scratch_bytes(int P, int S, int H, int d) {
+// smax [S] u64; perm, runs, rend [P] i32; hist [kBins+4] i32; qrow [d+4] f32.
+__host__ __device__ inline size_t warp_scratch_bytes(int P, int S, int d) {
     return align16(static_cast<size_t>(P) * 8) * 3 + align16(static_cast<size_t>(S) * 8) +
-           align16(static_cast<size_t>(H) * 8) + align16(static_cast<size_t>(P) * 4) * 3 +
+           align16(static_cast<size_t>(P) * 4) * 3 +
            align16((kBins + 4) * 4) + align16((static_cast<size_t>(d) + 4) * 4);
 }
 
-__device__ __forceinline__ WarpScratch carve(unsigned char* base, int P, int S, int H) {
+__device__ __forceinline__ WarpScratch carve(unsigned char* base, int P, int S) {
     WarpScratch w;
     size_t o = 0;
     w.keys = reinterpret_cast<uint64_t*>(base + o);   o += align16(static_cast<size_t>(P) * 8);
     w.sorted = reinterpret_cast<uint64_t*>(base + o); o += align16(static_cast<size_t>(P) * 8);
     w.d64 = reinterpret_cast<uint64_t*>(base + o);    o += align16(static_cast<size_t>(P) * 8);
     w.smax = reinterpret_cast<uint64_t*>(base + o);   o += align16(static_cast<size_t>(S) * 8);
-    w.hbuf = reinterpret_cast<uint64_t*>(base + o);   o += align16(static_cast<size_t>(H) * 8);
     w.perm = reinterpret_cast<int32_t*>(base + o);    o += align16(static_cast<size_t>(P) * 4);
     w.runs = reinterpret_cast<int32_t*>(base + o);    o += align16(static_cast<size_t>(P) * 4);
     w.rend = reinterpret_cast<int32_t*>(base + o);    o += align16(static_cast<size_t>(P) * 4);
@@ -232,16 +227,115 @@ __device__ void cut_bin(const int32_t* hist, int need, int lane, int* bin, int* 
     *before = own ? __shfl_sync(0xffffffffu, mb, __ffs(own) - 1) : 0;
 }
 
+constexpr int kRegHits = 16;   // hit-list entries held in registers per lane
+
 // Hit-list front end: keep the listed references whose low-precision key is
 // among the best c, cutting at a histogram bin (refined once), so at least c
 // and usually a few more are kept; their exact float32 keys go to w.keys.
 // Returns the number kept, or -1 (list shorter than c), -2 (overflowed),
 // -3 (the cut kept more than P) to send the query to the exact fallback.
+// Lists of up to 32*kRegHits entries are read once into registers; longer
+// ones are re-read from global memory at every pass.
+template <int METRIC, bool REG>
+__device__ int gather_hits_impl(const FinalizeArgs& a, int64_t q, int P, WarpScratch& w, int lane,
+                                int total) {
+    const HitLists& hl = a.hits;
+    const int S = hl.S, cap = hl.cap, c = hl.c;
+    const uint64_t* base = hl.keys + q * static_cast<int64_t>(S) * cap;
+    const int32_t* cnts = hl.counts + q * static_cast<int64_t>(S);
+    uint64_t reg[REG ? kRegHits : 1];
+    if (REG) {
+        // entry e of the concatenated lists -> lane e % 32, slot e / 32
+        int o = 0;
+#pragma unroll
+        for (int i = 0; i < kRegHits; ++i) reg[i] = kEmptyKey;
+        for (int s = 0; s < S; ++s) {
+            const int cs = min(cnts[s], cap);
+            const uint64_t* sp = base + static_cast<int64_t>(s) * cap;
+#pragma unroll
+            for (int i = 0; i < kRegHits; ++i) {
+                const int e = i * 32 + lane - o;          // index into split s
+                if (e >= 0 && e < cs) reg[i] = sp[e];
+            }
+            o += cs;
+        }
+    }
+    // visit every entry: f(key) for valid entries
+    auto for_each = [&](auto&& f) {
+        if (REG) {
+#pragma unroll
+            for (int i = 0; i < kRegHits; ++i)
+                if (reg[i] != kEmptyKey) f(reg[i]);
+        } else {
+            for (int s = 0; s < S; ++s) {
+                const int cs = min(cnts[s], cap);
+                const uint64_t* sp = base + static_cast<int64_t>(s) * cap;
+                for (int e = lane; e < cs; e += 32) f(sp[e]);
+            }
+        }
+    };
+    float vmin = __int_as_float(0x7f800000), vmax = -vmin;
+    for_each([&](uint64_t key) {
+        const float v = key_dist(key);
+        vmin = fminf(vmin, v);
+        vmax = fmaxf(vmax, v);
+    });
+    for (int o = 16; o > 0; o >>= 1) {
+        vmin = fminf(vmin, __shfl_xor_sync(0xffffffffu, vmin, o));
+        vmax = fmaxf(vmax, __shfl_xor_sync(0xffffffffu, vmax, o));
+    }
+    Binning b1{vmin, vmax > vmin ? kBins / (vmax - vmin) : 0.f};
+    int cut1 = kBins - 1, cut2 = kBins - 1;
+    Binning b2{0.f, 0.f};
+    if (total > c) {
+        for (int b = lane; b < kBins; b += 32) w.hist[b] = 0;
+        __syncwarp();
+        for_each([&](uint64_t key) { atomicAdd(&w.hist[b1.bin(key_dist(key))], 1); });
+        __syncwarp();
+        int before;
+        cut_bin(w.hist, c, lane, &cut1, &before);
+        const int in_bin = w.hist[cut1];
+        __syncwarp();
+        if (before + in_bin > P && b1.inv > 0.f) {   // refine the cut bin once
+            b2.lo = vmin + cut1 / b1.inv;
+            b2.inv = b1.inv * kBins;
+            for (int b = lane; b < kBins; b += 32) w.hist[b] = 0;
+            __syncwarp();
+            for_each([&](uint64_t key) {
+                const float v = key_dist(key);
+                if (b1.bin(v) == cut1) atomicAdd(&w.hist[b2.bin(v)], 1);
+            });
+            __syncwarp();
+            int before2;
+            cut_bin(w.hist, c - before, lane, &cut2, &before2);
+            __syncwarp();
+        }
+    }
+    auto keep = [&](uint64_t key) {
+        const float v = key_dist(key);
+        const int bb = b1.bin(v);
+        return bb < cut1 || (bb == cut1 && (b2.inv == 0.f || b2.bin(v) <= cut2));
+    };
+    // compact the kept indices into w.keys (shared-memory counter)
+    if (lane == 0) w.hist[kBins] = 0;
+    __syncwarp();
+    for_each([&](uint64_t key) {
+        if (keep(key)) {
+            const int pos = atomicAdd(&w.hist[kBins], 1);
+            if (pos < P) w.keys[pos] = key_idx(key);
+        }
+    });
+    __syncwarp();
+    const int kept = w.hist[kBins];
+    if (kept > P) return -3;
+    exact_keys<METRIC>(w.keys, kept, a, w.qrow, lane);
+    return kept;
+}
+
 template <int METRIC>
 __device__ int gather_hits(const FinalizeArgs& a, int64_t q, int P, WarpScratch& w, int lane) {
     const HitLists& hl = a.hits;
-    const int S = hl.S, cap = hl.cap, c = hl.c, d = a.d;
-    const uint64_t* base = hl.keys + q * static_cast<int64_t>(S) * cap;
+    const int S = hl.S, cap = hl.cap;
     const int32_t* cnts = hl.counts + q * static_cast<int64_t>(S);
     int total = 0, over = 0;
     for (int s = lane; s < S; s += 32) {
@@ -254,106 +348,9 @@ __device__ int gather_hits(const FinalizeArgs& a, int64_t q, int P, WarpScratch&
         over |= __shfl_xor_sync(0xffffffffu, over, o);
     }
     if (over) return -2;
-    if (total < c && total < a.m) return -1;
-    // stage the lists in shared memory when they fit: the passes below read them three times
-    const uint64_t* src = base;
-    int64_t sstride = cap;
-    if (total <= kHitBuf) {
-        int o = 0;
-        for (int s = 0; s < S; ++s) {
-            const int cs = min(cnts[s], cap);
-            for (int e = lane; e < cs; e += 32) w.hbuf[o + e] = base[static_cast<int64_t>(s) * cap + e];
-            o += cs;
-        }
-        __syncwarp();
-        src = w.hbuf;
-        sstride = 0;
-    }
-    // entry e of split s lives at src[s * sstride + off(s) + e] with off = running
-    // count when staged (sstride 0), 0 otherwise
-
-    // level-1 range of the ranking values
-    float vmin = __int_as_float(0x7f800000), vmax = -vmin;
-    for (int s = 0, o = 0; s < S; ++s) {
-        const int cs = min(cnts[s], cap);
-        const uint64_t* sp = src + (sstride ? static_cast<int64_t>(s) * sstride : o);
-        for (int e = lane; e < cs; e += 32) {
-            const float v = key_dist(sp[e]);
-            vmin = fminf(vmin, v);
-            vmax = fmaxf(vmax, v);
-        }
-        o += cs;
-    }
-    for (int o = 16; o > 0; o >>= 1) {
-        vmin = fminf(vmin, __shfl_xor_sync(0xffffffffu, vmin, o));
-        vmax = fmaxf(vmax, __shfl_xor_sync(0xffffffffu, vmax, o));
-    }
-    Binning b1{vmin, vmax > vmin ? kBins / (vmax - vmin) : 0.f};
-    int cut1 = kBins - 1, cut2 = kBins - 1;
-    Binning b2{0.f, 0.f};
-    if (total > c) {
-        for (int b = lane; b < kBins; b += 32) w.hist[b] = 0;
-        __syncwarp();
-        for (int s = 0, o = 0; s < S; ++s) {
-            const int cs = min(cnts[s], cap);
-            const uint64_t* sp = src + (sstride ? static_cast<int64_t>(s) * sstride : o);
-            for (int e = lane; e < cs; e += 32) atomicAdd(&w.hist[b1.bin(key_dist(sp[e]))], 1);
-            o += cs;
-        }
-        __syncwarp();
-        int before;
-        cut_bin(w.hist, c, lane, &cut1, &before);
-        const int in_bin = w.hist[cut1];
-        __syncwarp();
-        if (before + in_bin > P && b1.inv > 0.f) {
-            // refine the cut bin once
-            b2.lo = vmin + cut1 / b1.inv;
-            b2.inv = b1.inv * kBins;
-            for (int b = lane; b < kBins; b += 32) w.hist[b] = 0;
-            __syncwarp();
-            for (int s = 0, o = 0; s < S; ++s) {
-                const int cs = min(cnts[s], cap);
-                const uint64_t* sp = src + (sstride ? static_cast<int64_t>(s) * sstride : o);
-                for (int e = lane; e < cs; e += 32) {
-                    const float v = key_dist(sp[e]);
-                    if (b1.bin(v) == cut1) atomicAdd(&w.hist[b2.bin(v)], 1);
-                }
-                o += cs;
-            }
-            __syncwarp();
-            int before2;
-            cut_bin(w.hist, c - before, lane, &cut2, &before2);
-            __syncwarp();
-        }
-    }
-    // compact the kept indices, then compute their exact keys with all lanes busy
-    int kept = 0;
-    for (int s = 0, o = 0; s < S; ++s) {
-        const int cs = min(cnts[s], cap);
-        const uint64_t* sp = src + (sstride ? static_cast<int64_t>(s) * sstride : o);
-        o += cs;
-        for (int e0 = 0; e0 < cs; e0 += 32) {
-            const int e = e0 + lane;
-            bool take = false;
-            uint32_t j = 0;
-            if (e < cs) {
-                const uint64_t key = sp[e];
-                const float v = key_dist(key);
-                const int bb = b1.bin(v);
-                take = bb < cut1 || (bb == cut1 && (b2.inv == 0.f || b2.bin(v) <= cut2));
-                j = key_idx(key);
-            }
-            const unsigned bal = __ballot_sync(0xffffffffu, take);
-            const int pos = kept + __popc(bal & ((1u << lane) - 1u));
-            if (take && pos < P) w.keys[pos] = j;
-            kept += __popc(bal);
-        }
-    }
-    __syncwarp();
-    if (kept > P) return -3;
-    exact_keys<METRIC>(w.keys, kept, a, w.qrow, lane);
-    (void)d;
-    return kept;
+    if (total < hl.c && total < a.m) return -1;
+    if (total <= 32 * kRegHits) return gather_hits_impl<METRIC, true>(a, q, P, w, lane, total);
+    return gather_hits_impl<METRIC, false>(a, q, P, w, lane, total);
 }
 
 __device__ __forceinline__ void local_min(const uint64_t* keys, int pool, int lane, uint64_t* lmin,
@@ -384,8 +381,7 @@ __global__ void finalize_kernel(FinalizeArgs a, int P, int warps_per_block) {
 
     const int S = a.use_hits ? 1 : a.cand.S;
     const int d = a.d, k = a.k;
-    const int H = a.use_hits ? kHitBuf : 0;
-    WarpScratch w = carve(smem_raw + warp_scratch_bytes(P, S, H, d) * warp, P, S, H);
+    WarpScratch w = carve(smem_raw + warp_scratch_bytes(P, S, d) * warp, P, S);
     for (int t = lane; t < d; t += 32) w.qrow[t] = a.Q[q * d + t];
     for (int s = lane; s < S; s += 32) w.smax[s] = 0;
     __syncwarp();
@@ -680,7 +676,7 @@ cudaError_t launch_finalize(const FinalizeArgs& a, cudaStream_t st, int* launche
     P = (P + 3) & ~3;
     if (P > kMaxPool) return cudaErrorInvalidValue;
     const size_t per_warp =
-        warp_scratch_bytes(P, a.use_hits ? 1 : a.cand.S, a.use_hits ? kHitBuf : 0, a.d);
+        warp_scratch_bytes(P, a.use_hits ? 1 : a.cand.S, a.d);
     int wpb = static_cast<int>((96 * 1024) / per_warp);
     wpb = wpb < 1 ? 1 : (wpb > 8 ? 8 : wpb);
     const size_t smem = per_warp * wpb;

@@ -127,18 +127,20 @@ enum LowPrecision : int { kTF32 = 1, kBF16 = 2 };
 
 // Row length (elements) of the low-precision operand copies: d coordinates,
 // four augmentation words (norm halves, threshold halves), zero padded to a
-// whole 32-byte MMA K step.
+// whole number of 128-byte K blocks.
 int tc_padded_dim(int32_t d, int prec);
 
 // Launch plan of the pilot and filter passes for one search.
 struct TcPlan {
     int32_t mt;          // 128-query tiles per CTA (1 or 2)
     int32_t kb;          // 128-byte K blocks per operand row
-    int32_t ksteps;      // MMA instructions per tile pair
-    int32_t stages;      // reference-tile ring depth
+    int32_t ksteps;      // 32-byte MMA K steps that carry data
+    int32_t rb;          // references per TMA stage (128 or 256)
+    int32_t kbs;         // K blocks per TMA stage (kb, or 1 for long rows)
+    int32_t stages;      // reference-stage ring depth
     int32_t S;           // reference splits
-    int64_t chunk;       // references per split (multiple of 128)
-    int32_t stride;      // pilot samples every stride-th tile
+    int64_t chunk;       // references per split (multiple of rb)
+    int32_t stride;      // pilot samples every stride-th stage
     int32_t spt;         // pilot tile slots per split
     int32_t G;           // pilot group maxima per query
     int32_t cprime;      // order statistic of the group maxima used as threshold
@@ -146,7 +148,7 @@ struct TcPlan {
     int32_t cap;         // list capacity per (query, split)
     size_t smem_filter;
 };
-TcPlan tc_plan(int64_t n, int64_t m, int32_t kp, int prec, int32_t c, int num_sms);
+TcPlan tc_plan(int64_t n, int64_t m, int32_t d, int32_t kp, int prec, int32_t c, int num_sms);
 
 // Reference copy [r, -||r||^2/2 (hi, lo), 1, 1, 0..] and float32 norms.
 cudaError_t launch_prepare_ref(const float* R, int64_t m, int32_t d, int32_t kp, int prec,

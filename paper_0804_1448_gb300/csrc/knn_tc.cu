@@ -25,12 +25,14 @@
 // CTA layout: MT tiles of 128 queries (MMA M; one TMEM lane per query) share
 // every reference tile of 128 (MMA N):
 //   warp 0        TMA producer: the query tiles once, then reference tiles into
-//                 a ring of `stages` shared-memory buffers (128-byte swizzle);
+//                 a ring of single-K-block shared-memory stages (128-byte swizzle);
 //   warp 1        MMA issuer: per reference tile and query tile, kp*elt/32
 //                 tcgen05.mma into one of two TMEM accumulators per query tile;
 //                 tcgen05.commit frees the smem stage and publishes the tile;
-//   warps 2..     epilogue, 4 per query tile: thread t of warp w owns the query
-//                 row 32*(w%4)+t; tcgen05.ld 32x32b reads 32 columns at a time.
+//   warps 2..     epilogue, 8 per query tile: warp w may read the TMEM lanes
+//                 32*(w%4)..+31, so thread t of warp w owns query row
+//                 32*(w%4)+t; the two warps sharing a lane quarter split the
+//                 four 32-column slices of each tile between them.
 // Every mbarrier wait is bounded; on expiry the CTA raises the error flag,
 // stops, waits for what it issued and frees its TMEM.
 #include <cmath>
@@ -54,12 +56,16 @@ constexpr int kAugCols = 4;
 
 struct TcArgs {
     int64_t n, m;
-    int32_t kb, ksteps, stages;
-    int64_t chunk;        // references per split (multiple of kBlockN)
+    int32_t kb;           // 128-byte K blocks per operand row (row pitch = kb * 128 bytes)
+    int32_t ksteps;       // 32-byte MMA K steps that carry data
+    int32_t rb;           // references per pipeline stage (128 or 256): rb/128 MMA tiles
+    int32_t kbs;          // K blocks per stage: kb (whole rows) or 1 (then rb = 128)
+    int32_t stages;
+    int64_t chunk;        // references per split (multiple of rb)
     int32_t S;
-    int32_t stride;       // pilot: every stride-th tile of a split
-    int32_t spt;          // pilot: sampled-tile slots per split
-    int32_t G;            // pilot: group maxima per query (S * spt * 4)
+    int32_t stride;       // pilot: every stride-th stage of a split
+    int32_t spt;          // pilot: sampled-stage slots per split
+    int32_t G;            // pilot: group maxima per query (S * spt * rb / 32)
     uint32_t* gmax;       // pilot: [n][G] order-mapped maxima, 0 = no group
     uint64_t* lists;      // filter: [n][S][cap]
     int32_t* counts;      // filter: [n][S] (may exceed cap: overflow)
@@ -68,28 +74,54 @@ struct TcArgs {
     int32_t* error_flag;
 };
 
-// A: mt query tiles of kb K blocks (resident); B: a ring of `stages` single
-// K blocks of one reference tile; staging of hit values (filter only).
-__host__ __device__ constexpr size_t tc_smem_bytes(int mt, int kb, int stages, bool pilot) {
-    return 1024 + static_cast<size_t>(kTileBytes) * (static_cast<size_t>(mt) * kb + stages) +
-           (pilot ? 0 : static_cast<size_t>(128) * mt * 32 * 4) + 512;
+// A: mt query tiles of kb K blocks (resident); B: a ring of `stages` boxes of
+// rb references x kbs K blocks; staging of hit values (filter only).
+__host__ __device__ constexpr size_t tc_smem_bytes(int mt, int kb, int rb, int kbs, int stages,
+                                                   bool pilot) {
+    return 1024 + static_cast<size_t>(kTileBytes) * mt * kb +
+           static_cast<size_t>(rb) * kAtomBytes * kbs * stages +
+           (pilot ? 0 : static_cast<size_t>(256) * mt * 32 * 4 + 128 * mt * 4) + 512;
 }
 
-template <int PREC, int MT, bool PILOT>
-__global__ void __launch_bounds__(64 + 128 * MT, 1)
+// MMAs of one 128-byte K block of one reference tile for all MT query tiles.
+// Fully unrolled over the four 32-byte K steps (a runtime guard skips steps
+// past the data): issue from the single MMA thread must keep pace with the
+// tensor core, and a loop with runtime bounds halves the issue rate.
+template <int PREC, int MT>
+__device__ __forceinline__ void issue_kblock(uint32_t d_tmem, uint32_t a_kb, uint32_t a_mt_stride,
+                                             uint32_t b_kb, int k4, bool first, uint32_t id) {
+#pragma unroll
+    for (int mt = 0; mt < MT; ++mt) {
+#pragma unroll
+        for (int ks = 0; ks < 4; ++ks) {
+            if (ks < k4)
+                mma<PREC>(d_tmem + mt * kBlockN, sdesc(a_kb + mt * a_mt_stride + ks * 32),
+                          sdesc(b_kb + ks * 32), id, (first && ks == 0) ? 0u : 1u);
+        }
+    }
+}
+
+// KBT > 0: whole-K stages of exactly KBT K blocks (compile-time, unrolled);
+// KBT == 0: any K-block count and either stage layout (loops over K blocks).
+template <int PREC, int MT, bool PILOT, int KBT>
+__global__ void __launch_bounds__(64 + 256 * MT, 1)
 tc_kernel(const __grid_constant__ CUtensorMap tmap_q, const __grid_constant__ CUtensorMap tmap_r,
           TcArgs a) {
-    constexpr int kEpi = 128 * MT;
+    constexpr int kEpi = 256 * MT;             // epilogue threads: two per query row
     constexpr uint32_t kTmemCols = 256 * MT;   // two 128-column accumulators per query tile
     extern __shared__ unsigned char smem_raw[];
     const uint32_t raw = smem_u32(smem_raw);
     unsigned char* smem = smem_raw + (((raw + 1023u) & ~1023u) - raw);
 
-    const int KB = a.kb, NST = a.stages;
+    const int KB = KBT > 0 ? KBT : a.kb, KBS = KBT > 0 ? KBT : a.kbs;
+    const int NST = a.stages, RB = a.rb, TPS = a.rb / kBlockN;
+    const int SPT = KB / KBS;                   // stages per reference tile (1, or KB when KBS = 1)
+    const size_t stage_bytes = static_cast<size_t>(RB) * kAtomBytes * KBS;
     unsigned char* sA = smem;
     unsigned char* sB = sA + static_cast<size_t>(MT) * KB * kTileBytes;
-    float* stage = reinterpret_cast<float*>(sB + static_cast<size_t>(NST) * kTileBytes);
-    uint64_t* bars = reinterpret_cast<uint64_t*>(stage + (PILOT ? 0 : kEpi * 32));
+    float* stage = reinterpret_cast<float*>(sB + NST * stage_bytes);
+    int* row_cnt = reinterpret_cast<int*>(stage + (PILOT ? 0 : kEpi * 32));   // [128*MT]
+    uint64_t* bars = reinterpret_cast<uint64_t*>(row_cnt + (PILOT ? 0 : 128 * MT));
     uint64_t* full = bars;
     uint64_t* empty = bars + kMaxStages;
     uint64_t* a_full = bars + 2 * kMaxStages;
@@ -104,9 +136,10 @@ tc_kernel(const __grid_constant__ CUtensorMap tmap_q, const __grid_constant__ CU
     const int split = blockIdx.y;
     const int64_t r_begin = static_cast<int64_t>(split) * a.chunk;
     const int64_t r_end = min(a.m, r_begin + a.chunk);
-    const int tiles_all = static_cast<int>((r_end - r_begin + kBlockN - 1) / kBlockN);
+    const int stages_all = static_cast<int>((r_end - r_begin + RB - 1) / RB);
     const int stride = PILOT ? a.stride : 1;
-    const int nt = (tiles_all + stride - 1) / stride;
+    const int ng = (stages_all + stride - 1) / stride;   // stages this CTA processes
+    const int nt = ng * TPS;                             // MMA tiles
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < NST; ++s) {
@@ -135,29 +168,24 @@ tc_kernel(const __grid_constant__ CUtensorMap tmap_q, const __grid_constant__ CU
 
     if (warp == 0) {
         // -------------------------------------------------------- producer
+        // one 3-D box per operand load: (128 bytes of K) x rows x all K blocks
         if (lane == 0) {
-            constexpr int box_x = kAtomBytes / ((PREC == kBF16) ? 2 : 4);
             mbar_expect_tx(a_full, MT * KB * kTileBytes);
             for (int mt = 0; mt < MT; ++mt)
-                for (int kb = 0; kb < KB; ++kb)
-                    tma_load_2d(sA + static_cast<size_t>(mt * KB + kb) * kTileBytes, &tmap_q, a_full,
-                                kb * box_x, static_cast<int>(q0 + mt * kBlockM));
-            int issued = 0;   // K blocks issued; block g goes to stage g % NST
-            bool ok = true;
-            for (int i = 0; ok && i < nt; ++i) {
-                const int y = static_cast<int>(r_begin + static_cast<int64_t>(i) * stride * kBlockN);
-                for (int kb = 0; kb < KB; ++kb) {
-                    const int g = i * KB + kb, s = g % NST;
-                    if (!mbar_wait(&empty[s], ((g / NST) & 1) ^ 1, abort_flag)) { fail(); ok = false; break; }
-                    mbar_expect_tx(&full[s], kTileBytes);
-                    tma_load_2d(sB + static_cast<size_t>(s) * kTileBytes, &tmap_r, &full[s],
-                                kb * box_x, y);
-                    issued = g + 1;
-                }
+                tma_load_3d(sA + static_cast<size_t>(mt) * KB * kTileBytes, &tmap_q, a_full, 0,
+                            static_cast<int>(q0 + mt * kBlockM), 0);
+            int issued = 0;   // stage h = g * SPT + kb: reference rows of g, K blocks kb..
+            for (int h = 0; h < ng * SPT; ++h) {
+                const int g = h / SPT, z = (h % SPT) * KBS, s = h % NST;
+                if (!mbar_wait(&empty[s], ((h / NST) & 1) ^ 1, abort_flag)) { fail(); break; }
+                mbar_expect_tx(&full[s], static_cast<uint32_t>(stage_bytes));
+                const int y = static_cast<int>(r_begin + static_cast<int64_t>(g) * stride * RB);
+                tma_load_3d(sB + s * stage_bytes, &tmap_r, &full[s], 0, y, z);
+                issued = h + 1;
             }
             mbar_wait(a_full, 0, nullptr);   // drain: every issued copy has landed
-            for (int g = (issued > NST ? issued - NST : 0); g < issued; ++g)
-                mbar_wait(&full[g % NST], (g / NST) & 1, nullptr);
+            for (int h = (issued > NST ? issued - NST : 0); h < issued; ++h)
+                mbar_wait(&full[h % NST], (h / NST) & 1, nullptr);
         }
         __syncwarp();
     } else if (warp == 1) {
@@ -167,27 +195,59 @@ tc_kernel(const __grid_constant__ CUtensorMap tmap_q, const __grid_constant__ CU
             bool ok = mbar_wait(a_full, 0, abort_flag);
             if (!ok) fail();
             const uint32_t a_base = smem_u32(sA);
-            for (int i = 0; ok && i < nt; ++i) {
-                const int buf = i & 1;
-                if (!mbar_wait(&t_empty[buf], ((i >> 1) & 1) ^ 1, abort_flag)) { fail(); break; }
-                for (int kb = 0; kb < KB; ++kb) {
-                    const int g = i * KB + kb, s = g % NST;
-                    if (!mbar_wait(&full[s], (g / NST) & 1, abort_flag)) { fail(); ok = false; break; }
-                    tc_fence_after();
-                    const uint32_t b_base = smem_u32(sB + static_cast<size_t>(s) * kTileBytes);
-                    const int k4 = min(4, a.ksteps - kb * 4);   // 32-byte K steps in this block
+            if (SPT == 1) {
+                // whole-K stages: stage g holds TPS tiles of 128 references
+                for (int g = 0; ok && g < ng; ++g) {
+                    const int s = g % NST;
+                    if (!mbar_wait(&full[s], (g / NST) & 1, abort_flag)) { fail(); break; }
+                    const uint32_t b_stage = smem_u32(sB + s * stage_bytes);
+                    for (int t2 = 0; t2 < TPS; ++t2) {
+                        const int i = g * TPS + t2, buf = i & 1;
+                        if (!mbar_wait(&t_empty[buf], ((i >> 1) & 1) ^ 1, abort_flag)) {
+                            fail();
+                            ok = false;
+                            break;
+                        }
+                        tc_fence_after();
+                        const uint32_t d_tmem = tmem + buf * MT * kBlockN;
+                        const uint32_t b_tile = b_stage + t2 * kTileBytes;
+                        if (KBT > 0) {
 #pragma unroll
-                    for (int mt = 0; mt < MT; ++mt) {
-                        const uint32_t d_tmem = tmem + (buf * MT + mt) * kBlockN;
-                        const uint32_t am = a_base + (mt * KB + kb) * kTileBytes;
-                        for (int ks = 0; ks < k4; ++ks)
-                            mma<PREC>(d_tmem, sdesc(am + ks * 32), sdesc(b_base + ks * 32), id,
-                                      (kb | ks) ? 1u : 0u);
+                            for (int kb = 0; kb < (KBT > 0 ? KBT : 1); ++kb)
+                                issue_kblock<PREC, MT>(d_tmem, a_base + kb * kTileBytes, KB * kTileBytes,
+                                                       b_tile + kb * RB * kAtomBytes,
+                                                       a.ksteps - kb * 4, kb == 0, id);
+                        } else {
+                            for (int kb = 0; kb < KB; ++kb)
+                                issue_kblock<PREC, MT>(d_tmem, a_base + kb * kTileBytes, KB * kTileBytes,
+                                                       b_tile + kb * RB * kAtomBytes,
+                                                       a.ksteps - kb * 4, kb == 0, id);
+                        }
+                        tc_commit(&t_full[buf]);
                     }
-                    tc_commit(&empty[s]);
+                    tc_commit(&empty[s]);   // the stage is free once these MMAs complete
                 }
-                if (!ok) break;
-                tc_commit(&t_full[buf]);
+            } else {
+                // one K block per stage: tile g takes stages g*KB .. g*KB+KB-1
+                for (int g = 0; ok && g < ng; ++g) {
+                    const int buf = g & 1;
+                    if (!mbar_wait(&t_empty[buf], ((g >> 1) & 1) ^ 1, abort_flag)) { fail(); break; }
+                    for (int kb = 0; kb < KB; ++kb) {
+                        const int h = g * KB + kb, s = h % NST;
+                        if (!mbar_wait(&full[s], (h / NST) & 1, abort_flag)) {
+                            fail();
+                            ok = false;
+                            break;
+                        }
+                        tc_fence_after();
+                        issue_kblock<PREC, MT>(tmem + buf * MT * kBlockN, a_base + kb * kTileBytes,
+                                               KB * kTileBytes, smem_u32(sB + s * stage_bytes),
+                                               a.ksteps - kb * 4, kb == 0, id);
+                        tc_commit(&empty[s]);
+                    }
+                    if (!ok) break;
+                    tc_commit(&t_full[buf]);
+                }
             }
             tc_commit(drain);   // arrives once every MMA issued above has completed
             mbar_wait(drain, 0, nullptr);
@@ -196,7 +256,9 @@ tc_kernel(const __grid_constant__ CUtensorMap tmap_q, const __grid_constant__ CU
     } else {
         // -------------------------------------------------------- epilogue
         const int et = threadIdx.x - 64;            // 0 .. kEpi-1
-        const int mt = et / 128;
+        const int ew = et / 32;
+        const int mt = (ew / 4) % MT;
+        const int half = ew / (4 * MT);             // slices 2*half, 2*half+1 of every tile
         const int quarter = warp & 3;               // the TMEM lanes this warp may access
         const int row = quarter * 32 + lane;
         const int64_t q = q0 + mt * kBlockM + row;
@@ -204,60 +266,83 @@ tc_kernel(const __grid_constant__ CUtensorMap tmap_q, const __grid_constant__ CU
         const uint32_t lane_addr = tmem + (static_cast<uint32_t>(quarter * 32) << 16);
         float* st = stage + et * 32;
         const int sw = et & 7;                      // bank swizzle of this thread's slot
+        const int gpt = RB / 32;                    // groups of 32 references per stage
         uint64_t* list = nullptr;
         uint32_t* gout = nullptr;
-        if (PILOT) gout = a.gmax + q * a.G + static_cast<int64_t>(split) * a.spt * 4;
+        if (PILOT) gout = a.gmax + q * a.G + static_cast<int64_t>(split) * a.spt * gpt;
         else list = a.lists + (q * a.S + split) * static_cast<int64_t>(a.cap);
-        int cnt = 0;
+        int* rcnt = row_cnt + mt * kBlockM + row;   // hits of this row (both halves)
+        if (!PILOT && half == 0) *rcnt = 0;
+        named_bar_sync(1, kEpi);
         for (int i = 0; i < nt; ++i) {
-            const int buf = i & 1;
+            const int buf = i & 1, g = i / TPS, t2 = i % TPS;
             const bool ok = mbar_wait(&t_full[buf], (i >> 1) & 1, abort_flag);
             if (!__all_sync(0xffffffffu, ok)) { fail(); break; }
             tc_fence_after();
-            const int64_t jt = r_begin + static_cast<int64_t>(i) * stride * kBlockN;
-#pragma unroll 1
-            for (int ch = 0; ch < kBlockN / 32; ++ch) {
-                uint32_t r[32];
-                __syncwarp();
-                tmem_ld32u(lane_addr + (buf * MT + mt) * kBlockN + ch * 32, r);
-                if (ch == kBlockN / 32 - 1) {
+            const int64_t jt = r_begin + static_cast<int64_t>(g) * stride * RB + t2 * kBlockN;
+            // this warp's two 32-column slices; the second loads while the
+            // first is processed
+            uint32_t ra[32], rb[32];
+            const uint32_t col0 = lane_addr + (buf * MT + mt) * kBlockN + half * 64;
+            __syncwarp();
+            tmem_ld32u_async(col0, ra);
+#pragma unroll
+            for (int sl = 0; sl < 2; ++sl) {
+                const int ch = 2 * half + sl;
+                uint32_t (&r)[32] = sl ? rb : ra;
+                tmem_wait_ld(r);
+                if (sl == 0) {
+                    tmem_ld32u_async(col0 + 32, rb);
+                } else {
                     tc_fence_before();
-                    mbar_arrive(&t_empty[buf]);
+                    mbar_arrive(&t_empty[buf]);   // both slices of this buffer are in registers
                 }
                 const int64_t j0 = jt + ch * 32;
                 const int64_t left = r_end - j0;
                 const int nvalid = left <= 0 ? 0 : (left >= 32 ? 32 : static_cast<int>(left));
                 if (PILOT) {
-                    float mx = __int_as_float(0xff800000);   // -inf
+                    float v[32];
 #pragma unroll
                     for (int u = 0; u < 32; ++u)
-                        mx = fmaxf(mx, u < nvalid ? __uint_as_float(r[u]) : __int_as_float(0xff800000));
-                    if (active && nvalid > 0) gout[i * 4 + ch] = ord_f32(mx);
-                } else {
-                    uint32_t sm = 0;
+                        v[u] = u < nvalid ? __uint_as_float(r[u]) : __int_as_float(0xff800000);
 #pragma unroll
-                    for (int u = 0; u < 32; ++u) sm = __funnelshift_l(r[u], sm, 1);
-                    // bit 31-u is the sign of element u; a pass is acc >= 0
+                    for (int w2 = 16; w2 > 0; w2 >>= 1)
+#pragma unroll
+                        for (int u = 0; u < w2; ++u) v[u] = fmaxf(v[u], v[u + w2]);
+                    if (active && nvalid > 0) gout[g * gpt + t2 * 4 + ch] = ord_f32(v[0]);
+                } else {
+                    // sign bits, bit 31-u for element u, as four independent chains
+                    uint32_t m4[4] = {0u, 0u, 0u, 0u};
+#pragma unroll
+                    for (int u = 0; u < 8; ++u)
+#pragma unroll
+                        for (int h = 0; h < 4; ++h) m4[h] = __funnelshift_l(r[8 * h + u], m4[h], 1);
+                    const uint32_t sm = (m4[0] << 24) | (m4[1] << 16) | (m4[2] << 8) | m4[3];
+                    // a pass is acc >= 0
                     uint32_t hits = a.append_all ? 0xffffffffu : ~sm;
                     hits &= nvalid == 0 ? 0u : (0xffffffffu << (32 - nvalid));
                     if (!active) hits = 0;
                     if (hits) {
 #pragma unroll
-                        for (int g = 0; g < 8; ++g)
-                            reinterpret_cast<uint4*>(st)[g ^ sw] =
-                                make_uint4(r[4 * g], r[4 * g + 1], r[4 * g + 2], r[4 * g + 3]);
+                        for (int h = 0; h < 8; ++h)
+                            reinterpret_cast<uint4*>(st)[h ^ sw] =
+                                make_uint4(r[4 * h], r[4 * h + 1], r[4 * h + 2], r[4 * h + 3]);
                         while (hits) {
                             const int u = __clz(hits);
                             hits &= ~(0x80000000u >> u);
                             const float v = st[(((u >> 2) ^ sw) << 2) | (u & 3)];
-                            if (cnt < a.cap) list[cnt] = make_key(-v, static_cast<uint32_t>(j0 + u));
-                            ++cnt;
+                            const int slot = atomicAdd(rcnt, 1);
+                            if (slot < a.cap) list[slot] = make_key(-v, static_cast<uint32_t>(j0 + u));
                         }
                     }
+                    __syncwarp();
                 }
             }
         }
-        if (!PILOT && active) a.counts[q * a.S + split] = cnt;
+        if (!PILOT) {
+            named_bar_sync(1, kEpi);
+            if (active && half == 0) a.counts[q * a.S + split] = *rcnt;
+        }
     }
     tc_fence_before();
     __syncthreads();
@@ -378,45 +463,67 @@ EncodeTiledFn encode_fn() {
     return fn;
 }
 
-// rows x kp operand; box = 128 bytes of K x 128 rows; 128-byte swizzle; zero fill.
-bool make_map(CUtensorMap* map, const void* base, int64_t rows, int kp, int prec) {
+// rows x kp operand seen as 3-D: (128 bytes of K) x rows x K blocks, so one box
+// brings box_rows rows with all their K blocks, laid out block-major
+// ([K block][row][128 bytes], 128-byte swizzle) as the MMA descriptors expect.
+// Rows outside the tensor read as zero.
+bool make_map(CUtensorMap* map, const void* base, int64_t rows, int kp, int prec, int box_rows,
+              int box_kb) {
     EncodeTiledFn fn = encode_fn();
     if (!fn) return false;
     const int elt = (prec == kBF16) ? 2 : 4;
-    cuuint64_t dims[2] = {static_cast<cuuint64_t>(kp), static_cast<cuuint64_t>(rows)};
-    cuuint64_t strides[1] = {static_cast<cuuint64_t>(kp) * elt};
-    cuuint32_t box[2] = {static_cast<cuuint32_t>(kAtomBytes / elt), static_cast<cuuint32_t>(kBlockM)};
-    cuuint32_t estr[2] = {1, 1};
+    const int kb = kp * elt / kAtomBytes;
+    cuuint64_t dims[3] = {static_cast<cuuint64_t>(kAtomBytes / elt), static_cast<cuuint64_t>(rows),
+                          static_cast<cuuint64_t>(kb)};
+    cuuint64_t strides[2] = {static_cast<cuuint64_t>(kp) * elt, static_cast<cuuint64_t>(kAtomBytes)};
+    cuuint32_t box[3] = {static_cast<cuuint32_t>(kAtomBytes / elt), static_cast<cuuint32_t>(box_rows),
+                         static_cast<cuuint32_t>(box_kb > 0 ? box_kb : kb)};
+    cuuint32_t estr[3] = {1, 1, 1};
     CUresult r = fn(map,
                     prec == kBF16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32,
-                    2, const_cast<void*>(base), dims, strides, box, estr,
+                    3, const_cast<void*>(base), dims, strides, box, estr,
                     CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
                     CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     return r == CUDA_SUCCESS;
 }
 
-template <int PREC, int MT, bool PILOT>
+template <int PREC, int MT, bool PILOT, int KBT>
 cudaError_t launch_kernel(const TcPlan& p, const CUtensorMap& mq, const CUtensorMap& mr,
                           const TcArgs& a, cudaStream_t st) {
-    auto kern = tc_kernel<PREC, MT, PILOT>;
-    const size_t smem = tc_smem_bytes(MT, p.kb, p.stages, PILOT);
+    auto kern = tc_kernel<PREC, MT, PILOT, KBT>;
+    const size_t smem = tc_smem_bytes(MT, p.kb, p.rb, p.kbs, p.stages, PILOT);
     cudaError_t err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                            static_cast<int>(smem));
     if (err != cudaSuccess) return err;
     dim3 grid(static_cast<unsigned>((a.n + kBlockM * MT - 1) / (kBlockM * MT)),
               static_cast<unsigned>(a.S));
-    kern<<<grid, 64 + 128 * MT, smem, st>>>(mq, mr, a);
+    kern<<<grid, 64 + 256 * MT, smem, st>>>(mq, mr, a);
     return cudaGetLastError();
+}
+
+template <int PREC, int MT, bool PILOT>
+cudaError_t dispatch_kb(const TcPlan& p, const CUtensorMap& mq, const CUtensorMap& mr,
+                        const TcArgs& a, cudaStream_t st) {
+    if (p.kbs == p.kb) {   // whole-K stages: unrolled issue for the common row lengths
+        switch (p.kb) {
+            case 1: return launch_kernel<PREC, MT, PILOT, 1>(p, mq, mr, a, st);
+            case 2: return launch_kernel<PREC, MT, PILOT, 2>(p, mq, mr, a, st);
+            case 3: return launch_kernel<PREC, MT, PILOT, 3>(p, mq, mr, a, st);
+            case 4: return launch_kernel<PREC, MT, PILOT, 4>(p, mq, mr, a, st);
+            default: break;
+        }
+    }
+    return launch_kernel<PREC, MT, PILOT, 0>(p, mq, mr, a, st);
 }
 
 template <bool PILOT>
 cudaError_t dispatch(const TcPlan& p, int prec, const CUtensorMap& mq, const CUtensorMap& mr,
                      const TcArgs& a, cudaStream_t st) {
     if (prec == kBF16)
-        return p.mt == 2 ? launch_kernel<kBF16, 2, PILOT>(p, mq, mr, a, st)
-                         : launch_kernel<kBF16, 1, PILOT>(p, mq, mr, a, st);
-    return p.mt == 2 ? launch_kernel<kTF32, 2, PILOT>(p, mq, mr, a, st)
-                     : launch_kernel<kTF32, 1, PILOT>(p, mq, mr, a, st);
+        return p.mt == 2 ? dispatch_kb<kBF16, 2, PILOT>(p, mq, mr, a, st)
+                         : dispatch_kb<kBF16, 1, PILOT>(p, mq, mr, a, st);
+    return p.mt == 2 ? dispatch_kb<kTF32, 2, PILOT>(p, mq, mr, a, st)
+                     : dispatch_kb<kTF32, 1, PILOT>(p, mq, mr, a, st);
 }
 
 TcArgs base_args(const TcPlan& p, int64_t n, int64_t m, int32_t* error_flag) {
@@ -425,6 +532,8 @@ TcArgs base_args(const TcPlan& p, int64_t n, int64_t m, int32_t* error_flag) {
     a.m = m;
     a.kb = p.kb;
     a.ksteps = p.ksteps;
+    a.rb = p.rb;
+    a.kbs = p.kbs;
     a.stages = p.stages;
     a.chunk = p.chunk;
     a.S = p.S;
@@ -440,22 +549,32 @@ TcArgs base_args(const TcPlan& p, int64_t n, int64_t m, int32_t* error_flag) {
 }  // namespace
 
 int tc_padded_dim(int32_t d, int prec) {
-    const int step = (prec == kBF16) ? 16 : 8;   // 32 bytes: one MMA K step
+    const int step = (prec == kBF16) ? 64 : 32;   // whole 128-byte K blocks per row
     return (d + kAugCols + step - 1) / step * step;
 }
 
-TcPlan tc_plan(int64_t n, int64_t m, int32_t kp, int prec, int32_t c, int num_sms) {
+TcPlan tc_plan(int64_t n, int64_t m, int32_t d, int32_t kp, int prec, int32_t c, int num_sms) {
     TcPlan p{};
     const int elt = (prec == kBF16) ? 2 : 4;
-    p.kb = (kp * elt + kAtomBytes - 1) / kAtomBytes;
-    p.ksteps = kp * elt / 32;
+    const int kstep = 32 / elt;                    // elements per MMA K step
+    p.kb = kp * elt / kAtomBytes;
+    p.ksteps = (d + kAugCols + kstep - 1) / kstep;
     p.stages = 0;
-    // two query tiles per CTA when the ring still holds two reference tiles
-    for (int mt = 2; mt >= 1 && p.stages == 0; --mt) {
-        const int need = (mt == 2) ? 2 * p.kb : 2;
-        for (int s = kMaxStages; s >= need; --s) {
-            if (tc_smem_bytes(mt, p.kb, s, false) <= kSmemLimit) {
-                p.mt = mt;
+    // prefer two query tiles per CTA and whole-K 256-reference stages, then
+    // shrink; single-K-block stages (more TMA boxes) only when rows are long
+    const int shapes[6][3] = {{2, 256, 0}, {2, 128, 0}, {1, 256, 0}, {1, 128, 0}, {2, 128, 1},
+                              {1, 128, 1}};
+    // whole-K 256-reference stages need a third stage to hide the TMA latency;
+    // with 128-reference stages two boxes per tile pair are already in flight
+    for (int si = 0; si < 6 && p.stages == 0; ++si) {
+        const int kbs = shapes[si][2] ? 1 : p.kb;
+        const int smax = shapes[si][2] ? 12 : kMaxStages;
+        const int smin = (!shapes[si][2] && shapes[si][1] == 256) ? 3 : 2;
+        for (int s = smax; s >= smin; --s) {
+            if (tc_smem_bytes(shapes[si][0], p.kb, shapes[si][1], kbs, s, false) <= kSmemLimit) {
+                p.mt = shapes[si][0];
+                p.rb = shapes[si][1];
+                p.kbs = kbs;
                 p.stages = s;
                 break;
             }
@@ -464,7 +583,7 @@ TcPlan tc_plan(int64_t n, int64_t m, int32_t kp, int prec, int32_t c, int num_sm
     if (p.stages == 0) return p;   // operand rows too long for shared memory
     const int64_t qtiles = (n + kBlockM * p.mt - 1) / (kBlockM * p.mt);
     // reference splits: the fewest whose CTAs fill at least 85% of the last wave
-    int64_t max_s = m / (16 * kBlockN);
+    int64_t max_s = m / (8 * p.rb);
     if (max_s < 1) max_s = 1;
     if (max_s > 64) max_s = 64;
     int S = 1;
@@ -477,19 +596,21 @@ TcPlan tc_plan(int64_t n, int64_t m, int32_t kp, int prec, int32_t c, int num_sm
         if (eff >= 0.85) break;
     }
     int64_t chunk = (m + S - 1) / S;
-    chunk = (chunk + kBlockN - 1) / kBlockN * kBlockN;
+    chunk = (chunk + p.rb - 1) / p.rb * p.rb;
     S = static_cast<int>((m + chunk - 1) / chunk);
     p.S = S;
     p.chunk = chunk;
-    // pilot sampling: every stride-th tile, at most ~1024 groups per query
-    const int64_t tiles_total = (m + kBlockN - 1) / kBlockN;
-    int stride = 16;
-    while (tiles_total * 4 / stride > 1024) stride *= 2;
-    const int tps = static_cast<int>(chunk / kBlockN);
+    // pilot sampling: every stride-th stage, at most ~1024 groups per query
+    const int gps = p.rb / 32;                     // groups of 32 references per stage
+    const int64_t stages_total = (m + p.rb - 1) / p.rb;
+    int stride = 2048 / p.rb;                      // one stage in 16 tiles of 128
+    while (stages_total * gps / stride > 1024) stride *= 2;
+    const int sps = static_cast<int>(chunk / p.rb);
     p.stride = stride;
-    p.spt = (tps + stride - 1) / stride;
-    p.G = S * p.spt * 4;
-    const double lambda = static_cast<double>(c) / stride;
+    p.spt = (sps + stride - 1) / stride;
+    p.G = S * p.spt * gps;
+    const double frac = static_cast<double>(p.rb) / (static_cast<double>(stride) * p.rb);
+    const double lambda = static_cast<double>(c) * frac;
     p.cprime = static_cast<int>(std::ceil(lambda + 6.0 * std::sqrt(lambda) + 4.0));
     p.pilot = (p.G >= 2 * p.cprime) ? 1 : 0;
     if (p.pilot) {
@@ -499,7 +620,7 @@ TcPlan tc_plan(int64_t n, int64_t m, int32_t kp, int prec, int32_t c, int num_sm
     } else {
         p.cap = static_cast<int32_t>(chunk);
     }
-    p.smem_filter = tc_smem_bytes(p.mt, p.kb, p.stages, false);
+    p.smem_filter = tc_smem_bytes(p.mt, p.kb, p.rb, p.kbs, p.stages, false);
     return p;
 }
 
@@ -525,7 +646,7 @@ cudaError_t launch_tc_pilot(const TcPlan& p, const void* Q_lp, int64_t n, const 
                             int32_t kp, int prec, uint32_t* gmax, int32_t* error_flag, cudaStream_t st,
                             int* launches) {
     CUtensorMap mq, mr;
-    if (!make_map(&mq, Q_lp, n, kp, prec) || !make_map(&mr, R_lp, m, kp, prec))
+    if (!make_map(&mq, Q_lp, n, kp, prec, kBlockM, 0) || !make_map(&mr, R_lp, m, kp, prec, p.rb, p.kbs))
         return cudaErrorInvalidValue;
     cudaError_t err = cudaMemsetAsync(gmax, 0, static_cast<size_t>(n) * p.G * 4, st);
     if (err != cudaSuccess) return err;
@@ -552,7 +673,7 @@ cudaError_t launch_tc_filter(const TcPlan& p, const void* Q_lp, int64_t n, const
                              int32_t kp, int prec, uint64_t* lists, int32_t* counts,
                              int32_t* error_flag, cudaStream_t st, int* launches) {
     CUtensorMap mq, mr;
-    if (!make_map(&mq, Q_lp, n, kp, prec) || !make_map(&mr, R_lp, m, kp, prec))
+    if (!make_map(&mq, Q_lp, n, kp, prec, kBlockM, 0) || !make_map(&mr, R_lp, m, kp, prec, p.rb, p.kbs))
         return cudaErrorInvalidValue;
     TcArgs a = base_args(p, n, m, error_flag);
     a.stride = 1;
