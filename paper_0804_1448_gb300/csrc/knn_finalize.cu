@@ -83,10 +83,11 @@ __device__ __forceinline__ double bitsd(uint64_t b) {
 }
 
 // True when b (>= a) is within the float32 rounding of a, i.e. the exact
-// order of the two can differ from their float32 order.
-__device__ __forceinline__ bool near_tie(float a, float b, double rel) {
-    return static_cast<double>(b) - static_cast<double>(a) <=
-           2.0 * rel * static_cast<double>(b) + 1e-37;
+// order of the two can differ from their float32 order.  Evaluated in float:
+// b - a is exact when a <= b <= 2a (and only larger otherwise), and relf
+// carries a 1% margin over 2 * rel for the rounding of relf * b.
+__device__ __forceinline__ bool near_tie(float a, float b, float relf) {
+    return b - a <= relf * b + 1e-37f;
 }
 
 // Per-warp shared scratch of the finalize kernel.
@@ -403,6 +404,7 @@ __global__ void finalize_kernel(FinalizeArgs a, int P, int warps_per_block) {
     // 2. ascending prefix by repeated minimum: the first k, continued through
     //    the near-tie run holding position k-1
     const double rel = f32_rel_bound(d);
+    const float relf = static_cast<float>(2.02 * rel);
     uint64_t lmin;
     int lpos;
     local_min(w.keys, pool, lane, &lmin, &lpos);
@@ -415,7 +417,7 @@ __global__ void finalize_kernel(FinalizeArgs a, int P, int warps_per_block) {
         const uint32_t mlo = __reduce_min_sync(0xffffffffu, lo);
         const uint64_t win = (static_cast<uint64_t>(mhi) << 32) | mlo;
         if (win == kEmptyKey) break;
-        if (L >= k && !near_tie(key_dist(prev), key_dist(win), rel)) break;
+        if (L >= k && !near_tie(key_dist(prev), key_dist(win), relf)) break;
         if (lane == 0) w.sorted[L] = win;
         if (lmin == win) {                 // owner: take it, rescan
             w.keys[lpos] = kEmptyKey;
@@ -430,7 +432,7 @@ __global__ void finalize_kernel(FinalizeArgs a, int P, int warps_per_block) {
     // 3. float64 re-check of near-tie runs inside the prefix
     bool any_tie = false;
     for (int p = 1 + lane; p < L; p += 32)
-        any_tie |= near_tie(key_dist(w.sorted[p - 1]), key_dist(w.sorted[p]), rel);
+        any_tie |= near_tie(key_dist(w.sorted[p - 1]), key_dist(w.sorted[p]), relf);
     any_tie = __any_sync(0xffffffffu, any_tie);
     for (int p = lane; p < L; p += 32) w.runs[p] = -1;
     __syncwarp();
@@ -439,7 +441,7 @@ __global__ void finalize_kernel(FinalizeArgs a, int P, int warps_per_block) {
             int p = 0;
             while (p < L) {
                 int e = p;
-                while (e + 1 < L && near_tie(key_dist(w.sorted[e]), key_dist(w.sorted[e + 1]), rel)) ++e;
+                while (e + 1 < L && near_tie(key_dist(w.sorted[e]), key_dist(w.sorted[e + 1]), relf)) ++e;
                 if (e > p)
                     for (int x = p; x <= e; ++x) { w.runs[x] = p; w.rend[x] = e; }
                 p = e + 1;

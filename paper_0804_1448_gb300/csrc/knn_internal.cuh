@@ -74,9 +74,10 @@ struct CandidateSet {
                       //    (completeness can be certified); 0: ranking scores
 };
 
-// Per-(query, split) lists of references that passed the tensor-core filter;
-// keys rank by the low-precision score (smaller key = nearer).  counts may
-// exceed cap, meaning the list overflowed.
+// Per-query lists of references that passed the tensor-core filter (S lists
+// per query: one per reference split and epilogue half); keys rank by the
+// low-precision score (smaller key = nearer).  counts may exceed cap, meaning
+// the list overflowed.
 struct HitLists {
     const uint64_t* keys;   // [n][S][cap]
     const int32_t* counts;  // [n][S]
@@ -137,6 +138,7 @@ struct TcPlan {
     int32_t ksteps;      // 32-byte MMA K steps that carry data
     int32_t rb;          // references per TMA stage (128 or 256)
     int32_t kbs;         // K blocks per TMA stage (kb, or 1 for long rows)
+    int32_t stage_half;  // stage hit values per 16-element half slice (less shared memory)
     int32_t stages;      // reference-stage ring depth
     int32_t S;           // reference splits
     int64_t chunk;       // references per split (multiple of rb)
@@ -145,7 +147,7 @@ struct TcPlan {
     int32_t G;           // pilot group maxima per query
     int32_t cprime;      // order statistic of the group maxima used as threshold
     int32_t pilot;       // 0: no pilot, every reference is appended
-    int32_t cap;         // list capacity per (query, split)
+    int32_t cap;         // list capacity per (query, split, epilogue half)
     size_t smem_filter;
 };
 TcPlan tc_plan(int64_t n, int64_t m, int32_t d, int32_t kp, int prec, int32_t c, int num_sms);

@@ -53,6 +53,11 @@ constexpr int kTileBytes = kBlockM * kAtomBytes;   // one 128-byte K block of 12
 constexpr int kMaxStages = 12;
 constexpr size_t kSmemLimit = 232448;
 constexpr int kAugCols = 4;
+// Floats per thread in the hit-staging area: a whole 32-value slice + pad, or
+// (when shared memory is short) 16 values + pad; either stride keeps eight
+// lanes' 16-byte stores on distinct banks.
+constexpr int kStageFull = 36;
+constexpr int kStageHalf = 20;
 
 struct TcArgs {
     int64_t n, m;
@@ -67,20 +72,32 @@ struct TcArgs {
     int32_t spt;          // pilot: sampled-stage slots per split
     int32_t G;            // pilot: group maxima per query (S * spt * rb / 32)
     uint32_t* gmax;       // pilot: [n][G] order-mapped maxima, 0 = no group
-    uint64_t* lists;      // filter: [n][S][cap]
-    int32_t* counts;      // filter: [n][S] (may exceed cap: overflow)
+    uint64_t* lists;      // filter: [n][S][2][cap], one list per epilogue half
+    int32_t* counts;      // filter: [n][S][2] (may exceed cap: overflow)
     int32_t cap;
     int32_t append_all;   // filter: every valid reference passes
+    int32_t stage_half;   // filter: stage hit values per 16-element half slice
     int32_t* error_flag;
 };
 
 // A: mt query tiles of kb K blocks (resident); B: a ring of `stages` boxes of
 // rb references x kbs K blocks; staging of hit values (filter only).
 __host__ __device__ constexpr size_t tc_smem_bytes(int mt, int kb, int rb, int kbs, int stages,
-                                                   bool pilot) {
+                                                   bool pilot, bool half_stage = false) {
     return 1024 + static_cast<size_t>(kTileBytes) * mt * kb +
            static_cast<size_t>(rb) * kAtomBytes * kbs * stages +
-           (pilot ? 0 : static_cast<size_t>(256) * mt * 32 * 4 + 128 * mt * 4) + 512;
+           (pilot ? 0 : static_cast<size_t>(256) * mt * (half_stage ? kStageHalf : kStageFull) * 4) +
+           512;
+}
+
+// Append one passing reference to a hit list.  key = (order of -acc, index):
+// a threshold pass has acc >= +0, so the order of -acc is ~bits(acc) without
+// its sign bit; without a threshold acc may have either sign.
+__device__ __forceinline__ void append(uint64_t* list, int& cnt, int cap, uint32_t vb, uint32_t j,
+                                       int append_all) {
+    const uint32_t o = append_all ? ord_f32(-__uint_as_float(vb)) : (~vb & 0x7fffffffu);
+    if (cnt < cap) list[cnt] = (static_cast<uint64_t>(o) << 32) | j;
+    ++cnt;
 }
 
 // MMAs of one 128-byte K block of one reference tile for all MT query tiles.
@@ -120,8 +137,8 @@ tc_kernel(const __grid_constant__ CUtensorMap tmap_q, const __grid_constant__ CU
     unsigned char* sA = smem;
     unsigned char* sB = sA + static_cast<size_t>(MT) * KB * kTileBytes;
     float* stage = reinterpret_cast<float*>(sB + NST * stage_bytes);
-    int* row_cnt = reinterpret_cast<int*>(stage + (PILOT ? 0 : kEpi * 32));   // [128*MT]
-    uint64_t* bars = reinterpret_cast<uint64_t*>(row_cnt + (PILOT ? 0 : 128 * MT));
+    const int stride_st = a.stage_half ? kStageHalf : kStageFull;
+    uint64_t* bars = reinterpret_cast<uint64_t*>(stage + (PILOT ? 0 : kEpi * stride_st));
     uint64_t* full = bars;
     uint64_t* empty = bars + kMaxStages;
     uint64_t* a_full = bars + 2 * kMaxStages;
@@ -264,16 +281,14 @@ tc_kernel(const __grid_constant__ CUtensorMap tmap_q, const __grid_constant__ CU
         const int64_t q = q0 + mt * kBlockM + row;
         const bool active = q < a.n;
         const uint32_t lane_addr = tmem + (static_cast<uint32_t>(quarter * 32) << 16);
-        float* st = stage + et * 32;
-        const int sw = et & 7;                      // bank swizzle of this thread's slot
+        float* st = stage + et * stride_st;
         const int gpt = RB / 32;                    // groups of 32 references per stage
         uint64_t* list = nullptr;
         uint32_t* gout = nullptr;
         if (PILOT) gout = a.gmax + q * a.G + static_cast<int64_t>(split) * a.spt * gpt;
-        else list = a.lists + (q * a.S + split) * static_cast<int64_t>(a.cap);
-        int* rcnt = row_cnt + mt * kBlockM + row;   // hits of this row (both halves)
-        if (!PILOT && half == 0) *rcnt = 0;
-        named_bar_sync(1, kEpi);
+        // each half-warp owns its own list: (query, split, half)
+        else list = a.lists + ((q * a.S + split) * 2 + half) * static_cast<int64_t>(a.cap);
+        int cnt = 0;
         for (int i = 0; i < nt; ++i) {
             const int buf = i & 1, g = i / TPS, t2 = i % TPS;
             const bool ok = mbar_wait(&t_full[buf], (i >> 1) & 1, abort_flag);
@@ -318,31 +333,50 @@ tc_kernel(const __grid_constant__ CUtensorMap tmap_q, const __grid_constant__ CU
 #pragma unroll
                         for (int h = 0; h < 4; ++h) m4[h] = __funnelshift_l(r[8 * h + u], m4[h], 1);
                     const uint32_t sm = (m4[0] << 24) | (m4[1] << 16) | (m4[2] << 8) | m4[3];
-                    // a pass is acc >= 0
-                    uint32_t hits = a.append_all ? 0xffffffffu : ~sm;
-                    hits &= nvalid == 0 ? 0u : (0xffffffffu << (32 - nvalid));
+                    // a pass is acc >= 0; bit u of `hits` is element u after the reversal
+                    uint32_t hits = __brev(a.append_all ? 0xffffffffu : ~sm);
+                    hits &= nvalid >= 32 ? 0xffffffffu : ((1u << nvalid) - 1u);
                     if (!active) hits = 0;
-                    if (hits) {
+                    // the append loop reads the hit values with a dynamic index, which
+                    // registers do not allow: they go through shared memory first
+                    if (!a.stage_half) {
+                        if (hits) {
 #pragma unroll
-                        for (int h = 0; h < 8; ++h)
-                            reinterpret_cast<uint4*>(st)[h ^ sw] =
-                                make_uint4(r[4 * h], r[4 * h + 1], r[4 * h + 2], r[4 * h + 3]);
-                        while (hits) {
-                            const int u = __clz(hits);
-                            hits &= ~(0x80000000u >> u);
-                            const float v = st[(((u >> 2) ^ sw) << 2) | (u & 3)];
-                            const int slot = atomicAdd(rcnt, 1);
-                            if (slot < a.cap) list[slot] = make_key(-v, static_cast<uint32_t>(j0 + u));
+                            for (int h = 0; h < 8; ++h)
+                                reinterpret_cast<uint4*>(st)[h] =
+                                    make_uint4(r[4 * h], r[4 * h + 1], r[4 * h + 2], r[4 * h + 3]);
+                            const uint32_t jb = static_cast<uint32_t>(j0);
+                            do {
+                                const int u = __ffs(hits) - 1;
+                                hits &= hits - 1;
+                                append(list, cnt, a.cap, __float_as_uint(st[u]), jb + u, a.append_all);
+                            } while (hits);
+                        }
+                    } else {
+#pragma unroll
+                        for (int hf = 0; hf < 2; ++hf) {
+                            uint32_t hh = (hits >> (16 * hf)) & 0xffffu;
+                            if (hh) {
+#pragma unroll
+                                for (int h = 0; h < 4; ++h)
+                                    reinterpret_cast<uint4*>(st)[h] =
+                                        make_uint4(r[16 * hf + 4 * h], r[16 * hf + 4 * h + 1],
+                                                   r[16 * hf + 4 * h + 2], r[16 * hf + 4 * h + 3]);
+                                const uint32_t jb = static_cast<uint32_t>(j0) + 16 * hf;
+                                do {
+                                    const int u = __ffs(hh) - 1;
+                                    hh &= hh - 1;
+                                    append(list, cnt, a.cap, __float_as_uint(st[u]), jb + u,
+                                           a.append_all);
+                                } while (hh);
+                            }
                         }
                     }
                     __syncwarp();
                 }
             }
         }
-        if (!PILOT) {
-            named_bar_sync(1, kEpi);
-            if (active && half == 0) a.counts[q * a.S + split] = *rcnt;
-        }
+        if (!PILOT && active) a.counts[(q * a.S + split) * 2 + half] = cnt;
     }
     tc_fence_before();
     __syncthreads();
@@ -491,7 +525,7 @@ template <int PREC, int MT, bool PILOT, int KBT>
 cudaError_t launch_kernel(const TcPlan& p, const CUtensorMap& mq, const CUtensorMap& mr,
                           const TcArgs& a, cudaStream_t st) {
     auto kern = tc_kernel<PREC, MT, PILOT, KBT>;
-    const size_t smem = tc_smem_bytes(MT, p.kb, p.rb, p.kbs, p.stages, PILOT);
+    const size_t smem = tc_smem_bytes(MT, p.kb, p.rb, p.kbs, p.stages, PILOT, p.stage_half != 0);
     cudaError_t err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                            static_cast<int>(smem));
     if (err != cudaSuccess) return err;
@@ -542,6 +576,7 @@ TcArgs base_args(const TcPlan& p, int64_t n, int64_t m, int32_t* error_flag) {
     a.G = p.G;
     a.cap = p.cap;
     a.append_all = p.pilot ? 0 : 1;
+    a.stage_half = p.stage_half;
     a.error_flag = error_flag;
     return a;
 }
@@ -562,19 +597,23 @@ TcPlan tc_plan(int64_t n, int64_t m, int32_t d, int32_t kp, int prec, int32_t c,
     p.stages = 0;
     // prefer two query tiles per CTA and whole-K 256-reference stages, then
     // shrink; single-K-block stages (more TMA boxes) only when rows are long
-    const int shapes[6][3] = {{2, 256, 0}, {2, 128, 0}, {1, 256, 0}, {1, 128, 0}, {2, 128, 1},
-                              {1, 128, 1}};
+    // {query tiles, references per stage, one K block per stage, half-slice staging}
+    const int shapes[10][4] = {{2, 256, 0, 0}, {2, 128, 0, 0}, {1, 256, 0, 0}, {1, 128, 0, 0},
+                               {2, 128, 0, 1}, {1, 128, 0, 1}, {2, 128, 1, 0}, {1, 128, 1, 0},
+                               {2, 128, 1, 1}, {1, 128, 1, 1}};
     // whole-K 256-reference stages need a third stage to hide the TMA latency;
     // with 128-reference stages two boxes per tile pair are already in flight
-    for (int si = 0; si < 6 && p.stages == 0; ++si) {
+    for (int si = 0; si < 10 && p.stages == 0; ++si) {
         const int kbs = shapes[si][2] ? 1 : p.kb;
         const int smax = shapes[si][2] ? 12 : kMaxStages;
         const int smin = (!shapes[si][2] && shapes[si][1] == 256) ? 3 : 2;
         for (int s = smax; s >= smin; --s) {
-            if (tc_smem_bytes(shapes[si][0], p.kb, shapes[si][1], kbs, s, false) <= kSmemLimit) {
+            if (tc_smem_bytes(shapes[si][0], p.kb, shapes[si][1], kbs, s, false, shapes[si][3] != 0) <=
+                kSmemLimit) {
                 p.mt = shapes[si][0];
                 p.rb = shapes[si][1];
                 p.kbs = kbs;
+                p.stage_half = shapes[si][3];
                 p.stages = s;
                 break;
             }
@@ -613,14 +652,15 @@ TcPlan tc_plan(int64_t n, int64_t m, int32_t d, int32_t kp, int prec, int32_t c,
     const double lambda = static_cast<double>(c) * frac;
     p.cprime = static_cast<int>(std::ceil(lambda + 6.0 * std::sqrt(lambda) + 4.0));
     p.pilot = (p.G >= 2 * p.cprime) ? 1 : 0;
+    // list capacity per (query, split, half): twice the expected hits plus slack
     if (p.pilot) {
         const int64_t expect = static_cast<int64_t>(p.cprime) * stride;
-        int64_t cap = (2 * expect + 255) / S + 128;
+        int64_t cap = (2 * expect + 255) / (2 * S) + 96;
         p.cap = static_cast<int32_t>((cap + 31) / 32 * 32);
     } else {
-        p.cap = static_cast<int32_t>(chunk);
+        p.cap = static_cast<int32_t>(chunk / 2);
     }
-    p.smem_filter = tc_smem_bytes(p.mt, p.kb, p.rb, p.kbs, p.stages, false);
+    p.smem_filter = tc_smem_bytes(p.mt, p.kb, p.rb, p.kbs, p.stages, false, p.stage_half != 0);
     return p;
 }
 
