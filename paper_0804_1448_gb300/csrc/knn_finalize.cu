@@ -107,24 +107,28 @@ constexpr int kBins = 64;
 
 __host__ __device__ constexpr size_t align16(size_t x) { return (x + 15) & ~static_cast<size_t>(15); }
 
-// Layout (every array starts 16-byte aligned): keys, sorted, d64 [P] u64;
-// smax [S] u64; perm, runs, rend [P] i32; hist [kBins+4] i32; qrow [d+4] f32.
-__host__ __device__ inline size_t warp_scratch_bytes(int P, int S, int d) {
-    return align16(static_cast<size_t>(P) * 8) * 3 + align16(static_cast<size_t>(S) * 8) +
-           align16(static_cast<size_t>(P) * 4) * 3 +
+// Layout (every array starts 16-byte aligned): keys [P] u64; sorted, d64
+// [L] u64; smax [S] u64; perm, runs, rend [L] i32; hist [kBins+4] i32;
+// qrow [d+4] f32.  L bounds the sorted prefix (the first k and the near-tie
+// run that crosses position k-1).
+__host__ __device__ inline size_t warp_scratch_bytes(int P, int L, int S, int d) {
+    return align16(static_cast<size_t>(P) * 8) + align16(static_cast<size_t>(L) * 8) * 2 +
+           align16(static_cast<size_t>(S) * 8) + align16(static_cast<size_t>(L) * 4) * 3 +
            align16((kBins + 4) * 4) + align16((static_cast<size_t>(d) + 4) * 4);
 }
 
-__device__ __forceinline__ WarpScratch carve(unsigned char* base, int P, int S) {
+__host__ __device__ inline int prefix_cap(int P, int k) { return P < k + 64 ? P : k + 64; }
+
+__device__ __forceinline__ WarpScratch carve(unsigned char* base, int P, int L, int S) {
     WarpScratch w;
     size_t o = 0;
     w.keys = reinterpret_cast<uint64_t*>(base + o);   o += align16(static_cast<size_t>(P) * 8);
-    w.sorted = reinterpret_cast<uint64_t*>(base + o); o += align16(static_cast<size_t>(P) * 8);
-    w.d64 = reinterpret_cast<uint64_t*>(base + o);    o += align16(static_cast<size_t>(P) * 8);
+    w.sorted = reinterpret_cast<uint64_t*>(base + o); o += align16(static_cast<size_t>(L) * 8);
+    w.d64 = reinterpret_cast<uint64_t*>(base + o);    o += align16(static_cast<size_t>(L) * 8);
     w.smax = reinterpret_cast<uint64_t*>(base + o);   o += align16(static_cast<size_t>(S) * 8);
-    w.perm = reinterpret_cast<int32_t*>(base + o);    o += align16(static_cast<size_t>(P) * 4);
-    w.runs = reinterpret_cast<int32_t*>(base + o);    o += align16(static_cast<size_t>(P) * 4);
-    w.rend = reinterpret_cast<int32_t*>(base + o);    o += align16(static_cast<size_t>(P) * 4);
+    w.perm = reinterpret_cast<int32_t*>(base + o);    o += align16(static_cast<size_t>(L) * 4);
+    w.runs = reinterpret_cast<int32_t*>(base + o);    o += align16(static_cast<size_t>(L) * 4);
+    w.rend = reinterpret_cast<int32_t*>(base + o);    o += align16(static_cast<size_t>(L) * 4);
     w.hist = reinterpret_cast<int32_t*>(base + o);    o += align16((kBins + 4) * 4);
     w.qrow = reinterpret_cast<float*>(base + o);
     return w;
@@ -141,29 +145,42 @@ __device__ void exact_keys(uint64_t* keys, int cnt, const FinalizeArgs& a, const
     if ((d & 3) == 0) {
         const int g = lane >> 3, sub = lane & 7, d4 = d >> 2;
         const float4* q4 = reinterpret_cast<const float4*>(qrow);
-        for (int e0 = 0; e0 < cnt; e0 += 4) {
-            const int e = e0 + g;
-            const uint64_t raw = (e < cnt) ? keys[e] : kEmptyKey;
-            float acc = 0.f;
-            if (raw != kEmptyKey) {
-                const float4* r4 =
-                    reinterpret_cast<const float4*>(a.R + static_cast<int64_t>(raw) * d);
-                for (int t = sub; t < d4; t += 8) {
-                    const float4 x = __ldg(r4 + t);
-                    const float4 y = q4[t];
+        constexpr int kGroups = 3;   // candidates in flight per lane group: loads issue together
+        for (int e0 = 0; e0 < cnt; e0 += 4 * kGroups) {
+            uint64_t raw[kGroups];
+            float acc[kGroups];
+#pragma unroll
+            for (int u = 0; u < kGroups; ++u) {
+                const int e = e0 + 4 * u + g;
+                raw[u] = (e < cnt) ? keys[e] : kEmptyKey;
+                acc[u] = 0.f;
+            }
+            for (int t = sub; t < d4; t += 8) {
+                const float4 y = q4[t];
+#pragma unroll
+                for (int u = 0; u < kGroups; ++u) {
+                    if (raw[u] == kEmptyKey) continue;
+                    const float4 x = __ldg(reinterpret_cast<const float4*>(
+                                               a.R + static_cast<int64_t>(raw[u]) * d) + t);
                     const float e0f = y.x - x.x, e1 = y.y - x.y, e2 = y.z - x.z, e3 = y.w - x.w;
                     if (METRIC == kL2) {
-                        acc = fmaf(e0f, e0f, acc); acc = fmaf(e1, e1, acc);
-                        acc = fmaf(e2, e2, acc); acc = fmaf(e3, e3, acc);
+                        acc[u] = fmaf(e0f, e0f, acc[u]); acc[u] = fmaf(e1, e1, acc[u]);
+                        acc[u] = fmaf(e2, e2, acc[u]); acc[u] = fmaf(e3, e3, acc[u]);
                     } else {
-                        acc += fabsf(e0f); acc += fabsf(e1); acc += fabsf(e2); acc += fabsf(e3);
+                        acc[u] += fabsf(e0f); acc[u] += fabsf(e1); acc[u] += fabsf(e2); acc[u] += fabsf(e3);
                     }
                 }
             }
-            acc += __shfl_xor_sync(0xffffffffu, acc, 4);
-            acc += __shfl_xor_sync(0xffffffffu, acc, 2);
-            acc += __shfl_xor_sync(0xffffffffu, acc, 1);
-            if (sub == 0 && raw != kEmptyKey) keys[e] = make_key(acc, static_cast<uint32_t>(raw));
+#pragma unroll
+            for (int u = 0; u < kGroups; ++u) {
+                float v = acc[u];
+                v += __shfl_xor_sync(0xffffffffu, v, 4);
+                v += __shfl_xor_sync(0xffffffffu, v, 2);
+                v += __shfl_xor_sync(0xffffffffu, v, 1);
+                const int e = e0 + 4 * u + g;
+                if (sub == 0 && raw[u] != kEmptyKey)
+                    keys[e] = make_key(v, static_cast<uint32_t>(raw[u]));
+            }
         }
     } else {
         for (int e = lane; e < cnt; e += 32) {
@@ -382,7 +399,8 @@ __global__ void finalize_kernel(FinalizeArgs a, int P, int warps_per_block) {
 
     const int S = a.use_hits ? 1 : a.cand.S;
     const int d = a.d, k = a.k;
-    WarpScratch w = carve(smem_raw + warp_scratch_bytes(P, S, d) * warp, P, S);
+    const int Lcap = prefix_cap(P, k);
+    WarpScratch w = carve(smem_raw + warp_scratch_bytes(P, Lcap, S, d) * warp, P, Lcap, S);
     for (int t = lane; t < d; t += 32) w.qrow[t] = a.Q[q * d + t];
     for (int s = lane; s < S; s += 32) w.smax[s] = 0;
     __syncwarp();
@@ -410,7 +428,8 @@ __global__ void finalize_kernel(FinalizeArgs a, int P, int warps_per_block) {
     local_min(w.keys, pool, lane, &lmin, &lpos);
     int L = 0;
     uint64_t prev = 0;
-    while (L < P) {
+    bool truncated = false;
+    while (true) {
         const uint32_t hi = static_cast<uint32_t>(lmin >> 32);
         const uint32_t mhi = __reduce_min_sync(0xffffffffu, hi);
         const uint32_t lo = (hi == mhi) ? static_cast<uint32_t>(lmin) : 0xffffffffu;
@@ -418,6 +437,7 @@ __global__ void finalize_kernel(FinalizeArgs a, int P, int warps_per_block) {
         const uint64_t win = (static_cast<uint64_t>(mhi) << 32) | mlo;
         if (win == kEmptyKey) break;
         if (L >= k && !near_tie(key_dist(prev), key_dist(win), relf)) break;
+        if (L == Lcap) { truncated = true; break; }   // run longer than the prefix holds
         if (lane == 0) w.sorted[L] = win;
         if (lmin == win) {                 // owner: take it, rescan
             w.keys[lpos] = kEmptyKey;
@@ -427,6 +447,10 @@ __global__ void finalize_kernel(FinalizeArgs a, int P, int warps_per_block) {
         ++L;
     }
     __syncwarp();
+    if (truncated) {
+        if (lane == 0) queue_fallback(a, q, 3);
+        return;
+    }
     const int kk = min(k, L);
 
     // 3. float64 re-check of near-tie runs inside the prefix
@@ -678,7 +702,7 @@ cudaError_t launch_finalize(const FinalizeArgs& a, cudaStream_t st, int* launche
     P = (P + 3) & ~3;
     if (P > kMaxPool) return cudaErrorInvalidValue;
     const size_t per_warp =
-        warp_scratch_bytes(P, a.use_hits ? 1 : a.cand.S, a.d);
+        warp_scratch_bytes(P, prefix_cap(P, a.k), a.use_hits ? 1 : a.cand.S, a.d);
     int wpb = static_cast<int>((96 * 1024) / per_warp);
     wpb = wpb < 1 ? 1 : (wpb > 8 ? 8 : wpb);
     const size_t smem = per_warp * wpb;
