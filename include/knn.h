@@ -168,6 +168,39 @@ knn_status knn_set_profiling(knn_handle h, int on);
 knn_status knn_get_profile(knn_handle h, float* ms, const char** names, int32_t cap,
                            int32_t* count);
 
+/*
+ * The float32 search of knn_search (distance from coordinate differences,
+ * float64 re-check of near ties, exact fallback) for callers that cannot
+ * allocate device memory when they search: code running while a CUDA graph is
+ * being captured (cudaMalloc is not a stream operation and breaks a
+ * global-mode capture), frameworks that route every device allocation through
+ * their own pool, and latency-critical paths that cannot take the device-wide
+ * synchronisation of cudaMalloc/cudaFree.  The paper has no counterpart: it
+ * describes the search, not its memory management.
+ *
+ * No handle and no allocation: R (m x d), Q (n x d), dist_out and idx_out
+ * (n x k) are device pointers on the current device, valid on cuda_stream
+ * (NULL = the legacy default stream); metric is KNN_L2 or KNN_L1; the results
+ * follow knn_search's conventions.  The call only enqueues work
+ * (asynchronous).  Intermediates live in one 32 MiB __device__ array that
+ * belongs to the library's device image, so every GPU that loads the library
+ * holds those 32 MiB until the process exits.
+ *
+ * The first call on a device looks the array's address up (once per device);
+ * make that first call before any stream capture.  Every call shares the
+ * array and leaves its contents there; calls that overlap on the GPU (on
+ * different streams, or from different threads) race and must be serialised
+ * by the caller.
+ *
+ * Errors: KNN_ERR_INVALID (bad argument, k > m), KNN_ERR_UNSUPPORTED when the
+ * problem needs more scratch than the array holds (about n * 8 * (k + max(8,
+ * k/4)) bytes of candidates plus m * 8 bytes for the exact fallback; e.g.
+ * n = m = 38400, d = 96, k = 20 fits) or k > KNN_K_MAX, KNN_ERR_CUDA.
+ */
+knn_status knn_search_static(const float* R, int64_t m, const float* Q, int64_t n, int32_t d,
+                             int32_t k, knn_metric metric, float* dist_out, int32_t* idx_out,
+                             void* cuda_stream);
+
 /* Release the handle and everything it owns.  NULL is accepted. */
 knn_status knn_destroy(knn_handle h);
 

@@ -63,6 +63,7 @@ _SIGS = {
     "knn_get_profile": (ctypes.c_int, [_H, ctypes.POINTER(ctypes.c_float),
                                        ctypes.POINTER(ctypes.c_char_p), _i32,
                                        ctypes.POINTER(_i32)]),
+    "knn_search_static": (ctypes.c_int, [_P, _i64, _P, _i64, _i32, _i32, ctypes.c_int, _P, _P, _P]),
     "knn_destroy": (ctypes.c_int, [_H]),
     "knn_status_string": (ctypes.c_char_p, [ctypes.c_int]),
     "knn_last_error": (ctypes.c_char_p, [_H]),
@@ -82,6 +83,7 @@ knn_set_precision = _lib.knn_set_precision
 knn_get_stats = _lib.knn_get_stats
 knn_set_profiling = _lib.knn_set_profiling
 knn_get_profile = _lib.knn_get_profile
+knn_search_static = _lib.knn_search_static
 knn_destroy = _lib.knn_destroy
 knn_status_string = _lib.knn_status_string
 knn_last_error = _lib.knn_last_error
