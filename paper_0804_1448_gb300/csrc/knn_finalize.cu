@@ -1,32 +1,42 @@
 // knn_finalize.cu -- per-query completion of the search, and the exact fallback.
 //
 // finalize (one warp per query):
-//   1. exact float32 distance of every candidate (differences, coordinate 0
-//      first: the same arithmetic as the CUDA-core select kernel), which is
-//      the "re-rank" of the tensor-core candidates;
-//   2. sort by (distance, index) -- step 2 of the brute-force algorithm of
-//      Sec. 2.1, restricted to the candidates;
-//   3. near-tie re-check: consecutive candidates whose float32 distances are
-//      closer than twice the float32 rounding bound can be out of exact order,
-//      so every such run that reaches the first k positions is recomputed in
-//      float64 (the oracle's arithmetic: widen, subtract, square or abs, add,
-//      coordinate 0 first, no fused multiply-add) and re-ordered by
-//      (float64 distance, index);
+//   1. candidates: the S*c keys of the select stage, or the tensor-core hit
+//      lists cut to (at least) the best c by their low-precision keys; then the
+//      exact float32 distance of every candidate (differences, as the CUDA-core
+//      select kernel computes them): the "re-rank";
+//   2. ascending prefix by (distance, index) -- step 2 of the brute-force
+//      algorithm of Sec. 2.1, restricted to the candidates: the first k, and
+//      the run of near-equal distances that crosses position k-1;
+//   3. near-tie re-check: consecutive prefix entries whose float32 distances
+//      are within twice the float32 rounding bound may be out of exact order.
+//      Every such run is re-evaluated as a float-float sum (error far below the
+//      float32 window); entries whose float-float values are still within that
+//      sum's own error bound of a run neighbour are recomputed in float64 with
+//      the oracle's arithmetic (widen, subtract, square or abs, add,
+//      coordinate 0 first, no fused multiply-add).  Each run is then ordered by
+//      (refined distance, index);
 //   4. completeness check (float32 candidates only): the references that are
 //      not candidates have float32 distances >= the largest key kept by their
 //      split; if that bound, lowered by the rounding bound, does not exceed the
-//      k-th exact distance, a non-candidate could still belong to the answer
-//      and the query is queued for the fallback instead of being written;
+//      k-th distance, a non-candidate could still belong to the answer and the
+//      query is queued for the fallback instead of being written;
 //   5. the k outputs (Euclidean: square root of the squared distance).
 //
-// fallback (one CTA per queued query): float64 distances to all m references,
-// exact radix selection of the k smallest (distance, index) pairs, sort, write.
+// fallback (one CTA per queued query): float32 distances to all m references,
+// the k-th by radix selection, float64 distances for every reference that
+// could still be in the answer, an exact radix selection, a sort, the outputs.
 #include "knn_internal.cuh"
 
 namespace knn {
 namespace {
 
 constexpr int kMaxPool = 4096;
+constexpr int kRegPool = 128;            // pools up to 4 x 32 keys: prefix selection in registers
+constexpr int kRegHits = 16;             // hit-list entries per lane held in registers
+constexpr int kStage = 32 * kRegHits;    // hit lists up to this length are staged in shared memory
+constexpr int kBins = 64;
+constexpr int kThreads = 256;
 
 // Relative rounding bound of the float32 distance (squared Euclidean or
 // Manhattan) accumulated over d coordinates with one rounding per difference
@@ -36,10 +46,20 @@ __device__ __forceinline__ double f32_rel_bound(int d) {
     return 2.0 * (d + 2) * 5.9604644775390625e-8;
 }
 
+// Relative error bound of the float-float distance below: the low word stays
+// below 4(d+2) 2^-24 of the sum and is rounded at most twice per term, so the
+// sum is within (d+2)^2 2^-45 of the exact one; the oracle's float64 sum is
+// within (d+2) 2^-53 of it.
+__device__ __forceinline__ double ff_rel_bound(int d) {
+    const double e = static_cast<double>(d + 2);
+    return e * e * 2.8421709430404007e-14 + e * 1.1102230246251565e-16;
+}
+
 template <int METRIC>
 __device__ __forceinline__ float dist_f32(const float* q, const float* __restrict__ r, int d) {
     float acc = 0.f;
-    if ((d & 3) == 0) {   // rows are 16-byte aligned: vector loads, same order of operations
+    if ((d & 3) == 0 && ((reinterpret_cast<uintptr_t>(r) | reinterpret_cast<uintptr_t>(q)) & 15) == 0) {
+        // 16-byte aligned rows: vector loads, same order of operations
         const float4* r4 = reinterpret_cast<const float4*>(r);
         const float4* q4 = reinterpret_cast<const float4*>(q);
         for (int t = 0; t < d / 4; ++t) {
@@ -75,6 +95,45 @@ __device__ __forceinline__ double dist_f64(const float* q, const float* __restri
     return acc;
 }
 
+// ---- float-float arithmetic (round to nearest, no contraction) -----------
+
+// s + e == a + b exactly (Knuth's two-sum).
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+    s = __fadd_rn(a, b);
+    const float bb = __fsub_rn(s, a);
+    e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+
+// (H, Lo) += the term of coordinate pair (x, y): (x - y)^2 or |x - y|.
+// x - y = s + e exactly; s^2 = p + (s^2 - p) exactly with one fused
+// multiply-add; the 2se cross term joins the low word, e^2 (<= 2^-48 s^2) is
+// dropped.
+template <int METRIC>
+__device__ __forceinline__ void ff_term(float& H, float& Lo, float x, float y) {
+    float s, e;
+    two_sum(x, -y, s, e);
+    float p, t;
+    if (METRIC == kL2) {
+        p = __fmul_rn(s, s);
+        t = fmaf(__fadd_rn(s, s), e, fmaf(s, s, -p));
+    } else {
+        const bool neg = s < 0.f;   // s == 0 only when x == y, and then e == 0
+        p = neg ? -s : s;
+        t = neg ? -e : e;
+    }
+    float hs, he;
+    two_sum(H, p, hs, he);
+    H = hs;
+    Lo = __fadd_rn(Lo, __fadd_rn(t, he));
+}
+
+__device__ __forceinline__ void ff_combine(float& H, float& Lo, float H2, float Lo2) {
+    float s, e;
+    two_sum(H, H2, s, e);
+    H = s;
+    Lo = __fadd_rn(Lo, __fadd_rn(Lo2, e));
+}
+
 __device__ __forceinline__ uint64_t dbits(double x) {
     return static_cast<uint64_t>(__double_as_longlong(x));
 }
@@ -90,89 +149,122 @@ __device__ __forceinline__ bool near_tie(float a, float b, float relf) {
     return b - a <= relf * b + 1e-37f;
 }
 
+__device__ __forceinline__ void cp_async8(void* smem, const void* gmem) {
+    const uint32_t s = static_cast<uint32_t>(__cvta_generic_to_shared(smem));
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() {
+    asm volatile("cp.async.wait_all;\n" ::: "memory");
+}
+
 // Per-warp shared scratch of the finalize kernel.
 struct WarpScratch {
-    uint64_t* keys;    // [P] candidates (float32 distance, index); kEmptyKey = none / taken
-    uint64_t* sorted;  // [P] ascending prefix, extracted from keys
-    uint64_t* d64;     // [P] float64 distance bits of re-checked prefix entries
-    int32_t* perm;     // [P] output position -> prefix position inside re-checked runs
-    int32_t* runs;     // [P] run start of a re-checked prefix entry, -1 otherwise
-    int32_t* rend;     // [P] run end (inclusive)
+    uint64_t* keys;    // [P] candidates: reference index, then exact float32 key; kEmptyKey = none
+    uint64_t* stage;   // [kStage] the query's hit-list entries (shares space with sorted..rlist)
+    uint64_t* sorted;  // [L] ascending prefix
+    uint64_t* d64;     // [L] refined distance (float64 bits) of re-checked prefix entries
+    int32_t* perm;     // [L] output position -> prefix position inside re-checked runs
+    int32_t* runs;     // [L] run start of a re-checked prefix entry, -1 otherwise
+    int32_t* rend;     // [L] run end (inclusive)
+    int32_t* rlist;    // [L] prefix positions of the re-checked entries
     uint64_t* smax;    // [S] largest select-stage key per split
     int32_t* hist;     // [kBins + 4]
     float* qrow;       // [d + 4], 16-byte aligned
 };
 
-constexpr int kBins = 64;
-
 __host__ __device__ constexpr size_t align16(size_t x) { return (x + 15) & ~static_cast<size_t>(15); }
 
-// Layout (every array starts 16-byte aligned): keys [P] u64; sorted, d64
-// [L] u64; smax [S] u64; perm, runs, rend [L] i32; hist [kBins+4] i32;
-// qrow [d+4] f32.  L bounds the sorted prefix (the first k and the near-tie
-// run that crosses position k-1).
-__host__ __device__ inline size_t warp_scratch_bytes(int P, int L, int S, int d) {
-    return align16(static_cast<size_t>(P) * 8) + align16(static_cast<size_t>(L) * 8) * 2 +
-           align16(static_cast<size_t>(S) * 8) + align16(static_cast<size_t>(L) * 4) * 3 +
-           align16((kBins + 4) * 4) + align16((static_cast<size_t>(d) + 4) * 4);
+// Layout (every array 16-byte aligned): keys [P] u64; then either the hit
+// staging area [kStage] u64 or, once it is consumed, sorted, d64 [L] u64 and
+// perm, runs, rend, rlist [L] i32; smax [S] u64; hist [kBins+4] i32; qrow
+// [d+4] f32.  L bounds the sorted prefix (the first k and the near-tie run
+// that crosses position k-1).
+__host__ __device__ inline size_t prefix_bytes(int L) {
+    return align16(static_cast<size_t>(L) * 8) * 2 + align16(static_cast<size_t>(L) * 4) * 4;
+}
+__host__ __device__ inline size_t warp_scratch_bytes(int P, int L, int S, int d, bool staged) {
+    const size_t u = prefix_bytes(L);
+    const size_t st = staged ? static_cast<size_t>(kStage) * 8 : 0;
+    return align16(static_cast<size_t>(P) * 8) + (u > st ? u : st) +
+           align16(static_cast<size_t>(S) * 8) + align16((kBins + 4) * 4) +
+           align16((static_cast<size_t>(d) + 4) * 4);
 }
 
 __host__ __device__ inline int prefix_cap(int P, int k) { return P < k + 64 ? P : k + 64; }
 
-__device__ __forceinline__ WarpScratch carve(unsigned char* base, int P, int L, int S) {
+__device__ __forceinline__ WarpScratch carve(unsigned char* base, int P, int L, int S, bool staged) {
     WarpScratch w;
     size_t o = 0;
     w.keys = reinterpret_cast<uint64_t*>(base + o);   o += align16(static_cast<size_t>(P) * 8);
+    const size_t u0 = o;
+    w.stage = reinterpret_cast<uint64_t*>(base + o);
     w.sorted = reinterpret_cast<uint64_t*>(base + o); o += align16(static_cast<size_t>(L) * 8);
     w.d64 = reinterpret_cast<uint64_t*>(base + o);    o += align16(static_cast<size_t>(L) * 8);
-    w.smax = reinterpret_cast<uint64_t*>(base + o);   o += align16(static_cast<size_t>(S) * 8);
     w.perm = reinterpret_cast<int32_t*>(base + o);    o += align16(static_cast<size_t>(L) * 4);
     w.runs = reinterpret_cast<int32_t*>(base + o);    o += align16(static_cast<size_t>(L) * 4);
     w.rend = reinterpret_cast<int32_t*>(base + o);    o += align16(static_cast<size_t>(L) * 4);
+    w.rlist = reinterpret_cast<int32_t*>(base + o);   o += align16(static_cast<size_t>(L) * 4);
+    const size_t st = staged ? static_cast<size_t>(kStage) * 8 : 0;
+    if (o < u0 + st) o = u0 + st;
+    w.smax = reinterpret_cast<uint64_t*>(base + o);   o += align16(static_cast<size_t>(S) * 8);
     w.hist = reinterpret_cast<int32_t*>(base + o);    o += align16((kBins + 4) * 4);
     w.qrow = reinterpret_cast<float*>(base + o);
     return w;
 }
 
 // Replace raw reference indices keys[0..cnt) (kEmptyKey = none) by exact
-// float32 keys.  With d % 4 == 0 eight lanes share one candidate: each loads
-// every eighth float4 of the row (coalesced 128-byte segments) and sums its
-// part; three shuffles finish the sum.  Otherwise one lane per candidate.
-template <int METRIC>
-__device__ void exact_keys(uint64_t* keys, int cnt, const FinalizeArgs& a, const float* qrow,
-                           int lane) {
-    const int d = a.d;
-    if ((d & 3) == 0) {
+// float32 keys.  NV > 0 (d % 4 == 0, d <= 128, NV = ceil(d/32)): eight lanes
+// share one candidate, lane `sub` taking float4 number sub + 8v (v < NV) of
+// the row, so one warp instruction reads four rows in 128-byte segments;
+// every lane issues the loads of G candidates before using any of them, and
+// three shuffles finish each sum.  NV == 0: one lane per candidate.
+template <int METRIC, int NV>
+__device__ void exact_keys(uint64_t* keys, int cnt, const float* __restrict__ R, int d,
+                           const float* qrow, int lane) {
+    if constexpr (NV > 0) {
+        constexpr int G = NV >= 3 ? 2 : (NV == 2 ? 3 : 4);
         const int g = lane >> 3, sub = lane & 7, d4 = d >> 2;
         const float4* q4 = reinterpret_cast<const float4*>(qrow);
-        constexpr int kGroups = 3;   // candidates in flight per lane group: loads issue together
-        for (int e0 = 0; e0 < cnt; e0 += 4 * kGroups) {
-            uint64_t raw[kGroups];
-            float acc[kGroups];
+        for (int e0 = 0; e0 < cnt; e0 += 4 * G) {
+            uint64_t raw[G];
+            float4 x[G][NV];
 #pragma unroll
-            for (int u = 0; u < kGroups; ++u) {
+            for (int u = 0; u < G; ++u) {
                 const int e = e0 + 4 * u + g;
                 raw[u] = (e < cnt) ? keys[e] : kEmptyKey;
-                acc[u] = 0.f;
-            }
-            for (int t = sub; t < d4; t += 8) {
-                const float4 y = q4[t];
+                const float4* row = reinterpret_cast<const float4*>(
+                    R + static_cast<int64_t>(raw[u] == kEmptyKey ? 0 : raw[u]) * d);
 #pragma unroll
-                for (int u = 0; u < kGroups; ++u) {
-                    if (raw[u] == kEmptyKey) continue;
-                    const float4 x = __ldg(reinterpret_cast<const float4*>(
-                                               a.R + static_cast<int64_t>(raw[u]) * d) + t);
-                    const float e0f = y.x - x.x, e1 = y.y - x.y, e2 = y.z - x.z, e3 = y.w - x.w;
-                    if (METRIC == kL2) {
-                        acc[u] = fmaf(e0f, e0f, acc[u]); acc[u] = fmaf(e1, e1, acc[u]);
-                        acc[u] = fmaf(e2, e2, acc[u]); acc[u] = fmaf(e3, e3, acc[u]);
-                    } else {
-                        acc[u] += fabsf(e0f); acc[u] += fabsf(e1); acc[u] += fabsf(e2); acc[u] += fabsf(e3);
+                for (int v = 0; v < NV; ++v) {
+                    const int t = sub + 8 * v;
+                    x[u][v] = (raw[u] != kEmptyKey && t < d4) ? __ldg(row + t)
+                                                              : make_float4(0.f, 0.f, 0.f, 0.f);
+                }
+            }
+            float acc[G];
+#pragma unroll
+            for (int u = 0; u < G; ++u) acc[u] = 0.f;
+#pragma unroll
+            for (int v = 0; v < NV; ++v) {
+                const int t = sub + 8 * v;
+                if (t < d4) {
+                    const float4 y = q4[t];
+#pragma unroll
+                    for (int u = 0; u < G; ++u) {
+                        const float4 r = x[u][v];
+                        const float e0f = y.x - r.x, e1 = y.y - r.y, e2 = y.z - r.z, e3 = y.w - r.w;
+                        if (METRIC == kL2) {
+                            acc[u] = fmaf(e0f, e0f, acc[u]); acc[u] = fmaf(e1, e1, acc[u]);
+                            acc[u] = fmaf(e2, e2, acc[u]); acc[u] = fmaf(e3, e3, acc[u]);
+                        } else {
+                            acc[u] += fabsf(e0f); acc[u] += fabsf(e1);
+                            acc[u] += fabsf(e2); acc[u] += fabsf(e3);
+                        }
                     }
                 }
             }
 #pragma unroll
-            for (int u = 0; u < kGroups; ++u) {
+            for (int u = 0; u < G; ++u) {
                 float v = acc[u];
                 v += __shfl_xor_sync(0xffffffffu, v, 4);
                 v += __shfl_xor_sync(0xffffffffu, v, 2);
@@ -186,8 +278,56 @@ __device__ void exact_keys(uint64_t* keys, int cnt, const FinalizeArgs& a, const
         for (int e = lane; e < cnt; e += 32) {
             const uint64_t raw = keys[e];
             if (raw != kEmptyKey)
-                keys[e] = make_key(dist_f32<METRIC>(qrow, a.R + static_cast<int64_t>(raw) * d, d),
+                keys[e] = make_key(dist_f32<METRIC>(qrow, R + static_cast<int64_t>(raw) * d, d),
                                    static_cast<uint32_t>(raw));
+        }
+    }
+    __syncwarp();
+}
+
+// Float-float distances of the prefix entries listed in rlist[0..nr), as
+// float64 bits in d64[position].  Same lane layout as exact_keys.
+template <int METRIC, int NV>
+__device__ void refine_ff(const WarpScratch& w, int nr, const float* __restrict__ R, int d, int lane) {
+    if constexpr (NV > 0) {
+        const int g = lane >> 3, sub = lane & 7, d4 = d >> 2;
+        const float4* q4 = reinterpret_cast<const float4*>(w.qrow);
+        for (int e0 = 0; e0 < nr; e0 += 4) {
+            const int e = e0 + g;
+            const int p = (e < nr) ? w.rlist[e] : -1;
+            float H = 0.f, Lo = 0.f;
+            if (p >= 0) {
+                const float4* row = reinterpret_cast<const float4*>(
+                    R + static_cast<int64_t>(key_idx(w.sorted[p])) * d);
+#pragma unroll
+                for (int v = 0; v < NV; ++v) {
+                    const int t = sub + 8 * v;
+                    if (t < d4) {
+                        const float4 r = __ldg(row + t);
+                        const float4 y = q4[t];
+                        ff_term<METRIC>(H, Lo, y.x, r.x);
+                        ff_term<METRIC>(H, Lo, y.y, r.y);
+                        ff_term<METRIC>(H, Lo, y.z, r.z);
+                        ff_term<METRIC>(H, Lo, y.w, r.w);
+                    }
+                }
+            }
+#pragma unroll
+            for (int o = 4; o > 0; o >>= 1) {
+                const float H2 = __shfl_xor_sync(0xffffffffu, H, o);
+                const float L2 = __shfl_xor_sync(0xffffffffu, Lo, o);
+                ff_combine(H, Lo, H2, L2);
+            }
+            if (sub == 0 && p >= 0)
+                w.d64[p] = dbits(static_cast<double>(H) + static_cast<double>(Lo));
+        }
+    } else {
+        for (int e = lane; e < nr; e += 32) {
+            const int p = w.rlist[e];
+            const float* r = R + static_cast<int64_t>(key_idx(w.sorted[p])) * d;
+            float H = 0.f, Lo = 0.f;
+            for (int t = 0; t < d; ++t) ff_term<METRIC>(H, Lo, w.qrow[t], __ldg(r + t));
+            w.d64[p] = dbits(static_cast<double>(H) + static_cast<double>(Lo));
         }
     }
     __syncwarp();
@@ -195,10 +335,10 @@ __device__ void exact_keys(uint64_t* keys, int cnt, const FinalizeArgs& a, const
 
 // Candidate-set front end: exact float32 keys of the S*c entries of query q,
 // and the largest select-stage key of every split.
-template <int METRIC>
+template <int METRIC, int NV>
 __device__ void gather_cand(const FinalizeArgs& a, int64_t q, WarpScratch& w, int lane) {
     const CandidateSet& cs = a.cand;
-    const int Sc = cs.S * cs.c, d = a.d;
+    const int Sc = cs.S * cs.c;
     const uint64_t* src = cs.keys + q * static_cast<int64_t>(Sc);
     for (int e = lane; e < Sc; e += 32) {
         const uint64_t key = src[e];
@@ -211,12 +351,10 @@ __device__ void gather_cand(const FinalizeArgs& a, int64_t q, WarpScratch& w, in
         w.keys[e] = raw;
     }
     __syncwarp();
-    exact_keys<METRIC>(w.keys, Sc, a, w.qrow, lane);
-    (void)d;
+    exact_keys<METRIC, NV>(w.keys, Sc, a.R, a.d, w.qrow, lane);
 }
 
-// Histogram over [lo, lo + kBins/inv) of the entries of the hit lists that
-// satisfy keep1 (first level: all; second level: those in bin b1 of level 1).
+// Histogram over [lo, lo + kBins/inv).
 struct Binning {
     float lo, inv;
     __device__ int bin(float v) const {
@@ -225,8 +363,8 @@ struct Binning {
     }
 };
 
-// Smallest bin whose cumulative count reaches `need` (counts summed with `base`),
-// and the cumulative count before it.  Two bins per lane.
+// Smallest bin whose cumulative count reaches `need`, and the cumulative
+// count before it.  Two bins per lane.
 __device__ void cut_bin(const int32_t* hist, int need, int lane, int* bin, int* before) {
     const int h0 = hist[2 * lane], h1 = hist[2 * lane + 1];
     int incl = h0 + h1;
@@ -245,56 +383,79 @@ __device__ void cut_bin(const int32_t* hist, int need, int lane, int* bin, int* 
     *before = own ? __shfl_sync(0xffffffffu, mb, __ffs(own) - 1) : 0;
 }
 
-constexpr int kRegHits = 16;   // hit-list entries held in registers per lane
+// Sizes of the query's hit lists: total entries and whether one overflowed.
+__device__ __forceinline__ void hit_totals(const FinalizeArgs& a, int64_t q, int lane, int* total,
+                                           int* over) {
+    const HitLists& hl = a.hits;
+    const int32_t* cnts = hl.counts + q * static_cast<int64_t>(hl.S);
+    int t = 0, o = 0;
+    for (int s = lane; s < hl.S; s += 32) {
+        const int cs = cnts[s];
+        o |= cs > hl.cap;
+        t += min(cs, hl.cap);
+    }
+    *total = __reduce_add_sync(0xffffffffu, t);
+    *over = __reduce_or_sync(0xffffffffu, o);
+}
 
 // Hit-list front end: keep the listed references whose low-precision key is
 // among the best c, cutting at a histogram bin (refined once), so at least c
 // and usually a few more are kept; their exact float32 keys go to w.keys.
 // Returns the number kept, or -1 (list shorter than c), -2 (overflowed),
 // -3 (the cut kept more than P) to send the query to the exact fallback.
-// Lists of up to 32*kRegHits entries are read once into registers; longer
-// ones are re-read from global memory at every pass.
-template <int METRIC, bool REG>
+// Lists of up to kStage entries are copied once into shared memory (8-byte
+// asynchronous copies, all in flight together) and their keys held in
+// registers; longer ones are re-read from global memory at every pass.
+template <int METRIC, int NV, bool STAGED>
 __device__ int gather_hits_impl(const FinalizeArgs& a, int64_t q, int P, WarpScratch& w, int lane,
                                 int total) {
     const HitLists& hl = a.hits;
     const int S = hl.S, cap = hl.cap, c = hl.c;
     const uint64_t* base = hl.keys + q * static_cast<int64_t>(S) * cap;
     const int32_t* cnts = hl.counts + q * static_cast<int64_t>(S);
-    uint64_t reg[REG ? kRegHits : 1];
-    if (REG) {
-        // entry e of the concatenated lists -> lane e % 32, slot e / 32
+    uint32_t hv[STAGED ? kRegHits : 1];   // high words of the staged keys (order of the score)
+    if constexpr (STAGED) {
         int o = 0;
-#pragma unroll
-        for (int i = 0; i < kRegHits; ++i) reg[i] = kEmptyKey;
-        for (int s = 0; s < S; ++s) {
-            const int cs = min(cnts[s], cap);
-            const uint64_t* sp = base + static_cast<int64_t>(s) * cap;
-#pragma unroll
-            for (int i = 0; i < kRegHits; ++i) {
-                const int e = i * 32 + lane - o;          // index into split s
-                if (e >= 0 && e < cs) reg[i] = sp[e];
+        for (int s0 = 0; s0 < S; s0 += 32) {
+            const int mine = (s0 + lane < S) ? min(cnts[s0 + lane], cap) : 0;
+            int incl = mine;
+            for (int sh = 1; sh < 32; sh <<= 1) {
+                const int v = __shfl_up_sync(0xffffffffu, incl, sh);
+                if (lane >= sh) incl += v;
             }
-            o += cs;
+            const int ns = min(32, S - s0);
+            for (int s = 0; s < ns; ++s) {
+                const int cs = __shfl_sync(0xffffffffu, mine, s);
+                const int os = o + __shfl_sync(0xffffffffu, incl, s) - cs;
+                const uint64_t* sp = base + static_cast<int64_t>(s0 + s) * cap;
+                for (int x = lane; x < cs; x += 32) cp_async8(w.stage + os + x, sp + x);
+            }
+            o += __shfl_sync(0xffffffffu, incl, 31);
+        }
+        cp_async_wait_all();
+        __syncwarp();
+#pragma unroll
+        for (int i = 0; i < kRegHits; ++i) {
+            const int e = i * 32 + lane;
+            hv[i] = (e < total) ? static_cast<uint32_t>(w.stage[e] >> 32) : 0u;
         }
     }
-    // visit every entry: f(key) for valid entries
+    // visit every entry: f(score) for the staged registers, or f(key) re-read
     auto for_each = [&](auto&& f) {
-        if (REG) {
+        if constexpr (STAGED) {
 #pragma unroll
             for (int i = 0; i < kRegHits; ++i)
-                if (reg[i] != kEmptyKey) f(reg[i]);
+                if (i * 32 + lane < total) f(unord_f32(hv[i]));
         } else {
             for (int s = 0; s < S; ++s) {
                 const int cs = min(cnts[s], cap);
                 const uint64_t* sp = base + static_cast<int64_t>(s) * cap;
-                for (int e = lane; e < cs; e += 32) f(sp[e]);
+                for (int e = lane; e < cs; e += 32) f(key_dist(sp[e]));
             }
         }
     };
     float vmin = __int_as_float(0x7f800000), vmax = -vmin;
-    for_each([&](uint64_t key) {
-        const float v = key_dist(key);
+    for_each([&](float v) {
         vmin = fminf(vmin, v);
         vmax = fmaxf(vmax, v);
     });
@@ -308,7 +469,7 @@ __device__ int gather_hits_impl(const FinalizeArgs& a, int64_t q, int P, WarpScr
     if (total > c) {
         for (int b = lane; b < kBins; b += 32) w.hist[b] = 0;
         __syncwarp();
-        for_each([&](uint64_t key) { atomicAdd(&w.hist[b1.bin(key_dist(key))], 1); });
+        for_each([&](float v) { atomicAdd(&w.hist[b1.bin(v)], 1); });
         __syncwarp();
         int before;
         cut_bin(w.hist, c, lane, &cut1, &before);
@@ -319,8 +480,7 @@ __device__ int gather_hits_impl(const FinalizeArgs& a, int64_t q, int P, WarpScr
             b2.inv = b1.inv * kBins;
             for (int b = lane; b < kBins; b += 32) w.hist[b] = 0;
             __syncwarp();
-            for_each([&](uint64_t key) {
-                const float v = key_dist(key);
+            for_each([&](float v) {
                 if (b1.bin(v) == cut1) atomicAdd(&w.hist[b2.bin(v)], 1);
             });
             __syncwarp();
@@ -329,46 +489,43 @@ __device__ int gather_hits_impl(const FinalizeArgs& a, int64_t q, int P, WarpScr
             __syncwarp();
         }
     }
-    auto keep = [&](uint64_t key) {
-        const float v = key_dist(key);
+    auto keep = [&](float v) {
         const int bb = b1.bin(v);
         return bb < cut1 || (bb == cut1 && (b2.inv == 0.f || b2.bin(v) <= cut2));
     };
-    // compact the kept indices into w.keys (shared-memory counter)
-    if (lane == 0) w.hist[kBins] = 0;
-    __syncwarp();
-    for_each([&](uint64_t key) {
-        if (keep(key)) {
-            const int pos = atomicAdd(&w.hist[kBins], 1);
-            if (pos < P) w.keys[pos] = key_idx(key);
+    int kept = 0;
+    if constexpr (STAGED) {
+        // compact the kept reference indices into w.keys in entry order (ballots)
+#pragma unroll
+        for (int i = 0; i < kRegHits; ++i) {
+            const int e = i * 32 + lane;
+            const bool take = e < total && keep(unord_f32(hv[i]));
+            const unsigned bal = __ballot_sync(0xffffffffu, take);
+            const int pos = kept + __popc(bal & ((1u << lane) - 1u));
+            if (take && pos < P) w.keys[pos] = static_cast<uint32_t>(w.stage[e]);
+            kept += __popc(bal);
         }
-    });
+    } else {
+        if (lane == 0) w.hist[kBins] = 0;
+        __syncwarp();
+        for (int s = 0; s < S; ++s) {
+            const int cs = min(cnts[s], cap);
+            const uint64_t* sp = base + static_cast<int64_t>(s) * cap;
+            for (int e = lane; e < cs; e += 32) {
+                const uint64_t key = sp[e];
+                if (keep(key_dist(key))) {
+                    const int pos = atomicAdd(&w.hist[kBins], 1);
+                    if (pos < P) w.keys[pos] = key_idx(key);
+                }
+            }
+        }
+        __syncwarp();
+        kept = w.hist[kBins];
+    }
     __syncwarp();
-    const int kept = w.hist[kBins];
     if (kept > P) return -3;
-    exact_keys<METRIC>(w.keys, kept, a, w.qrow, lane);
+    exact_keys<METRIC, NV>(w.keys, kept, a.R, a.d, w.qrow, lane);
     return kept;
-}
-
-template <int METRIC>
-__device__ int gather_hits(const FinalizeArgs& a, int64_t q, int P, WarpScratch& w, int lane) {
-    const HitLists& hl = a.hits;
-    const int S = hl.S, cap = hl.cap;
-    const int32_t* cnts = hl.counts + q * static_cast<int64_t>(S);
-    int total = 0, over = 0;
-    for (int s = lane; s < S; s += 32) {
-        const int cs = cnts[s];
-        over |= cs > cap;
-        total += min(cs, cap);
-    }
-    for (int o = 16; o > 0; o >>= 1) {
-        total += __shfl_xor_sync(0xffffffffu, total, o);
-        over |= __shfl_xor_sync(0xffffffffu, over, o);
-    }
-    if (over) return -2;
-    if (total < hl.c && total < a.m) return -1;
-    if (total <= 32 * kRegHits) return gather_hits_impl<METRIC, true>(a, q, P, w, lane, total);
-    return gather_hits_impl<METRIC, false>(a, q, P, w, lane, total);
 }
 
 __device__ __forceinline__ void local_min(const uint64_t* keys, int pool, int lane, uint64_t* lmin,
@@ -383,6 +540,20 @@ __device__ __forceinline__ void local_min(const uint64_t* keys, int pool, int la
     *lpos = at;
 }
 
+__device__ __forceinline__ uint64_t warp_min_key(uint64_t x) {
+    const uint32_t hi = static_cast<uint32_t>(x >> 32);
+    const uint32_t mhi = __reduce_min_sync(0xffffffffu, hi);
+    const uint32_t lo = (hi == mhi) ? static_cast<uint32_t>(x) : 0xffffffffu;
+    const uint32_t mlo = __reduce_min_sync(0xffffffffu, lo);
+    return (static_cast<uint64_t>(mhi) << 32) | mlo;
+}
+
+__device__ __forceinline__ void cswap(uint64_t& a, uint64_t& b) {
+    const uint64_t lo = a < b ? a : b, hi = a < b ? b : a;
+    a = lo;
+    b = hi;
+}
+
 __device__ __forceinline__ void queue_fallback(const FinalizeArgs& a, int64_t q, int reason) {
     const int pos = atomicAdd(a.fallback_count, 1);
     a.fallback_list[pos] = static_cast<int32_t>(q);
@@ -390,8 +561,9 @@ __device__ __forceinline__ void queue_fallback(const FinalizeArgs& a, int64_t q,
     if (a.fallback_reason) atomicAdd(&a.fallback_reason[reason], 1ull);
 }
 
-template <int METRIC>
-__global__ void finalize_kernel(FinalizeArgs a, int P, int warps_per_block) {
+template <int METRIC, int NV>
+__global__ void __launch_bounds__(kThreads, 4)
+finalize_kernel(FinalizeArgs a, int P, int warps_per_block) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
     const int64_t q = static_cast<int64_t>(blockIdx.x) * warps_per_block + warp;
@@ -400,8 +572,21 @@ __global__ void finalize_kernel(FinalizeArgs a, int P, int warps_per_block) {
     const int S = a.use_hits ? 1 : a.cand.S;
     const int d = a.d, k = a.k;
     const int Lcap = prefix_cap(P, k);
-    WarpScratch w = carve(smem_raw + warp_scratch_bytes(P, Lcap, S, d) * warp, P, Lcap, S);
-    for (int t = lane; t < d; t += 32) w.qrow[t] = a.Q[q * d + t];
+    const bool staged = a.use_hits != 0;
+    WarpScratch w = carve(smem_raw + warp_scratch_bytes(P, Lcap, S, d, staged) * warp, P, Lcap, S,
+                          staged);
+    // the query row: its loads are issued before the hit-list sizes are read
+    const float* qg = a.Q + q * d;
+    float4 qv = make_float4(0.f, 0.f, 0.f, 0.f);
+    const bool qvec = NV > 0 && (reinterpret_cast<uintptr_t>(a.Q) & 15) == 0;
+    if (qvec) {
+        if (lane < (d >> 2)) qv = __ldg(reinterpret_cast<const float4*>(qg) + lane);
+    } else {
+        for (int t = lane; t < d; t += 32) w.qrow[t] = qg[t];
+    }
+    int total = 0, over = 0;
+    if (a.use_hits) hit_totals(a, q, lane, &total, &over);
+    if (qvec && lane < (d >> 2)) reinterpret_cast<float4*>(w.qrow)[lane] = qv;
     for (int s = lane; s < S; s += 32) w.smax[s] = 0;
     __syncwarp();
 
@@ -409,9 +594,12 @@ __global__ void finalize_kernel(FinalizeArgs a, int P, int warps_per_block) {
     int pool;
     if (!a.use_hits) {
         pool = a.cand.S * a.cand.c;
-        gather_cand<METRIC>(a, q, w, lane);
+        gather_cand<METRIC, NV>(a, q, w, lane);
     } else {
-        pool = gather_hits<METRIC>(a, q, P, w, lane);
+        if (over) pool = -2;
+        else if (total < a.hits.c && total < a.m) pool = -1;
+        else if (total <= kStage) pool = gather_hits_impl<METRIC, NV, true>(a, q, P, w, lane, total);
+        else pool = gather_hits_impl<METRIC, NV, false>(a, q, P, w, lane, total);
         if (pool < 0) {
             if (lane == 0) queue_fallback(a, q, -pool - 1);
             return;
@@ -423,28 +611,50 @@ __global__ void finalize_kernel(FinalizeArgs a, int P, int warps_per_block) {
     //    the near-tie run holding position k-1
     const double rel = f32_rel_bound(d);
     const float relf = static_cast<float>(2.02 * rel);
-    uint64_t lmin;
-    int lpos;
-    local_min(w.keys, pool, lane, &lmin, &lpos);
     int L = 0;
     uint64_t prev = 0;
     bool truncated = false;
-    while (true) {
-        const uint32_t hi = static_cast<uint32_t>(lmin >> 32);
-        const uint32_t mhi = __reduce_min_sync(0xffffffffu, hi);
-        const uint32_t lo = (hi == mhi) ? static_cast<uint32_t>(lmin) : 0xffffffffu;
-        const uint32_t mlo = __reduce_min_sync(0xffffffffu, lo);
-        const uint64_t win = (static_cast<uint64_t>(mhi) << 32) | mlo;
-        if (win == kEmptyKey) break;
-        if (L >= k && !near_tie(key_dist(prev), key_dist(win), relf)) break;
-        if (L == Lcap) { truncated = true; break; }   // run longer than the prefix holds
-        if (lane == 0) w.sorted[L] = win;
-        if (lmin == win) {                 // owner: take it, rescan
-            w.keys[lpos] = kEmptyKey;
-            local_min(w.keys, pool, lane, &lmin, &lpos);
+    if (pool <= kRegPool) {
+        // four keys per lane, sorted in registers; the owner of each warp
+        // minimum shifts its next key up
+        uint64_t kr[4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            const int e = lane + 32 * i;
+            kr[i] = (e < pool) ? w.keys[e] : kEmptyKey;
         }
-        prev = win;
-        ++L;
+        cswap(kr[0], kr[1]); cswap(kr[2], kr[3]); cswap(kr[0], kr[2]);
+        cswap(kr[1], kr[3]); cswap(kr[1], kr[2]);
+        __syncwarp();
+        while (true) {
+            const uint64_t win = warp_min_key(kr[0]);
+            if (win == kEmptyKey) break;
+            if (L >= k && !near_tie(key_dist(prev), key_dist(win), relf)) break;
+            if (L == Lcap) { truncated = true; break; }   // run longer than the prefix holds
+            if (kr[0] == win) {
+                w.sorted[L] = win;
+                kr[0] = kr[1]; kr[1] = kr[2]; kr[2] = kr[3]; kr[3] = kEmptyKey;
+            }
+            prev = win;
+            ++L;
+        }
+    } else {
+        uint64_t lmin;
+        int lpos;
+        local_min(w.keys, pool, lane, &lmin, &lpos);
+        while (true) {
+            const uint64_t win = warp_min_key(lmin);
+            if (win == kEmptyKey) break;
+            if (L >= k && !near_tie(key_dist(prev), key_dist(win), relf)) break;
+            if (L == Lcap) { truncated = true; break; }
+            if (lmin == win) {                 // owner: take it, rescan
+                w.sorted[L] = win;
+                w.keys[lpos] = kEmptyKey;
+                local_min(w.keys, pool, lane, &lmin, &lpos);
+            }
+            prev = win;
+            ++L;
+        }
     }
     __syncwarp();
     if (truncated) {
@@ -453,31 +663,48 @@ __global__ void finalize_kernel(FinalizeArgs a, int P, int warps_per_block) {
     }
     const int kk = min(k, L);
 
-    // 3. float64 re-check of near-tie runs inside the prefix
+    // 3. re-check of near-tie runs inside the prefix
     bool any_tie = false;
     for (int p = 1 + lane; p < L; p += 32)
         any_tie |= near_tie(key_dist(w.sorted[p - 1]), key_dist(w.sorted[p]), relf);
     any_tie = __any_sync(0xffffffffu, any_tie);
     for (int p = lane; p < L; p += 32) w.runs[p] = -1;
     __syncwarp();
+    const double ffw = 2.5 * ff_rel_bound(d);
     if (any_tie) {
         if (lane == 0) {
-            int p = 0;
+            int p = 0, nr = 0;
             while (p < L) {
                 int e = p;
                 while (e + 1 < L && near_tie(key_dist(w.sorted[e]), key_dist(w.sorted[e + 1]), relf)) ++e;
                 if (e > p)
-                    for (int x = p; x <= e; ++x) { w.runs[x] = p; w.rend[x] = e; }
+                    for (int x = p; x <= e; ++x) { w.runs[x] = p; w.rend[x] = e; w.rlist[nr++] = x; }
                 p = e + 1;
+            }
+            w.hist[kBins + 1] = nr;
+        }
+        __syncwarp();
+        const int nr = w.hist[kBins + 1];
+        // tier 1: float-float distances of every run entry
+        refine_ff<METRIC, NV>(w, nr, a.R, d, lane);
+        // tier 2: float64 (oracle arithmetic) where float-float cannot separate
+        // an entry from a run neighbour
+        uint64_t mark = 0;
+        for (int p = lane, i = 0; p < L; p += 32, ++i) {
+            const int s0 = w.runs[p];
+            if (s0 < 0) continue;
+            const double vp = bitsd(w.d64[p]);
+            for (int x = s0; x <= w.rend[p]; ++x) {
+                if (x == p) continue;
+                const double vx = bitsd(w.d64[x]);
+                if (fabs(vx - vp) <= ffw * fmax(vx, vp) + 1e-300) { mark |= 1ull << i; break; }
             }
         }
         __syncwarp();
-        int nre = 0;
-        for (int p = lane; p < L; p += 32) {
-            if (w.runs[p] >= 0) {
+        for (int p = lane, i = 0; p < L; p += 32, ++i) {
+            if ((mark >> i) & 1ull) {
                 const uint32_t j = key_idx(w.sorted[p]);
                 w.d64[p] = dbits(dist_f64<METRIC>(w.qrow, a.R + static_cast<int64_t>(j) * d, d));
-                ++nre;
             }
         }
         __syncwarp();
@@ -496,9 +723,8 @@ __global__ void finalize_kernel(FinalizeArgs a, int P, int warps_per_block) {
             }
         }
         __syncwarp();
-        for (int o = 16; o > 0; o >>= 1) nre += __shfl_xor_sync(0xffffffffu, nre, o);
-        if (lane == 0 && nre > 0 && a.recheck_counter)
-            atomicAdd(a.recheck_counter, static_cast<unsigned long long>(nre));
+        if (lane == 0 && nr > 0 && a.recheck_counter)
+            atomicAdd(a.recheck_counter, static_cast<unsigned long long>(nr));
     }
     auto source_of = [&](int s) { return (w.runs[s] >= 0) ? w.perm[s] : s; };
 
@@ -520,7 +746,7 @@ __global__ void finalize_kernel(FinalizeArgs a, int P, int warps_per_block) {
         if (have) {
             const int sk = source_of(kk - 1);
             const double upper = (w.runs[kk - 1] >= 0)
-                                     ? bitsd(w.d64[sk])
+                                     ? bitsd(w.d64[sk]) * (1.0 + ffw)
                                      : static_cast<double>(key_dist(w.sorted[sk])) * (1.0 + rel);
             if (!(lower > upper) || kk < k) {
                 if (lane == 0) queue_fallback(a, q, 3);
@@ -697,32 +923,49 @@ fallback_kernel(FinalizeArgs a, double* __restrict__ scratch) {
 
 int finalize_max_pool() { return kMaxPool; }
 
+template <int METRIC, int NV>
+cudaError_t launch_finalize_nv(const FinalizeArgs& a, int P, int wpb, size_t smem, unsigned grid,
+                               cudaStream_t st) {
+    cudaError_t err = cudaFuncSetAttribute(finalize_kernel<METRIC, NV>,
+                                           cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                           static_cast<int>(smem));
+    if (err != cudaSuccess) return err;
+    finalize_kernel<METRIC, NV><<<grid, wpb * 32, smem, st>>>(a, P, wpb);
+    return cudaGetLastError();
+}
+
+template <int METRIC>
+cudaError_t launch_finalize_m(const FinalizeArgs& a, int nv, int P, int wpb, size_t smem,
+                              unsigned grid, cudaStream_t st) {
+    switch (nv) {
+        case 1: return launch_finalize_nv<METRIC, 1>(a, P, wpb, smem, grid, st);
+        case 2: return launch_finalize_nv<METRIC, 2>(a, P, wpb, smem, grid, st);
+        case 3: return launch_finalize_nv<METRIC, 3>(a, P, wpb, smem, grid, st);
+        case 4: return launch_finalize_nv<METRIC, 4>(a, P, wpb, smem, grid, st);
+        default: return launch_finalize_nv<METRIC, 0>(a, P, wpb, smem, grid, st);
+    }
+}
+
 cudaError_t launch_finalize(const FinalizeArgs& a, cudaStream_t st, int* launches) {
     int P = a.use_hits ? 2 * a.hits.c + 32 : a.cand.S * a.cand.c;
     P = (P + 3) & ~3;
     if (P > kMaxPool) return cudaErrorInvalidValue;
-    const size_t per_warp =
-        warp_scratch_bytes(P, prefix_cap(P, a.k), a.use_hits ? 1 : a.cand.S, a.d);
-    int wpb = static_cast<int>((96 * 1024) / per_warp);
-    wpb = wpb < 1 ? 1 : (wpb > 8 ? 8 : wpb);
+    const size_t per_warp = warp_scratch_bytes(P, prefix_cap(P, a.k), a.use_hits ? 1 : a.cand.S,
+                                               a.d, a.use_hits != 0);
+    // up to eight warps per block and four blocks per SM when the scratch allows
+    int wpb = static_cast<int>((52 * 1024) / per_warp);
+    if (wpb < 8) wpb = static_cast<int>((96 * 1024) / per_warp);
+    wpb = wpb < 1 ? 1 : (wpb > kThreads / 32 ? kThreads / 32 : wpb);
     const size_t smem = per_warp * wpb;
     if (smem > 200 * 1024) return cudaErrorInvalidValue;
     const unsigned grid = static_cast<unsigned>((a.n + wpb - 1) / wpb);
+    // float4 rows need d % 4 == 0 and 16-byte aligned reference and query arrays
+    const bool aligned =
+        ((reinterpret_cast<uintptr_t>(a.R) | reinterpret_cast<uintptr_t>(a.Q)) & 15) == 0;
+    const int nv = (aligned && (a.d & 3) == 0 && a.d <= 128) ? (a.d + 31) / 32 : 0;
     if (launches) ++*launches;
-    if (a.metric == kL2) {
-        cudaError_t err = cudaFuncSetAttribute(finalize_kernel<kL2>,
-                                               cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                               static_cast<int>(smem));
-        if (err != cudaSuccess) return err;
-        finalize_kernel<kL2><<<grid, wpb * 32, smem, st>>>(a, P, wpb);
-    } else {
-        cudaError_t err = cudaFuncSetAttribute(finalize_kernel<kL1>,
-                                               cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                               static_cast<int>(smem));
-        if (err != cudaSuccess) return err;
-        finalize_kernel<kL1><<<grid, wpb * 32, smem, st>>>(a, P, wpb);
-    }
-    return cudaGetLastError();
+    if (a.metric == kL2) return launch_finalize_m<kL2>(a, nv, P, wpb, smem, grid, st);
+    return launch_finalize_m<kL1>(a, nv, P, wpb, smem, grid, st);
 }
 
 cudaError_t launch_fallback(const FinalizeArgs& a, double* scratch, int32_t grid,
