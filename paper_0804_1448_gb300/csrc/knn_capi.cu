@@ -323,8 +323,8 @@ knn_status knn_search(knn_handle h, const float* Q, int64_t n, int32_t d, int32_
     if (tensor) {
         off_ql = cv.take(static_cast<size_t>(n) * h->kp * (prec == kBF16 ? 2 : 4));
         if (plan.pilot) off_gmax = cv.take(static_cast<size_t>(n) * plan.G * 4);
-        off_lists = cv.take(static_cast<size_t>(n) * S * 2 * plan.cap * sizeof(uint64_t));
-        off_counts = cv.take(static_cast<size_t>(n) * S * 2 * sizeof(int32_t));
+        off_lists = cv.take(static_cast<size_t>(n) * S * plan.groups * plan.cap * sizeof(uint64_t));
+        off_counts = cv.take(static_cast<size_t>(n) * S * plan.groups * sizeof(int32_t));
     } else {
         off_cand = cv.take(static_cast<size_t>(n) * S * c * sizeof(uint64_t));
     }
@@ -378,7 +378,7 @@ knn_status knn_search(knn_handle h, const float* Q, int64_t n, int32_t d, int32_
         fa.use_hits = 1;
         fa.hits.keys = lists;
         fa.hits.counts = counts;
-        fa.hits.S = 2 * S;   // one list per (split, epilogue half)
+        fa.hits.S = plan.groups * S;   // one list per (split, epilogue column group)
         fa.hits.cap = plan.cap;
         fa.hits.c = c;
         fa.cand.exact = 0;

@@ -133,12 +133,12 @@ int tc_padded_dim(int32_t d, int prec);
 
 // Launch plan of the pilot and filter passes for one search.
 struct TcPlan {
-    int32_t mt;          // 128-query tiles per CTA (1 or 2)
+    int32_t mt;          // 128-query tiles per CTA (1)
     int32_t kb;          // 128-byte K blocks per operand row
     int32_t ksteps;      // 32-byte MMA K steps that carry data
-    int32_t rb;          // references per TMA stage (128 or 256)
+    int32_t rb;          // references per tile (MMA N = 256)
     int32_t kbs;         // K blocks per TMA stage (kb, or 1 for long rows)
-    int32_t stage_half;  // stage hit values per 16-element half slice (less shared memory)
+    int32_t groups;      // hit lists per (query, split): one per epilogue column group
     int32_t stages;      // reference-stage ring depth
     int32_t S;           // reference splits
     int64_t chunk;       // references per split (multiple of rb)
@@ -147,7 +147,7 @@ struct TcPlan {
     int32_t G;           // pilot group maxima per query
     int32_t cprime;      // order statistic of the group maxima used as threshold
     int32_t pilot;       // 0: no pilot, every reference is appended
-    int32_t cap;         // list capacity per (query, split, epilogue half)
+    int32_t cap;         // list capacity per (query, split, column group)
     size_t smem_filter;
 };
 TcPlan tc_plan(int64_t n, int64_t m, int32_t d, int32_t kp, int prec, int32_t c, int num_sms);

@@ -22,17 +22,22 @@
 // best c by acc, re-ranks them with exact float32 differences, and checks the
 // list was neither too short nor overflowed.
 //
-// CTA layout: MT tiles of 128 queries (MMA M; one TMEM lane per query) share
-// every reference tile of 128 (MMA N):
-//   warp 0        TMA producer: the query tiles once, then reference tiles into
-//                 a ring of single-K-block shared-memory stages (128-byte swizzle);
-//   warp 1        MMA issuer: per reference tile and query tile, kp*elt/32
-//                 tcgen05.mma into one of two TMEM accumulators per query tile;
-//                 tcgen05.commit frees the smem stage and publishes the tile;
-//   warps 2..     epilogue, 8 per query tile: warp w may read the TMEM lanes
-//                 32*(w%4)..+31, so thread t of warp w owns query row
-//                 32*(w%4)+t; the two warps sharing a lane quarter split the
-//                 four 32-column slices of each tile between them.
+// CTA layout: one tile of 128 queries (MMA M; one TMEM lane per query) meets
+// reference tiles of 256 (MMA N = 256: one tcgen05.mma per 16- or 8-element
+// K step covers the whole tile, which halves the instructions, commits and
+// waits per product against N = 128):
+//   warp 0        TMA producer: the query tile once, then reference tiles into
+//                 a ring of shared-memory stages (128-byte swizzle), a stage
+//                 being a whole tile with all its K blocks, or one K block of
+//                 it when rows are long;
+//   warp 1        MMA issuer: per reference tile, one tcgen05.mma per K step
+//                 into one of two 256-column TMEM accumulators (all 512
+//                 columns); tcgen05.commit frees the stage and publishes the tile;
+//   warps 2..17   epilogue: warp w may read the TMEM lanes 32*(w%4)..+31, so
+//                 thread t of warp w owns query row 32*(w%4)+t, and the four
+//                 warps sharing a lane quarter take 64 columns each.  A warp
+//                 loads its two 32-column slices, releases the accumulator,
+//                 then works on the slices while the next tile is multiplied.
 // Every mbarrier wait is bounded; on expiry the CTA raises the error flag,
 // stops, waits for what it issued and frees its TMEM.
 #include <cmath>
@@ -46,53 +51,56 @@ namespace knn {
 using namespace ptx;
 namespace {
 
-constexpr int kBlockM = 128;
-constexpr int kBlockN = 128;
+constexpr int kBlockM = 128;                        // queries per CTA
+constexpr int kTileN = 256;                         // references per tile (MMA N)
 constexpr int kAtomBytes = 128;
-constexpr int kTileBytes = kBlockM * kAtomBytes;   // one 128-byte K block of 128 rows
+constexpr int kQTileBytes = kBlockM * kAtomBytes;   // one 128-byte K block of the query tile
+constexpr int kRTileBytes = kTileN * kAtomBytes;    // one 128-byte K block of a reference tile
+constexpr int kEpiWarps = 16;
+constexpr int kEpi = 32 * kEpiWarps;                // epilogue threads
+constexpr int kThreads = 64 + kEpi;
+constexpr int kGroups = kEpiWarps / 4;              // column groups: hit lists per query and split
+constexpr int kGroupCols = kTileN / kGroups;        // 64: two 32-column slices per warp
+constexpr uint32_t kTmemCols = 2 * kTileN;          // two accumulators
 constexpr int kMaxStages = 12;
 constexpr size_t kSmemLimit = 232448;
 constexpr int kAugCols = 4;
-// Floats per thread in the hit-staging area: a whole 32-value slice + pad, or
-// (when shared memory is short) 16 values + pad; either stride keeps eight
-// lanes' 16-byte stores on distinct banks.
-constexpr int kStageFull = 36;
-constexpr int kStageHalf = 20;
+// Words per thread in the hit-staging area: a slice's 32 values packed to
+// their upper 16 bits (16 words) + pad, so that eight lanes' 16-byte stores
+// fall on distinct banks.
+constexpr int kStageWords = 20;
 
 struct TcArgs {
     int64_t n, m;
     int32_t kb;           // 128-byte K blocks per operand row (row pitch = kb * 128 bytes)
     int32_t ksteps;       // 32-byte MMA K steps that carry data
-    int32_t rb;           // references per pipeline stage (128 or 256): rb/128 MMA tiles
-    int32_t kbs;          // K blocks per stage: kb (whole rows) or 1 (then rb = 128)
+    int32_t kbs;          // K blocks per stage: kb (whole tiles) or 1 (long rows)
     int32_t stages;
-    int64_t chunk;        // references per split (multiple of rb)
+    int64_t chunk;        // references per split (multiple of kTileN)
     int32_t S;
-    int32_t stride;       // pilot: every stride-th stage of a split
-    int32_t spt;          // pilot: sampled-stage slots per split
-    int32_t G;            // pilot: group maxima per query (S * spt * rb / 32)
+    int32_t stride;       // pilot: every stride-th tile of a split
+    int32_t spt;          // pilot: sampled-tile slots per split
+    int32_t G;            // pilot: group maxima per query (S * spt * kTileN / 32)
     uint32_t* gmax;       // pilot: [n][G] order-mapped maxima, 0 = no group
-    uint64_t* lists;      // filter: [n][S][2][cap], one list per epilogue half
-    int32_t* counts;      // filter: [n][S][2] (may exceed cap: overflow)
+    uint64_t* lists;      // filter: [n][S][kGroups][cap], one list per column group
+    int32_t* counts;      // filter: [n][S][kGroups] (may exceed cap: overflow)
     int32_t cap;
     int32_t append_all;   // filter: every valid reference passes
-    int32_t stage_half;   // filter: stage hit values per 16-element half slice
     int32_t* error_flag;
 };
 
-// A: mt query tiles of kb K blocks (resident); B: a ring of `stages` boxes of
-// rb references x kbs K blocks; staging of hit values (filter only).
-__host__ __device__ constexpr size_t tc_smem_bytes(int mt, int kb, int rb, int kbs, int stages,
-                                                   bool pilot, bool half_stage = false) {
-    return 1024 + static_cast<size_t>(kTileBytes) * mt * kb +
-           static_cast<size_t>(rb) * kAtomBytes * kbs * stages +
-           (pilot ? 0 : static_cast<size_t>(256) * mt * (half_stage ? kStageHalf : kStageFull) * 4) +
-           512;
+// A: the query tile, kb K blocks (resident); B: a ring of `stages` stages of
+// kTileN references x kbs K blocks; hit staging (filter only); barriers.
+__host__ __device__ constexpr size_t tc_smem_bytes(int kb, int kbs, int stages, bool pilot) {
+    return 1024 + static_cast<size_t>(kQTileBytes) * kb +
+           static_cast<size_t>(kRTileBytes) * kbs * stages +
+           (pilot ? 0 : static_cast<size_t>(kEpi) * kStageWords * 4) + 512;
 }
 
 // Append one passing reference to a hit list.  key = (order of -acc, index):
 // a threshold pass has acc >= +0, so the order of -acc is ~bits(acc) without
-// its sign bit; without a threshold acc may have either sign.
+// its sign bit; without a threshold acc may have either sign.  vb holds the
+// upper 16 bits of acc's float32 bits (the lower ones are zero).
 __device__ __forceinline__ void append(uint64_t* list, int& cnt, int cap, uint32_t vb, uint32_t j,
                                        int append_all) {
     const uint32_t o = append_all ? ord_f32(-__uint_as_float(vb)) : (~vb & 0x7fffffffu);
@@ -100,45 +108,38 @@ __device__ __forceinline__ void append(uint64_t* list, int& cnt, int cap, uint32
     ++cnt;
 }
 
-// MMAs of one 128-byte K block of one reference tile for all MT query tiles.
-// Fully unrolled over the four 32-byte K steps (a runtime guard skips steps
-// past the data): issue from the single MMA thread must keep pace with the
-// tensor core, and a loop with runtime bounds halves the issue rate.
-template <int PREC, int MT>
-__device__ __forceinline__ void issue_kblock(uint32_t d_tmem, uint32_t a_kb, uint32_t a_mt_stride,
-                                             uint32_t b_kb, int k4, bool first, uint32_t id) {
+// MMAs of one 128-byte K block of one reference tile.  Fully unrolled over the
+// four 32-byte K steps (a runtime guard skips steps past the data): issue from
+// the single MMA thread must keep pace with the tensor core.  Descriptors
+// advance by 32 bytes (2 in their 16-byte address field) per K step.
+template <int PREC>
+__device__ __forceinline__ void issue_kblock(uint32_t d_tmem, uint64_t a_desc, uint64_t b_desc,
+                                             int k4, bool first, uint32_t id) {
 #pragma unroll
-    for (int mt = 0; mt < MT; ++mt) {
-#pragma unroll
-        for (int ks = 0; ks < 4; ++ks) {
-            if (ks < k4)
-                mma<PREC>(d_tmem + mt * kBlockN, sdesc(a_kb + mt * a_mt_stride + ks * 32),
-                          sdesc(b_kb + ks * 32), id, (first && ks == 0) ? 0u : 1u);
-        }
+    for (int ks = 0; ks < 4; ++ks) {
+        if (ks < k4)
+            mma<PREC>(d_tmem, a_desc + 2 * ks, b_desc + 2 * ks, id, (first && ks == 0) ? 0u : 1u);
     }
 }
 
-// KBT > 0: whole-K stages of exactly KBT K blocks (compile-time, unrolled);
-// KBT == 0: any K-block count and either stage layout (loops over K blocks).
-template <int PREC, int MT, bool PILOT, int KBT>
-__global__ void __launch_bounds__(64 + 256 * MT, 1)
+// KBT > 0: whole-tile stages of exactly KBT K blocks (compile-time, unrolled);
+// KBT == 0: any K-block count, whole-tile or single-K-block stages.
+template <int PREC, bool PILOT, int KBT>
+__global__ void __launch_bounds__(kThreads, 1)
 tc_kernel(const __grid_constant__ CUtensorMap tmap_q, const __grid_constant__ CUtensorMap tmap_r,
           TcArgs a) {
-    constexpr int kEpi = 256 * MT;             // epilogue threads: two per query row
-    constexpr uint32_t kTmemCols = 256 * MT;   // two 128-column accumulators per query tile
     extern __shared__ unsigned char smem_raw[];
     const uint32_t raw = smem_u32(smem_raw);
     unsigned char* smem = smem_raw + (((raw + 1023u) & ~1023u) - raw);
 
     const int KB = KBT > 0 ? KBT : a.kb, KBS = KBT > 0 ? KBT : a.kbs;
-    const int NST = a.stages, RB = a.rb, TPS = a.rb / kBlockN;
+    const int NST = a.stages;
     const int SPT = KB / KBS;                   // stages per reference tile (1, or KB when KBS = 1)
-    const size_t stage_bytes = static_cast<size_t>(RB) * kAtomBytes * KBS;
+    const size_t stage_bytes = static_cast<size_t>(kRTileBytes) * KBS;
     unsigned char* sA = smem;
-    unsigned char* sB = sA + static_cast<size_t>(MT) * KB * kTileBytes;
-    float* stage = reinterpret_cast<float*>(sB + NST * stage_bytes);
-    const int stride_st = a.stage_half ? kStageHalf : kStageFull;
-    uint64_t* bars = reinterpret_cast<uint64_t*>(stage + (PILOT ? 0 : kEpi * stride_st));
+    unsigned char* sB = sA + static_cast<size_t>(KB) * kQTileBytes;
+    uint32_t* stage = reinterpret_cast<uint32_t*>(sB + NST * stage_bytes);
+    uint64_t* bars = reinterpret_cast<uint64_t*>(stage + (PILOT ? 0 : kEpi * kStageWords));
     uint64_t* full = bars;
     uint64_t* empty = bars + kMaxStages;
     uint64_t* a_full = bars + 2 * kMaxStages;
@@ -149,14 +150,13 @@ tc_kernel(const __grid_constant__ CUtensorMap tmap_q, const __grid_constant__ CU
     volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
 
     const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
-    const int64_t q0 = static_cast<int64_t>(blockIdx.x) * kBlockM * MT;
+    const int64_t q0 = static_cast<int64_t>(blockIdx.x) * kBlockM;
     const int split = blockIdx.y;
     const int64_t r_begin = static_cast<int64_t>(split) * a.chunk;
     const int64_t r_end = min(a.m, r_begin + a.chunk);
-    const int stages_all = static_cast<int>((r_end - r_begin + RB - 1) / RB);
+    const int tiles_all = static_cast<int>((r_end - r_begin + kTileN - 1) / kTileN);
     const int stride = PILOT ? a.stride : 1;
-    const int ng = (stages_all + stride - 1) / stride;   // stages this CTA processes
-    const int nt = ng * TPS;                             // MMA tiles
+    const int nt = (tiles_all + stride - 1) / stride;   // tiles this CTA processes
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < NST; ++s) {
@@ -166,7 +166,7 @@ tc_kernel(const __grid_constant__ CUtensorMap tmap_q, const __grid_constant__ CU
         mbar_init(a_full, 1);
         for (int b = 0; b < 2; ++b) {
             mbar_init(&t_full[b], 1);
-            mbar_init(&t_empty[b], kEpi);
+            mbar_init(&t_empty[b], kEpiWarps);
         }
         mbar_init(drain, 1);
         *abort_flag = 0;
@@ -185,18 +185,16 @@ tc_kernel(const __grid_constant__ CUtensorMap tmap_q, const __grid_constant__ CU
 
     if (warp == 0) {
         // -------------------------------------------------------- producer
-        // one 3-D box per operand load: (128 bytes of K) x rows x all K blocks
+        // one 3-D box per load: (128 bytes of K) x rows x K blocks
         if (lane == 0) {
-            mbar_expect_tx(a_full, MT * KB * kTileBytes);
-            for (int mt = 0; mt < MT; ++mt)
-                tma_load_3d(sA + static_cast<size_t>(mt) * KB * kTileBytes, &tmap_q, a_full, 0,
-                            static_cast<int>(q0 + mt * kBlockM), 0);
-            int issued = 0;   // stage h = g * SPT + kb: reference rows of g, K blocks kb..
-            for (int h = 0; h < ng * SPT; ++h) {
+            mbar_expect_tx(a_full, KB * kQTileBytes);
+            tma_load_3d(sA, &tmap_q, a_full, 0, static_cast<int>(q0), 0);
+            int issued = 0;   // stage h = tile * SPT + K-block group
+            for (int h = 0; h < nt * SPT; ++h) {
                 const int g = h / SPT, z = (h % SPT) * KBS, s = h % NST;
                 if (!mbar_wait(&empty[s], ((h / NST) & 1) ^ 1, abort_flag)) { fail(); break; }
                 mbar_expect_tx(&full[s], static_cast<uint32_t>(stage_bytes));
-                const int y = static_cast<int>(r_begin + static_cast<int64_t>(g) * stride * RB);
+                const int y = static_cast<int>(r_begin + static_cast<int64_t>(g) * stride * kTileN);
                 tma_load_3d(sB + s * stage_bytes, &tmap_r, &full[s], 0, y, z);
                 issued = h + 1;
             }
@@ -208,47 +206,35 @@ tc_kernel(const __grid_constant__ CUtensorMap tmap_q, const __grid_constant__ CU
     } else if (warp == 1) {
         // ------------------------------------------------------ MMA issuer
         if (lane == 0) {
-            const uint32_t id = idesc(PREC == kBF16 ? 1 : 2, kBlockM, kBlockN);
+            const uint32_t id = idesc(PREC == kBF16 ? 1 : 2, kBlockM, kTileN);
             bool ok = mbar_wait(a_full, 0, abort_flag);
             if (!ok) fail();
-            const uint32_t a_base = smem_u32(sA);
-            if (SPT == 1) {
-                // whole-K stages: stage g holds TPS tiles of 128 references
-                for (int g = 0; ok && g < ng; ++g) {
+            const uint64_t a_desc = sdesc(smem_u32(sA));
+            constexpr uint32_t kQStep = kQTileBytes >> 4, kRStep = kRTileBytes >> 4;
+            for (int g = 0; ok && g < nt; ++g) {
+                const int buf = g & 1;
+                if (!mbar_wait(&t_empty[buf], ((g >> 1) & 1) ^ 1, abort_flag)) { fail(); break; }
+                tc_fence_after();
+                const uint32_t d_tmem = tmem + buf * kTileN;
+                if (SPT == 1) {
+                    // whole-tile stage g
                     const int s = g % NST;
                     if (!mbar_wait(&full[s], (g / NST) & 1, abort_flag)) { fail(); break; }
-                    const uint32_t b_stage = smem_u32(sB + s * stage_bytes);
-                    for (int t2 = 0; t2 < TPS; ++t2) {
-                        const int i = g * TPS + t2, buf = i & 1;
-                        if (!mbar_wait(&t_empty[buf], ((i >> 1) & 1) ^ 1, abort_flag)) {
-                            fail();
-                            ok = false;
-                            break;
-                        }
-                        tc_fence_after();
-                        const uint32_t d_tmem = tmem + buf * MT * kBlockN;
-                        const uint32_t b_tile = b_stage + t2 * kTileBytes;
-                        if (KBT > 0) {
+                    tc_fence_after();
+                    const uint64_t b_desc = sdesc(smem_u32(sB + s * stage_bytes));
+                    if (KBT > 0) {
 #pragma unroll
-                            for (int kb = 0; kb < (KBT > 0 ? KBT : 1); ++kb)
-                                issue_kblock<PREC, MT>(d_tmem, a_base + kb * kTileBytes, KB * kTileBytes,
-                                                       b_tile + kb * RB * kAtomBytes,
-                                                       a.ksteps - kb * 4, kb == 0, id);
-                        } else {
-                            for (int kb = 0; kb < KB; ++kb)
-                                issue_kblock<PREC, MT>(d_tmem, a_base + kb * kTileBytes, KB * kTileBytes,
-                                                       b_tile + kb * RB * kAtomBytes,
-                                                       a.ksteps - kb * 4, kb == 0, id);
-                        }
-                        tc_commit(&t_full[buf]);
+                        for (int kb = 0; kb < (KBT > 0 ? KBT : 1); ++kb)
+                            issue_kblock<PREC>(d_tmem, a_desc + kb * kQStep, b_desc + kb * kRStep,
+                                               a.ksteps - kb * 4, kb == 0, id);
+                    } else {
+                        for (int kb = 0; kb < KB; ++kb)
+                            issue_kblock<PREC>(d_tmem, a_desc + kb * kQStep, b_desc + kb * kRStep,
+                                               a.ksteps - kb * 4, kb == 0, id);
                     }
                     tc_commit(&empty[s]);   // the stage is free once these MMAs complete
-                }
-            } else {
-                // one K block per stage: tile g takes stages g*KB .. g*KB+KB-1
-                for (int g = 0; ok && g < ng; ++g) {
-                    const int buf = g & 1;
-                    if (!mbar_wait(&t_empty[buf], ((g >> 1) & 1) ^ 1, abort_flag)) { fail(); break; }
+                } else {
+                    // one K block per stage: tile g takes stages g*KB .. g*KB+KB-1
                     for (int kb = 0; kb < KB; ++kb) {
                         const int h = g * KB + kb, s = h % NST;
                         if (!mbar_wait(&full[s], (h / NST) & 1, abort_flag)) {
@@ -257,14 +243,14 @@ tc_kernel(const __grid_constant__ CUtensorMap tmap_q, const __grid_constant__ CU
                             break;
                         }
                         tc_fence_after();
-                        issue_kblock<PREC, MT>(tmem + buf * MT * kBlockN, a_base + kb * kTileBytes,
-                                               KB * kTileBytes, smem_u32(sB + s * stage_bytes),
-                                               a.ksteps - kb * 4, kb == 0, id);
+                        issue_kblock<PREC>(d_tmem, a_desc + kb * kQStep,
+                                           sdesc(smem_u32(sB + s * stage_bytes)), a.ksteps - kb * 4,
+                                           kb == 0, id);
                         tc_commit(&empty[s]);
                     }
                     if (!ok) break;
-                    tc_commit(&t_full[buf]);
                 }
+                tc_commit(&t_full[buf]);
             }
             tc_commit(drain);   // arrives once every MMA issued above has completed
             mbar_wait(drain, 0, nullptr);
@@ -273,46 +259,38 @@ tc_kernel(const __grid_constant__ CUtensorMap tmap_q, const __grid_constant__ CU
     } else {
         // -------------------------------------------------------- epilogue
         const int et = threadIdx.x - 64;            // 0 .. kEpi-1
-        const int ew = et / 32;
-        const int mt = (ew / 4) % MT;
-        const int half = ew / (4 * MT);             // slices 2*half, 2*half+1 of every tile
         const int quarter = warp & 3;               // the TMEM lanes this warp may access
+        const int cg = (warp - 2) / 4;              // column group: columns cg*64 .. +63
         const int row = quarter * 32 + lane;
-        const int64_t q = q0 + mt * kBlockM + row;
+        const int64_t q = q0 + row;
         const bool active = q < a.n;
         const uint32_t lane_addr = tmem + (static_cast<uint32_t>(quarter * 32) << 16);
-        float* st = stage + et * stride_st;
-        const int gpt = RB / 32;                    // groups of 32 references per stage
+        uint32_t* st = stage + et * kStageWords;
+        constexpr int gpt = kTileN / 32;            // groups of 32 references per tile
         uint64_t* list = nullptr;
         uint32_t* gout = nullptr;
         if (PILOT) gout = a.gmax + q * a.G + static_cast<int64_t>(split) * a.spt * gpt;
-        // each half-warp owns its own list: (query, split, half)
-        else list = a.lists + ((q * a.S + split) * 2 + half) * static_cast<int64_t>(a.cap);
+        else list = a.lists + ((q * a.S + split) * kGroups + cg) * static_cast<int64_t>(a.cap);
         int cnt = 0;
-        for (int i = 0; i < nt; ++i) {
-            const int buf = i & 1, g = i / TPS, t2 = i % TPS;
-            const bool ok = mbar_wait(&t_full[buf], (i >> 1) & 1, abort_flag);
+        for (int g = 0; g < nt; ++g) {
+            const int buf = g & 1;
+            const bool ok = mbar_wait(&t_full[buf], (g >> 1) & 1, abort_flag);
             if (!__all_sync(0xffffffffu, ok)) { fail(); break; }
             tc_fence_after();
-            const int64_t jt = r_begin + static_cast<int64_t>(g) * stride * RB + t2 * kBlockN;
-            // this warp's two 32-column slices; the second loads while the
-            // first is processed
+            const int64_t jt = r_begin + static_cast<int64_t>(g) * stride * kTileN + cg * kGroupCols;
+            // both 32-column slices into registers, then release the accumulator
             uint32_t ra[32], rb[32];
-            const uint32_t col0 = lane_addr + (buf * MT + mt) * kBlockN + half * 64;
-            __syncwarp();
+            const uint32_t col0 = lane_addr + buf * kTileN + cg * kGroupCols;
             tmem_ld32u_async(col0, ra);
+            tmem_ld32u_async(col0 + 32, rb);
+            tmem_wait_ld2(ra, rb);
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&t_empty[buf]);
 #pragma unroll
             for (int sl = 0; sl < 2; ++sl) {
-                const int ch = 2 * half + sl;
-                uint32_t (&r)[32] = sl ? rb : ra;
-                tmem_wait_ld(r);
-                if (sl == 0) {
-                    tmem_ld32u_async(col0 + 32, rb);
-                } else {
-                    tc_fence_before();
-                    mbar_arrive(&t_empty[buf]);   // both slices of this buffer are in registers
-                }
-                const int64_t j0 = jt + ch * 32;
+                const uint32_t (&r)[32] = sl ? rb : ra;
+                const int64_t j0 = jt + sl * 32;
                 const int64_t left = r_end - j0;
                 const int nvalid = left <= 0 ? 0 : (left >= 32 ? 32 : static_cast<int>(left));
                 if (PILOT) {
@@ -324,7 +302,7 @@ tc_kernel(const __grid_constant__ CUtensorMap tmap_q, const __grid_constant__ CU
                     for (int w2 = 16; w2 > 0; w2 >>= 1)
 #pragma unroll
                         for (int u = 0; u < w2; ++u) v[u] = fmaxf(v[u], v[u + w2]);
-                    if (active && nvalid > 0) gout[g * gpt + t2 * 4 + ch] = ord_f32(v[0]);
+                    if (active && nvalid > 0) gout[g * gpt + cg * 2 + sl] = ord_f32(v[0]);
                 } else {
                     // sign bits, bit 31-u for element u, as four independent chains
                     uint32_t m4[4] = {0u, 0u, 0u, 0u};
@@ -338,45 +316,29 @@ tc_kernel(const __grid_constant__ CUtensorMap tmap_q, const __grid_constant__ CU
                     hits &= nvalid >= 32 ? 0xffffffffu : ((1u << nvalid) - 1u);
                     if (!active) hits = 0;
                     // the append loop reads the hit values with a dynamic index, which
-                    // registers do not allow: they go through shared memory first
-                    if (!a.stage_half) {
-                        if (hits) {
+                    // registers do not allow: their upper halves go through shared memory
+                    if (hits) {
 #pragma unroll
-                            for (int h = 0; h < 8; ++h)
-                                reinterpret_cast<uint4*>(st)[h] =
-                                    make_uint4(r[4 * h], r[4 * h + 1], r[4 * h + 2], r[4 * h + 3]);
-                            const uint32_t jb = static_cast<uint32_t>(j0);
-                            do {
-                                const int u = __ffs(hits) - 1;
-                                hits &= hits - 1;
-                                append(list, cnt, a.cap, __float_as_uint(st[u]), jb + u, a.append_all);
-                            } while (hits);
-                        }
-                    } else {
-#pragma unroll
-                        for (int hf = 0; hf < 2; ++hf) {
-                            uint32_t hh = (hits >> (16 * hf)) & 0xffffu;
-                            if (hh) {
-#pragma unroll
-                                for (int h = 0; h < 4; ++h)
-                                    reinterpret_cast<uint4*>(st)[h] =
-                                        make_uint4(r[16 * hf + 4 * h], r[16 * hf + 4 * h + 1],
-                                                   r[16 * hf + 4 * h + 2], r[16 * hf + 4 * h + 3]);
-                                const uint32_t jb = static_cast<uint32_t>(j0) + 16 * hf;
-                                do {
-                                    const int u = __ffs(hh) - 1;
-                                    hh &= hh - 1;
-                                    append(list, cnt, a.cap, __float_as_uint(st[u]), jb + u,
-                                           a.append_all);
-                                } while (hh);
-                            }
-                        }
+                        for (int h = 0; h < 4; ++h)
+                            reinterpret_cast<uint4*>(st)[h] = make_uint4(
+                                __byte_perm(r[8 * h + 0], r[8 * h + 1], 0x7632),
+                                __byte_perm(r[8 * h + 2], r[8 * h + 3], 0x7632),
+                                __byte_perm(r[8 * h + 4], r[8 * h + 5], 0x7632),
+                                __byte_perm(r[8 * h + 6], r[8 * h + 7], 0x7632));
+                        const uint32_t jb = static_cast<uint32_t>(j0);
+                        const uint16_t* st16 = reinterpret_cast<const uint16_t*>(st);
+                        do {
+                            const int u = __ffs(hits) - 1;
+                            hits &= hits - 1;
+                            append(list, cnt, a.cap, static_cast<uint32_t>(st16[u]) << 16, jb + u,
+                                   a.append_all);
+                        } while (hits);
                     }
                     __syncwarp();
                 }
             }
         }
-        if (!PILOT && active) a.counts[(q * a.S + split) * 2 + half] = cnt;
+        if (!PILOT && active) a.counts[(q * a.S + split) * kGroups + cg] = cnt;
     }
     tc_fence_before();
     __syncthreads();
@@ -521,43 +483,38 @@ bool make_map(CUtensorMap* map, const void* base, int64_t rows, int kp, int prec
     return r == CUDA_SUCCESS;
 }
 
-template <int PREC, int MT, bool PILOT, int KBT>
+
+template <int PREC, bool PILOT, int KBT>
 cudaError_t launch_kernel(const TcPlan& p, const CUtensorMap& mq, const CUtensorMap& mr,
                           const TcArgs& a, cudaStream_t st) {
-    auto kern = tc_kernel<PREC, MT, PILOT, KBT>;
-    const size_t smem = tc_smem_bytes(MT, p.kb, p.rb, p.kbs, p.stages, PILOT, p.stage_half != 0);
+    auto kern = tc_kernel<PREC, PILOT, KBT>;
+    const size_t smem = tc_smem_bytes(p.kb, p.kbs, p.stages, PILOT);
     cudaError_t err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                            static_cast<int>(smem));
     if (err != cudaSuccess) return err;
-    dim3 grid(static_cast<unsigned>((a.n + kBlockM * MT - 1) / (kBlockM * MT)),
-              static_cast<unsigned>(a.S));
-    kern<<<grid, 64 + 256 * MT, smem, st>>>(mq, mr, a);
+    dim3 grid(static_cast<unsigned>((a.n + kBlockM - 1) / kBlockM), static_cast<unsigned>(a.S));
+    kern<<<grid, kThreads, smem, st>>>(mq, mr, a);
     return cudaGetLastError();
 }
 
-template <int PREC, int MT, bool PILOT>
+template <int PREC, bool PILOT>
 cudaError_t dispatch_kb(const TcPlan& p, const CUtensorMap& mq, const CUtensorMap& mr,
                         const TcArgs& a, cudaStream_t st) {
-    if (p.kbs == p.kb) {   // whole-K stages: unrolled issue for the common row lengths
+    if (p.kbs == p.kb) {   // whole-tile stages: unrolled issue for the common row lengths
         switch (p.kb) {
-            case 1: return launch_kernel<PREC, MT, PILOT, 1>(p, mq, mr, a, st);
-            case 2: return launch_kernel<PREC, MT, PILOT, 2>(p, mq, mr, a, st);
-            case 3: return launch_kernel<PREC, MT, PILOT, 3>(p, mq, mr, a, st);
-            case 4: return launch_kernel<PREC, MT, PILOT, 4>(p, mq, mr, a, st);
+            case 1: return launch_kernel<PREC, PILOT, 1>(p, mq, mr, a, st);
+            case 2: return launch_kernel<PREC, PILOT, 2>(p, mq, mr, a, st);
             default: break;
         }
     }
-    return launch_kernel<PREC, MT, PILOT, 0>(p, mq, mr, a, st);
+    return launch_kernel<PREC, PILOT, 0>(p, mq, mr, a, st);
 }
 
 template <bool PILOT>
 cudaError_t dispatch(const TcPlan& p, int prec, const CUtensorMap& mq, const CUtensorMap& mr,
                      const TcArgs& a, cudaStream_t st) {
-    if (prec == kBF16)
-        return p.mt == 2 ? dispatch_kb<kBF16, 2, PILOT>(p, mq, mr, a, st)
-                         : dispatch_kb<kBF16, 1, PILOT>(p, mq, mr, a, st);
-    return p.mt == 2 ? dispatch_kb<kTF32, 2, PILOT>(p, mq, mr, a, st)
-                     : dispatch_kb<kTF32, 1, PILOT>(p, mq, mr, a, st);
+    if (prec == kBF16) return dispatch_kb<kBF16, PILOT>(p, mq, mr, a, st);
+    return dispatch_kb<kTF32, PILOT>(p, mq, mr, a, st);
 }
 
 TcArgs base_args(const TcPlan& p, int64_t n, int64_t m, int32_t* error_flag) {
@@ -566,7 +523,6 @@ TcArgs base_args(const TcPlan& p, int64_t n, int64_t m, int32_t* error_flag) {
     a.m = m;
     a.kb = p.kb;
     a.ksteps = p.ksteps;
-    a.rb = p.rb;
     a.kbs = p.kbs;
     a.stages = p.stages;
     a.chunk = p.chunk;
@@ -576,7 +532,6 @@ TcArgs base_args(const TcPlan& p, int64_t n, int64_t m, int32_t* error_flag) {
     a.G = p.G;
     a.cap = p.cap;
     a.append_all = p.pilot ? 0 : 1;
-    a.stage_half = p.stage_half;
     a.error_flag = error_flag;
     return a;
 }
@@ -592,37 +547,28 @@ TcPlan tc_plan(int64_t n, int64_t m, int32_t d, int32_t kp, int prec, int32_t c,
     TcPlan p{};
     const int elt = (prec == kBF16) ? 2 : 4;
     const int kstep = 32 / elt;                    // elements per MMA K step
+    p.mt = 1;
+    p.rb = kTileN;
+    p.groups = kGroups;
     p.kb = kp * elt / kAtomBytes;
     p.ksteps = (d + kAugCols + kstep - 1) / kstep;
     p.stages = 0;
-    // prefer two query tiles per CTA and whole-K 256-reference stages, then
-    // shrink; single-K-block stages (more TMA boxes) only when rows are long
-    // {query tiles, references per stage, one K block per stage, half-slice staging}
-    const int shapes[10][4] = {{2, 256, 0, 0}, {2, 128, 0, 0}, {1, 256, 0, 0}, {1, 128, 0, 0},
-                               {2, 128, 0, 1}, {1, 128, 0, 1}, {2, 128, 1, 0}, {1, 128, 1, 0},
-                               {2, 128, 1, 1}, {1, 128, 1, 1}};
-    // whole-K 256-reference stages need a third stage to hide the TMA latency;
-    // with 128-reference stages two boxes per tile pair are already in flight
-    for (int si = 0; si < 10 && p.stages == 0; ++si) {
-        const int kbs = shapes[si][2] ? 1 : p.kb;
-        const int smax = shapes[si][2] ? 12 : kMaxStages;
-        const int smin = (!shapes[si][2] && shapes[si][1] == 256) ? 3 : 2;
-        for (int s = smax; s >= smin; --s) {
-            if (tc_smem_bytes(shapes[si][0], p.kb, shapes[si][1], kbs, s, false, shapes[si][3] != 0) <=
-                kSmemLimit) {
-                p.mt = shapes[si][0];
-                p.rb = shapes[si][1];
-                p.kbs = kbs;
-                p.stage_half = shapes[si][3];
-                p.stages = s;
-                break;
-            }
+    // whole-tile stages (one TMA box and one wait per tile) when two fit,
+    // else single-K-block stages, as many as fit
+    for (int s = 4; s >= 2 && p.stages == 0; --s)
+        if (tc_smem_bytes(p.kb, p.kb, s, false) <= kSmemLimit) {
+            p.kbs = p.kb;
+            p.stages = s;
         }
-    }
+    for (int s = kMaxStages; s >= 2 && p.stages == 0; --s)
+        if (tc_smem_bytes(p.kb, 1, s, false) <= kSmemLimit) {
+            p.kbs = 1;
+            p.stages = s;
+        }
     if (p.stages == 0) return p;   // operand rows too long for shared memory
-    const int64_t qtiles = (n + kBlockM * p.mt - 1) / (kBlockM * p.mt);
+    const int64_t qtiles = (n + kBlockM - 1) / kBlockM;
     // reference splits: the fewest whose CTAs fill at least 85% of the last wave
-    int64_t max_s = m / (8 * p.rb);
+    int64_t max_s = m / (4 * kTileN);
     if (max_s < 1) max_s = 1;
     if (max_s > 64) max_s = 64;
     int S = 1;
@@ -635,32 +581,32 @@ TcPlan tc_plan(int64_t n, int64_t m, int32_t d, int32_t kp, int prec, int32_t c,
         if (eff >= 0.85) break;
     }
     int64_t chunk = (m + S - 1) / S;
-    chunk = (chunk + p.rb - 1) / p.rb * p.rb;
+    chunk = (chunk + kTileN - 1) / kTileN * kTileN;
     S = static_cast<int>((m + chunk - 1) / chunk);
     p.S = S;
     p.chunk = chunk;
-    // pilot sampling: every stride-th stage, at most ~1024 groups per query
-    const int gps = p.rb / 32;                     // groups of 32 references per stage
-    const int64_t stages_total = (m + p.rb - 1) / p.rb;
-    int stride = 2048 / p.rb;                      // one stage in 16 tiles of 128
-    while (stages_total * gps / stride > 1024) stride *= 2;
-    const int sps = static_cast<int>(chunk / p.rb);
+    // pilot sampling: every stride-th tile (one reference in 16 or fewer), at
+    // most ~1024 groups of 32 per query
+    const int gpt = kTileN / 32;                   // groups per tile
+    const int64_t tiles_total = (m + kTileN - 1) / kTileN;
+    int stride = 4096 / kTileN;
+    while (tiles_total * gpt / stride > 1024) stride *= 2;
+    const int tps = static_cast<int>(chunk / kTileN);
     p.stride = stride;
-    p.spt = (sps + stride - 1) / stride;
-    p.G = S * p.spt * gps;
-    const double frac = static_cast<double>(p.rb) / (static_cast<double>(stride) * p.rb);
-    const double lambda = static_cast<double>(c) * frac;
+    p.spt = (tps + stride - 1) / stride;
+    p.G = S * p.spt * gpt;
+    const double lambda = static_cast<double>(c) / stride;
     p.cprime = static_cast<int>(std::ceil(lambda + 6.0 * std::sqrt(lambda) + 4.0));
     p.pilot = (p.G >= 2 * p.cprime) ? 1 : 0;
-    // list capacity per (query, split, half): twice the expected hits plus slack
+    // list capacity per (query, split, column group): twice the expected hits plus slack
     if (p.pilot) {
         const int64_t expect = static_cast<int64_t>(p.cprime) * stride;
-        int64_t cap = (2 * expect + 255) / (2 * S) + 96;
+        int64_t cap = (2 * expect + kGroups * S - 1) / (kGroups * S) + 64;
         p.cap = static_cast<int32_t>((cap + 31) / 32 * 32);
     } else {
-        p.cap = static_cast<int32_t>(chunk / 2);
+        p.cap = static_cast<int32_t>(chunk / kGroups);
     }
-    p.smem_filter = tc_smem_bytes(p.mt, p.kb, p.rb, p.kbs, p.stages, false, p.stage_half != 0);
+    p.smem_filter = tc_smem_bytes(p.kb, p.kbs, p.stages, false);
     return p;
 }
 

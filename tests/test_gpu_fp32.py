@@ -107,6 +107,43 @@ def test_lattice_ties(knn):
             np.testing.assert_allclose(g_dist, o_dist, rtol=1e-6, atol=0)
 
 
+def near_tie_ladder(d, metric, n_q=12, rungs=48, m_far=1500, step=3e-6, seed=123):
+    """For every query, `rungs` references on shells around it whose
+    distances (squared for l2) step by `step` relative: float32 distances of
+    neighbouring rungs are within float32 rounding of one another, while the
+    float64 order is fixed (step > the parity rule's tie tolerance), so every
+    position must match the oracle.  Far references fill the rest."""
+    rng = np.random.default_rng(seed)
+    Q = inputs.uniform(n_q, d, seed=seed)
+    rows = [inputs.uniform(m_far, d, seed=seed + 1) * np.float32(4.0) + np.float32(3.0)]
+    for i in range(n_q):
+        u = rng.standard_normal((rungs, d))
+        if metric == "l2":
+            u /= np.linalg.norm(u, axis=1, keepdims=True)
+            s = 0.5 * np.sqrt(1.0 + step * np.arange(rungs))
+        else:
+            u /= np.abs(u).sum(axis=1, keepdims=True)
+            s = 0.5 * (1.0 + step * np.arange(rungs))
+        rows.append((Q[i].astype(np.float64) + s[:, None] * u).astype(np.float32))
+    R = np.concatenate(rows)
+    perm = np.random.default_rng(seed + 2).permutation(R.shape[0])
+    return np.ascontiguousarray(R[perm]), Q
+
+
+@pytest.mark.parametrize("metric", ["l2", "l1"])
+@pytest.mark.parametrize("d", [96, 33])
+def test_near_tie_ladder_exact_order(knn, metric, d):
+    """Distances 3e-6 apart: beyond float32's resolution at this d, so the
+    float-float re-check (d = 96: eight lanes per entry; d = 33: one lane)
+    decides the order, which must be the oracle's at every position."""
+    R, Q = near_tie_ladder(d, metric)
+    k = 30
+    g_dist, g_idx, st = run_case(knn, R, Q, k, metric)
+    o_dist, o_idx = oracle.knn(R, Q, parity.oracle_k(k, R.shape[0]), metric)
+    parity.compare(g_dist, g_idx, o_dist, o_idx, k, R.shape[0])
+    assert st["recheck_entries"] > 0
+
+
 def test_all_identical_points_use_exact_fallback(knn):
     R = np.full((2000, 5), 0.125, dtype=np.float32)
     Q = np.array([[0.125] * 5, [0.5] * 5], dtype=np.float32)

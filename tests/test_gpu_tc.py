@@ -101,3 +101,17 @@ def test_self_neighbours(knn):
         g_dist, g_idx = run(knn, R, Q, 5, precision)
         np.testing.assert_array_equal(g_idx[:, 0], np.arange(0, 4000, 13))
         assert np.all(g_dist[:, 0] == 0.0)
+
+
+@pytest.mark.parametrize("precision", ["bf16", "tf32"])
+def test_near_tie_ladder(knn, precision):
+    """Shells of references 3e-6 apart in squared distance around every query:
+    all of them survive the low-precision filter, and the float32 re-rank plus
+    the float-float re-check must reproduce the oracle's order exactly."""
+    from tests.test_gpu_fp32 import near_tie_ladder
+    R, Q = near_tie_ladder(96, "l2")
+    k = 30
+    g_dist, g_idx = run(knn, R, Q, k, precision)
+    o_dist, o_idx = oracle.knn(R, Q, parity.oracle_k(k, R.shape[0]), "l2")
+    assert parity.recall(g_idx, o_idx, k) == 1.0
+    parity.compare(g_dist, g_idx, o_dist, o_idx, k, R.shape[0])
