@@ -42,7 +42,7 @@ constexpr int kThreads = 256;
 // Manhattan) accumulated over d coordinates with one rounding per difference
 // and one per accumulation step: |d32 - d| <= (d + 2) u d, u = 2^-24.
 // A safety factor of 2 covers the second-order terms.
-__device__ __forceinline__ double f32_rel_bound(int d) {
+__host__ __device__ inline double f32_rel_bound(int d) {
     return 2.0 * (d + 2) * 5.9604644775390625e-8;
 }
 
@@ -50,7 +50,7 @@ __device__ __forceinline__ double f32_rel_bound(int d) {
 // below 4(d+2) 2^-24 of the sum and is rounded at most twice per term, so the
 // sum is within (d+2)^2 2^-45 of the exact one; the oracle's float64 sum is
 // within (d+2) 2^-53 of it.
-__device__ __forceinline__ double ff_rel_bound(int d) {
+__host__ __device__ inline double ff_rel_bound(int d) {
     const double e = static_cast<double>(d + 2);
     return e * e * 2.8421709430404007e-14 + e * 1.1102230246251565e-16;
 }
@@ -132,6 +132,21 @@ __device__ __forceinline__ void ff_combine(float& H, float& Lo, float H2, float 
     two_sum(H, H2, s, e);
     H = s;
     Lo = __fadd_rn(Lo, __fadd_rn(Lo2, e));
+}
+
+// A float-float value, renormalized (|lo| <= half an ulp of hi), packed as
+// (bits(hi) << 32) | bits(lo).  Distances are >= 0, so hi orders by its bits
+// and pairs order lexicographically (hi, then lo as a float).
+__device__ __forceinline__ uint64_t ff_pack(float H, float Lo) {
+    const float hi = __fadd_rn(H, Lo);
+    const float lo = __fsub_rn(Lo, __fsub_rn(hi, H));
+    return (static_cast<uint64_t>(__float_as_uint(hi)) << 32) | __float_as_uint(lo);
+}
+__device__ __forceinline__ float ff_hi(uint64_t v) { return __uint_as_float(static_cast<uint32_t>(v >> 32)); }
+__device__ __forceinline__ float ff_lo(uint64_t v) { return __uint_as_float(static_cast<uint32_t>(v)); }
+__device__ __forceinline__ bool ff_less(uint64_t a, uint64_t b) {
+    const uint32_t ah = static_cast<uint32_t>(a >> 32), bh = static_cast<uint32_t>(b >> 32);
+    return ah < bh || (ah == bh && ff_lo(a) < ff_lo(b));
 }
 
 __device__ __forceinline__ uint64_t dbits(double x) {
@@ -318,8 +333,7 @@ __device__ void refine_ff(const WarpScratch& w, int nr, const float* __restrict_
                 const float L2 = __shfl_xor_sync(0xffffffffu, Lo, o);
                 ff_combine(H, Lo, H2, L2);
             }
-            if (sub == 0 && p >= 0)
-                w.d64[p] = dbits(static_cast<double>(H) + static_cast<double>(Lo));
+            if (sub == 0 && p >= 0) w.d64[p] = ff_pack(H, Lo);
         }
     } else {
         for (int e = lane; e < nr; e += 32) {
@@ -327,7 +341,7 @@ __device__ void refine_ff(const WarpScratch& w, int nr, const float* __restrict_
             const float* r = R + static_cast<int64_t>(key_idx(w.sorted[p])) * d;
             float H = 0.f, Lo = 0.f;
             for (int t = 0; t < d; ++t) ff_term<METRIC>(H, Lo, w.qrow[t], __ldg(r + t));
-            w.d64[p] = dbits(static_cast<double>(H) + static_cast<double>(Lo));
+            w.d64[p] = ff_pack(H, Lo);
         }
     }
     __syncwarp();
@@ -354,7 +368,17 @@ __device__ void gather_cand(const FinalizeArgs& a, int64_t q, WarpScratch& w, in
     exact_keys<METRIC, NV>(w.keys, Sc, a.R, a.d, w.qrow, lane);
 }
 
-// Histogram over [lo, lo + kBins/inv).
+// First-level histogram over [vmin, vmax]: inv = (kBins - 0.51) / (vmax - vmin),
+// so (v - lo) * inv lies in [0, kBins - 0.51] and one fused multiply-add onto
+// 1.5 * 2^23 rounds it to an integer held in the low mantissa bits.
+struct FastBin {
+    float lo, inv;
+    __device__ int bin(float v) const {
+        return __float_as_int(fmaf(v - lo, inv, 12582912.f)) & (kBins - 1);
+    }
+};
+
+// Histogram over [lo, lo + kBins/inv), values outside clamped to the ends.
 struct Binning {
     float lo, inv;
     __device__ int bin(float v) const {
@@ -440,6 +464,7 @@ __device__ int gather_hits_impl(const FinalizeArgs& a, int64_t q, int P, WarpScr
             hv[i] = (e < total) ? static_cast<uint32_t>(w.stage[e] >> 32) : 0u;
         }
     }
+    float vmin = __int_as_float(0x7f800000), vmax = -vmin;
     // visit every entry: f(score) for the staged registers, or f(key) re-read
     auto for_each = [&](auto&& f) {
         if constexpr (STAGED) {
@@ -454,7 +479,6 @@ __device__ int gather_hits_impl(const FinalizeArgs& a, int64_t q, int P, WarpScr
             }
         }
     };
-    float vmin = __int_as_float(0x7f800000), vmax = -vmin;
     for_each([&](float v) {
         vmin = fminf(vmin, v);
         vmax = fmaxf(vmax, v);
@@ -463,7 +487,8 @@ __device__ int gather_hits_impl(const FinalizeArgs& a, int64_t q, int P, WarpScr
         vmin = fminf(vmin, __shfl_xor_sync(0xffffffffu, vmin, o));
         vmax = fmaxf(vmax, __shfl_xor_sync(0xffffffffu, vmax, o));
     }
-    Binning b1{vmin, vmax > vmin ? kBins / (vmax - vmin) : 0.f};
+    const float range = vmax - vmin;
+    FastBin b1{vmin, range > 1e-30f ? (kBins - 0.51f) / range : 0.f};
     int cut1 = kBins - 1, cut2 = kBins - 1;
     Binning b2{0.f, 0.f};
     if (total > c) {
@@ -476,7 +501,7 @@ __device__ int gather_hits_impl(const FinalizeArgs& a, int64_t q, int P, WarpScr
         const int in_bin = w.hist[cut1];
         __syncwarp();
         if (before + in_bin > P && b1.inv > 0.f) {   // refine the cut bin once
-            b2.lo = vmin + cut1 / b1.inv;
+            b2.lo = vmin + (cut1 - 0.5f) / b1.inv;
             b2.inv = b1.inv * kBins;
             for (int b = lane; b < kBins; b += 32) w.hist[b] = 0;
             __syncwarp();
@@ -609,8 +634,7 @@ finalize_kernel(FinalizeArgs a, int P, int warps_per_block) {
 
     // 2. ascending prefix by repeated minimum: the first k, continued through
     //    the near-tie run holding position k-1
-    const double rel = f32_rel_bound(d);
-    const float relf = static_cast<float>(2.02 * rel);
+    const float relf = a.relf;
     int L = 0;
     uint64_t prev = 0;
     bool truncated = false;
@@ -670,7 +694,9 @@ finalize_kernel(FinalizeArgs a, int P, int warps_per_block) {
     any_tie = __any_sync(0xffffffffu, any_tie);
     for (int p = lane; p < L; p += 32) w.runs[p] = -1;
     __syncwarp();
-    const double ffw = 2.5 * ff_rel_bound(d);
+    // d64 of a re-checked entry: its float-float value (packed), or its float64
+    // value when dbl (some run entry needed the float64 tier)
+    bool dbl = false;
     if (any_tie) {
         if (lane == 0) {
             int p = 0, nr = 0;
@@ -693,18 +719,29 @@ finalize_kernel(FinalizeArgs a, int P, int warps_per_block) {
         for (int p = lane, i = 0; p < L; p += 32, ++i) {
             const int s0 = w.runs[p];
             if (s0 < 0) continue;
-            const double vp = bitsd(w.d64[p]);
+            const uint64_t vp = w.d64[p];
             for (int x = s0; x <= w.rend[p]; ++x) {
                 if (x == p) continue;
-                const double vx = bitsd(w.d64[x]);
-                if (fabs(vx - vp) <= ffw * fmax(vx, vp) + 1e-300) { mark |= 1ull << i; break; }
+                const uint64_t vx = w.d64[x];
+                const float diff = __fsub_rn(ff_hi(vx), ff_hi(vp)) + (ff_lo(vx) - ff_lo(vp));
+                if (fabsf(diff) <= a.ffw * fmaxf(ff_hi(vx), ff_hi(vp)) + 1e-37f) { mark |= 1ull << i; break; }
             }
         }
+        dbl = __any_sync(0xffffffffu, mark != 0);
         __syncwarp();
-        for (int p = lane, i = 0; p < L; p += 32, ++i) {
-            if ((mark >> i) & 1ull) {
-                const uint32_t j = key_idx(w.sorted[p]);
-                w.d64[p] = dbits(dist_f64<METRIC>(w.qrow, a.R + static_cast<int64_t>(j) * d, d));
+        if (dbl) {
+            // rare: every run entry as a float64 value, exact float-float sums
+            // or the oracle's own arithmetic for the marked ones
+            for (int p = lane, i = 0; p < L; p += 32, ++i) {
+                if (w.runs[p] < 0) continue;
+                double v;
+                if ((mark >> i) & 1ull) {
+                    const uint32_t j = key_idx(w.sorted[p]);
+                    v = dist_f64<METRIC>(w.qrow, a.R + static_cast<int64_t>(j) * d, d);
+                } else {
+                    v = static_cast<double>(ff_hi(w.d64[p])) + static_cast<double>(ff_lo(w.d64[p]));
+                }
+                w.d64[p] = dbits(v);
             }
         }
         __syncwarp();
@@ -717,7 +754,8 @@ finalize_kernel(FinalizeArgs a, int P, int warps_per_block) {
                 for (int x = s0; x <= w.rend[p]; ++x) {
                     const uint64_t o = w.d64[x];
                     const uint32_t oj = key_idx(w.sorted[x]);
-                    rank += (o < mine || (o == mine && oj < mj)) ? 1 : 0;
+                    const bool less = dbl ? (o < mine) : ff_less(o, mine);
+                    rank += (less || (o == mine && oj < mj)) ? 1 : 0;
                 }
                 w.perm[s0 + rank] = p;
             }
@@ -726,11 +764,16 @@ finalize_kernel(FinalizeArgs a, int P, int warps_per_block) {
         if (lane == 0 && nr > 0 && a.recheck_counter)
             atomicAdd(a.recheck_counter, static_cast<unsigned long long>(nr));
     }
+    // refined distance of a re-checked entry
+    auto refined = [&](uint64_t v) {
+        return dbl ? static_cast<float>(bitsd(v)) : __fadd_rn(ff_hi(v), ff_lo(v));
+    };
     auto source_of = [&](int s) { return (w.runs[s] >= 0) ? w.perm[s] : s; };
 
     // 4. completeness of a float32 candidate set: the references left out by a
     //    split have keys >= that split's largest kept key
     if (!a.use_hits && a.cand.exact && kk > 0) {
+        const double rel = a.rel;
         const CandidateSet& cs = a.cand;
         bool have = false;
         double lower = 0.0;
@@ -746,7 +789,7 @@ finalize_kernel(FinalizeArgs a, int P, int warps_per_block) {
         if (have) {
             const int sk = source_of(kk - 1);
             const double upper = (w.runs[kk - 1] >= 0)
-                                     ? bitsd(w.d64[sk]) * (1.0 + ffw)
+                                     ? static_cast<double>(refined(w.d64[sk])) * (1.0 + 1e-6)
                                      : static_cast<double>(key_dist(w.sorted[sk])) * (1.0 + rel);
             if (!(lower > upper) || kk < k) {
                 if (lane == 0) queue_fallback(a, q, 3);
@@ -763,8 +806,8 @@ finalize_kernel(FinalizeArgs a, int P, int warps_per_block) {
             const int sp = source_of(s);
             idx = static_cast<int32_t>(key_idx(w.sorted[sp]));
             if (w.runs[s] >= 0) {
-                const double v = bitsd(w.d64[sp]);
-                dist = (METRIC == kL2) ? static_cast<float>(__dsqrt_rn(v)) : static_cast<float>(v);
+                const float v = refined(w.d64[sp]);
+                dist = (METRIC == kL2) ? sqrtf(v) : v;
             } else {
                 const float v = key_dist(w.sorted[sp]);
                 dist = (METRIC == kL2) ? sqrtf(v) : v;
@@ -946,7 +989,11 @@ cudaError_t launch_finalize_m(const FinalizeArgs& a, int nv, int P, int wpb, siz
     }
 }
 
-cudaError_t launch_finalize(const FinalizeArgs& a, cudaStream_t st, int* launches) {
+cudaError_t launch_finalize(const FinalizeArgs& a_in, cudaStream_t st, int* launches) {
+    FinalizeArgs a = a_in;
+    a.rel = f32_rel_bound(a.d);
+    a.relf = static_cast<float>(2.02 * a.rel);
+    a.ffw = static_cast<float>(2.5 * ff_rel_bound(a.d));
     int P = a.use_hits ? 2 * a.hits.c + 32 : a.cand.S * a.cand.c;
     P = (P + 3) & ~3;
     if (P > kMaxPool) return cudaErrorInvalidValue;

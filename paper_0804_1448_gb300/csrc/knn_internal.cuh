@@ -102,6 +102,11 @@ struct FinalizeArgs {
     unsigned long long* recheck_counter;
     unsigned long long* fallback_total;
     unsigned long long* fallback_reason;   // [4]: short list, overflow, wide cut, uncertified
+    // rounding bounds for this d, set by launch_finalize: float32 distance
+    // (relative), its near-tie window as a float, and the float-float window
+    double rel;
+    float relf;
+    float ffw;
 };
 
 // ---- launchers (return cudaSuccess or the launch error) -------------------

@@ -399,35 +399,37 @@ __global__ void prepare_kernel(const float* __restrict__ X, int64_t rows, int32_
 
 // One warp per query: the cprime-th largest group maximum of the pilot becomes
 // the query's threshold, written into its threshold words with a margin that
-// covers the rounding difference between the pilot and filter products.
-template <int PREC>
+// covers the rounding difference between the pilot and filter products.  The
+// maxima (order-mapped, 0 = no group) sit in registers, VPL per lane; the
+// order statistic is found bit by bit from the top (is the count of values
+// >= prefix|bit at least cprime?) down to bit 8.  Stopping there leaves a
+// value at most 2^8 order steps (2^-15 relative) below the exact one: a
+// slightly lower threshold, so never fewer passing references.
+template <int PREC, int VPL>
 __global__ void threshold_kernel(const uint32_t* __restrict__ gmax, int64_t n, int32_t G,
                                  int32_t cprime, int32_t d, int32_t kp, void* __restrict__ Q_lp) {
-    extern __shared__ uint32_t vals[];
     const int wib = threadIdx.x / 32, lane = threadIdx.x % 32;
     const int64_t q = static_cast<int64_t>(blockIdx.x) * (blockDim.x / 32) + wib;
     if (q >= n) return;
-    uint32_t* v = vals + wib * G;
-    for (int g = lane; g < G; g += 32) v[g] = gmax[q * G + g];
-    __syncwarp();
-    uint32_t best = 0, least = 0xffffffffu;
-    for (int g = lane; g < G; g += 32)
-        if (v[g] != 0) least = min(least, v[g]);
-    for (int o = 16; o > 0; o >>= 1) least = min(least, __shfl_xor_sync(0xffffffffu, least, o));
-    for (int rep = 0; rep < cprime; ++rep) {
-        uint32_t mx = 0;
-        int at = -1;
-        for (int g = lane; g < G; g += 32)
-            if (v[g] > mx) { mx = v[g]; at = g; }
-        uint32_t wmx = mx;
-        for (int o = 16; o > 0; o >>= 1) wmx = max(wmx, __shfl_xor_sync(0xffffffffu, wmx, o));
-        if (wmx == 0) break;
-        const unsigned own = __ballot_sync(0xffffffffu, mx == wmx && at >= 0);
-        if (lane == __ffs(own) - 1) v[at] = 0;
-        __syncwarp();
-        best = wmx;
+    const uint32_t* src = gmax + q * G;
+    uint32_t v[VPL];
+    uint32_t least = 0xffffffffu;
+#pragma unroll
+    for (int i = 0; i < VPL; ++i) {
+        const int g = i * 32 + lane;
+        v[i] = (g < G) ? src[g] : 0u;
+        if (v[i] != 0u) least = min(least, v[i]);
     }
-    if (best == 0) best = least;   // fewer groups than cprime: weakest group seen
+    least = __reduce_min_sync(0xffffffffu, least);
+    uint32_t prefix = 0;
+    for (int b = 31; b >= 8; --b) {
+        const uint32_t cand = prefix | (1u << b);
+        int c = 0;
+#pragma unroll
+        for (int i = 0; i < VPL; ++i) c += (v[i] >= cand) ? 1 : 0;
+        if (__reduce_add_sync(0xffffffffu, c) >= cprime) prefix = cand;
+    }
+    const uint32_t best = prefix ? prefix : least;   // fewer than cprime groups: the weakest
     const float t_acc = unord_f32(best);
     const float tcol = -t_acc + 1e-3f * (1.f + fabsf(t_acc));
     const float hi = lowp_round<PREC>(tcol);
@@ -642,17 +644,34 @@ cudaError_t launch_tc_pilot(const TcPlan& p, const void* Q_lp, int64_t n, const 
     return dispatch<true>(p, prec, mq, mr, a, st);
 }
 
+template <int PREC, int VPL>
+void launch_threshold_vpl(const TcPlan& p, const uint32_t* gmax, int64_t n, int32_t d, int32_t kp,
+                          void* Q_lp, cudaStream_t st) {
+    constexpr int wpb = 8;
+    const unsigned grid = static_cast<unsigned>((n + wpb - 1) / wpb);
+    threshold_kernel<PREC, VPL><<<grid, wpb * 32, 0, st>>>(gmax, n, p.G, p.cprime, d, kp, Q_lp);
+}
+
+template <int PREC>
+cudaError_t launch_threshold_p(const TcPlan& p, const uint32_t* gmax, int64_t n, int32_t d,
+                               int32_t kp, void* Q_lp, cudaStream_t st) {
+    const int vpl = (p.G + 31) / 32;
+    if (vpl <= 1) launch_threshold_vpl<PREC, 1>(p, gmax, n, d, kp, Q_lp, st);
+    else if (vpl <= 2) launch_threshold_vpl<PREC, 2>(p, gmax, n, d, kp, Q_lp, st);
+    else if (vpl <= 4) launch_threshold_vpl<PREC, 4>(p, gmax, n, d, kp, Q_lp, st);
+    else if (vpl <= 8) launch_threshold_vpl<PREC, 8>(p, gmax, n, d, kp, Q_lp, st);
+    else if (vpl <= 16) launch_threshold_vpl<PREC, 16>(p, gmax, n, d, kp, Q_lp, st);
+    else if (vpl <= 32) launch_threshold_vpl<PREC, 32>(p, gmax, n, d, kp, Q_lp, st);
+    else if (vpl <= 64) launch_threshold_vpl<PREC, 64>(p, gmax, n, d, kp, Q_lp, st);
+    else return cudaErrorInvalidValue;
+    return cudaGetLastError();
+}
+
 cudaError_t launch_tc_threshold(const TcPlan& p, const uint32_t* gmax, int64_t n, int32_t d,
                                 int32_t kp, int prec, void* Q_lp, cudaStream_t st, int* launches) {
-    const int wpb = 4;
-    const size_t smem = static_cast<size_t>(wpb) * p.G * 4;
-    const unsigned grid = static_cast<unsigned>((n + wpb - 1) / wpb);
-    if (prec == kBF16)
-        threshold_kernel<kBF16><<<grid, wpb * 32, smem, st>>>(gmax, n, p.G, p.cprime, d, kp, Q_lp);
-    else
-        threshold_kernel<kTF32><<<grid, wpb * 32, smem, st>>>(gmax, n, p.G, p.cprime, d, kp, Q_lp);
     if (launches) ++*launches;
-    return cudaGetLastError();
+    if (prec == kBF16) return launch_threshold_p<kBF16>(p, gmax, n, d, kp, Q_lp, st);
+    return launch_threshold_p<kTF32>(p, gmax, n, d, kp, Q_lp, st);
 }
 
 cudaError_t launch_tc_filter(const TcPlan& p, const void* Q_lp, int64_t n, const void* R_lp, int64_t m,
