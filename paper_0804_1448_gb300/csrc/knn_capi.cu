@@ -23,6 +23,7 @@ struct Counters {
     unsigned long long recheck_total;       // float64 re-checked candidates
     unsigned long long fallback_total;      // queries finished by the fallback
     unsigned long long fallback_reason[4];  // short list, overflow, wide cut, uncertified
+    uint32_t rmax2;                         // largest squared reference norm (float bits)
 };
 
 }  // namespace
@@ -140,7 +141,8 @@ knn_status build_lowp(knn_ctx* h, int prec) {
     const size_t elt = (prec == kBF16) ? 2 : 4;
     KNN_CUDA(h, cudaMalloc(&h->R_lp, static_cast<size_t>(h->m) * kp * elt));
     int l = 0;
-    KNN_CUDA(h, launch_prepare_ref(h->R, h->m, h->d, kp, prec, h->R_lp, h->r_norms, h->stream, &l));
+    KNN_CUDA(h, launch_prepare_ref(h->R, h->m, h->d, kp, prec, h->R_lp, h->r_norms,
+                                   &h->counters->rmax2, h->stream, &l));
     h->launches += l;
     KNN_CUDA(h, cudaStreamSynchronize(h->stream));
     h->kp = kp;
@@ -319,12 +321,13 @@ knn_status knn_search(knn_handle h, const float* Q, int64_t n, int32_t d, int32_
 
     // workspace layout
     Carve cv;
-    size_t off_cand = 0, off_ql = 0, off_gmax = 0, off_lists = 0, off_counts = 0;
+    size_t off_cand = 0, off_ql = 0, off_gmax = 0, off_lists = 0, off_counts = 0, off_qs = 0;
     if (tensor) {
         off_ql = cv.take(static_cast<size_t>(n) * h->kp * (prec == kBF16 ? 2 : 4));
         if (plan.pilot) off_gmax = cv.take(static_cast<size_t>(n) * plan.G * 4);
         off_lists = cv.take(static_cast<size_t>(n) * S * plan.groups * plan.cap * sizeof(uint64_t));
         off_counts = cv.take(static_cast<size_t>(n) * S * plan.groups * sizeof(int32_t));
+        off_qs = cv.take(static_cast<size_t>(n) * sizeof(float));
     } else {
         off_cand = cv.take(static_cast<size_t>(n) * S * c * sizeof(uint64_t));
     }
@@ -362,17 +365,22 @@ knn_status knn_search(knn_handle h, const float* Q, int64_t n, int32_t d, int32_
         void* Ql = ws + off_ql;
         uint64_t* lists = reinterpret_cast<uint64_t*>(ws + off_lists);
         int32_t* counts = reinterpret_cast<int32_t*>(ws + off_counts);
-        KNN_CUDA(h, launch_prepare_query(Qd, n, d, h->kp, prec, Ql, st, &l));
+        HitScale qs;
+        qs.rmax2 = &ctr->rmax2;
+        qs.qscale = reinterpret_cast<float*>(ws + off_qs);
+        HitScale qs_prep = qs;   // the threshold pass sets B when there is one
+        if (plan.pilot) qs_prep.qscale = nullptr;
+        KNN_CUDA(h, launch_prepare_query(Qd, n, d, h->kp, prec, Ql, qs_prep, st, &l));
         stage(h, st, "prepare_q");
         if (plan.pilot) {
             uint32_t* gmax = reinterpret_cast<uint32_t*>(ws + off_gmax);
             KNN_CUDA(h, launch_tc_pilot(plan, Ql, n, h->R_lp, m, h->kp, prec, gmax, &ctr->error_flag,
                                         st, &l));
             stage(h, st, "tc_pilot");
-            KNN_CUDA(h, launch_tc_threshold(plan, gmax, n, d, h->kp, prec, Ql, st, &l));
+            KNN_CUDA(h, launch_tc_threshold(plan, gmax, n, d, h->kp, prec, Ql, qs, st, &l));
             stage(h, st, "tc_threshold");
         }
-        KNN_CUDA(h, launch_tc_filter(plan, Ql, n, h->R_lp, m, h->kp, prec, lists, counts,
+        KNN_CUDA(h, launch_tc_filter(plan, Ql, n, h->R_lp, m, h->kp, prec, lists, counts, qs.qscale,
                                      &ctr->error_flag, st, &l));
         stage(h, st, "tc_filter");
         fa.use_hits = 1;

@@ -368,6 +368,13 @@ __device__ void gather_cand(const FinalizeArgs& a, int64_t q, WarpScratch& w, in
     exact_keys<METRIC, NV>(w.keys, Sc, a.R, a.d, w.qrow, lane);
 }
 
+// The score of a hit-list key: its high word, a code in [0, 0xffff] that
+// falls linearly with the low-precision score, as a float (exact: the code
+// sits in the mantissa of 2^23 + code).
+__device__ __forceinline__ float hit_val(uint32_t hi) {
+    return __uint_as_float(0x4B000000u | hi) - 8388608.f;
+}
+
 // First-level histogram over [vmin, vmax]: inv = (kBins - 0.51) / (vmax - vmin),
 // so (v - lo) * inv lies in [0, kBins - 0.51] and one fused multiply-add onto
 // 1.5 * 2^23 rounds it to an integer held in the low mantissa bits.
@@ -470,12 +477,12 @@ __device__ int gather_hits_impl(const FinalizeArgs& a, int64_t q, int P, WarpScr
         if constexpr (STAGED) {
 #pragma unroll
             for (int i = 0; i < kRegHits; ++i)
-                if (i * 32 + lane < total) f(unord_f32(hv[i]));
+                if (i * 32 + lane < total) f(hit_val(hv[i]));
         } else {
             for (int s = 0; s < S; ++s) {
                 const int cs = min(cnts[s], cap);
                 const uint64_t* sp = base + static_cast<int64_t>(s) * cap;
-                for (int e = lane; e < cs; e += 32) f(key_dist(sp[e]));
+                for (int e = lane; e < cs; e += 32) f(hit_val(static_cast<uint32_t>(sp[e] >> 32)));
             }
         }
     };
@@ -524,7 +531,7 @@ __device__ int gather_hits_impl(const FinalizeArgs& a, int64_t q, int P, WarpScr
 #pragma unroll
         for (int i = 0; i < kRegHits; ++i) {
             const int e = i * 32 + lane;
-            const bool take = e < total && keep(unord_f32(hv[i]));
+            const bool take = e < total && keep(hit_val(hv[i]));
             const unsigned bal = __ballot_sync(0xffffffffu, take);
             const int pos = kept + __popc(bal & ((1u << lane) - 1u));
             if (take && pos < P) w.keys[pos] = static_cast<uint32_t>(w.stage[e]);
@@ -538,7 +545,7 @@ __device__ int gather_hits_impl(const FinalizeArgs& a, int64_t q, int P, WarpScr
             const uint64_t* sp = base + static_cast<int64_t>(s) * cap;
             for (int e = lane; e < cs; e += 32) {
                 const uint64_t key = sp[e];
-                if (keep(key_dist(key))) {
+                if (keep(hit_val(static_cast<uint32_t>(key >> 32)))) {
                     const int pos = atomicAdd(&w.hist[kBins], 1);
                     if (pos < P) w.keys[pos] = key_idx(key);
                 }

@@ -75,9 +75,10 @@ struct CandidateSet {
 };
 
 // Per-query lists of references that passed the tensor-core filter (S lists
-// per query: one per reference split and epilogue half); keys rank by the
-// low-precision score (smaller key = nearer).  counts may exceed cap, meaning
-// the list overflowed.
+// per query: one per reference split and epilogue column group).  A key is
+// (code, index) with code in [0, 0xffff] falling linearly with the
+// low-precision score (smaller code = nearer).  counts may exceed cap,
+// meaning the list overflowed.
 struct HitLists {
     const uint64_t* keys;   // [n][S][cap]
     const int32_t* counts;  // [n][S]
@@ -157,19 +158,31 @@ struct TcPlan {
 };
 TcPlan tc_plan(int64_t n, int64_t m, int32_t d, int32_t kp, int prec, int32_t c, int num_sms);
 
-// Reference copy [r, -||r||^2/2 (hi, lo), 1, 1, 0..] and float32 norms.
+// Per-query scale of the 16-bit hit codes (a power of two B > |acc|): the
+// largest squared reference norm (float bits, set by launch_prepare_ref) and
+// the queries' B, set by launch_tc_threshold once t is known, or by
+// launch_prepare_query for t = 0 when qscale is passed there (no threshold).
+struct HitScale {
+    const uint32_t* rmax2;
+    float* qscale;   // [n]
+};
+
+// Reference copy [r, -||r||^2/2 (hi, lo), 1, 1, 0..], float32 norms and their maximum.
 cudaError_t launch_prepare_ref(const float* R, int64_t m, int32_t d, int32_t kp, int prec,
-                               void* R_lp, float* norms, cudaStream_t st, int* launches);
+                               void* R_lp, float* norms, uint32_t* rmax2, cudaStream_t st,
+                               int* launches);
 // Query copy [q, 1, 1, 0, 0, 0..] (threshold words filled by the threshold pass).
 cudaError_t launch_prepare_query(const float* Q, int64_t n, int32_t d, int32_t kp, int prec,
-                                 void* Q_lp, cudaStream_t st, int* launches);
+                                 void* Q_lp, const HitScale& qs, cudaStream_t st, int* launches);
 cudaError_t launch_tc_pilot(const TcPlan& p, const void* Q_lp, int64_t n, const void* R_lp,
                             int64_t m, int32_t kp, int prec, uint32_t* gmax, int32_t* error_flag,
                             cudaStream_t st, int* launches);
 cudaError_t launch_tc_threshold(const TcPlan& p, const uint32_t* gmax, int64_t n, int32_t d,
-                                int32_t kp, int prec, void* Q_lp, cudaStream_t st, int* launches);
+                                int32_t kp, int prec, void* Q_lp, const HitScale& qs,
+                                cudaStream_t st, int* launches);
 cudaError_t launch_tc_filter(const TcPlan& p, const void* Q_lp, int64_t n, const void* R_lp,
                              int64_t m, int32_t kp, int prec, uint64_t* lists, int32_t* counts,
-                             int32_t* error_flag, cudaStream_t st, int* launches);
+                             const float* qscale, int32_t* error_flag, cudaStream_t st,
+                             int* launches);
 
 }  // namespace knn

@@ -86,6 +86,7 @@ struct TcArgs {
     int32_t* counts;      // filter: [n][S][kGroups] (may exceed cap: overflow)
     int32_t cap;
     int32_t append_all;   // filter: every valid reference passes
+    const float* qscale;  // filter: per-query B, a power of two with |acc| < B
     int32_t* error_flag;
 };
 
@@ -97,14 +98,26 @@ __host__ __device__ constexpr size_t tc_smem_bytes(int kb, int kbs, int stages, 
            (pilot ? 0 : static_cast<size_t>(kEpi) * kStageWords * 4) + 512;
 }
 
-// Append one passing reference to a hit list.  key = (order of -acc, index):
-// a threshold pass has acc >= +0, so the order of -acc is ~bits(acc) without
-// its sign bit; without a threshold acc may have either sign.  vb holds the
-// upper 16 bits of acc's float32 bits (the lower ones are zero).
-__device__ __forceinline__ void append(uint64_t* list, int& cnt, int cap, uint32_t vb, uint32_t j,
-                                       int append_all) {
-    const uint32_t o = append_all ? ord_f32(-__uint_as_float(vb)) : (~vb & 0x7fffffffu);
-    if (cnt < cap) list[cnt] = (static_cast<uint64_t>(o) << 32) | j;
+// Hit values are kept as a 16-bit code of acc: with B a power of two and
+// |acc| < B, acc + 3B lies in [2B, 4B), one binade, so bits 8..23 of its
+// float32 pattern (the low exponent bit, constant there, and the top 15
+// mantissa bits) grow with acc in steps of B 2^-14.  The list key is
+// (0xffff - code, index): smaller is nearer, and the finalize reads
+// 0xffff - code back as a plain number.
+// The codes of two accumulator words x0, x1 (acc bits) packed into one word
+// (x0's in the low half): one two-lane float32 add of 3B, then bytes 1-2 of
+// each sum.
+__device__ __forceinline__ uint32_t hit_code2(uint32_t x0, uint32_t x1, uint32_t off3b) {
+    uint32_t y0, y1;
+    asm("{\n .reg .b64 a, b;\n mov.b64 a, {%2, %3};\n mov.b64 b, {%4, %4};\n"
+        " add.rn.f32x2 a, a, b;\n mov.b64 {%0, %1}, a;\n}"
+        : "=r"(y0), "=r"(y1)
+        : "r"(x0), "r"(x1), "r"(off3b));
+    return __byte_perm(y0, y1, 0x6521);
+}
+
+__device__ __forceinline__ void append(uint64_t* list, int& cnt, int cap, uint32_t code, uint32_t j) {
+    if (cnt < cap) list[cnt] = (static_cast<uint64_t>(0xffffu - code) << 32) | j;
     ++cnt;
 }
 
@@ -271,6 +284,7 @@ tc_kernel(const __grid_constant__ CUtensorMap tmap_q, const __grid_constant__ CU
         uint32_t* gout = nullptr;
         if (PILOT) gout = a.gmax + q * a.G + static_cast<int64_t>(split) * a.spt * gpt;
         else list = a.lists + ((q * a.S + split) * kGroups + cg) * static_cast<int64_t>(a.cap);
+        const uint32_t off3b = __float_as_uint((!PILOT && active) ? 3.f * a.qscale[q] : 0.f);
         int cnt = 0;
         for (int g = 0; g < nt; ++g) {
             const int buf = g & 1;
@@ -321,17 +335,16 @@ tc_kernel(const __grid_constant__ CUtensorMap tmap_q, const __grid_constant__ CU
 #pragma unroll
                         for (int h = 0; h < 4; ++h)
                             reinterpret_cast<uint4*>(st)[h] = make_uint4(
-                                __byte_perm(r[8 * h + 0], r[8 * h + 1], 0x7632),
-                                __byte_perm(r[8 * h + 2], r[8 * h + 3], 0x7632),
-                                __byte_perm(r[8 * h + 4], r[8 * h + 5], 0x7632),
-                                __byte_perm(r[8 * h + 6], r[8 * h + 7], 0x7632));
+                                hit_code2(r[8 * h + 0], r[8 * h + 1], off3b),
+                                hit_code2(r[8 * h + 2], r[8 * h + 3], off3b),
+                                hit_code2(r[8 * h + 4], r[8 * h + 5], off3b),
+                                hit_code2(r[8 * h + 6], r[8 * h + 7], off3b));
                         const uint32_t jb = static_cast<uint32_t>(j0);
                         const uint16_t* st16 = reinterpret_cast<const uint16_t*>(st);
                         do {
                             const int u = __ffs(hits) - 1;
                             hits &= hits - 1;
-                            append(list, cnt, a.cap, static_cast<uint32_t>(st16[u]) << 16, jb + u,
-                                   a.append_all);
+                            append(list, cnt, a.cap, st16[u], jb + u);
                         } while (hits);
                     }
                     __syncwarp();
@@ -360,6 +373,11 @@ __device__ __forceinline__ void put(void* row, int t, float v) {
     }
 }
 template <int PREC>
+__device__ __forceinline__ float get(const void* row, int t) {
+    if (PREC == kBF16) return __bfloat162float(reinterpret_cast<const __nv_bfloat16*>(row)[t]);
+    return __uint_as_float(reinterpret_cast<const uint32_t*>(row)[t]);
+}
+template <int PREC>
 __device__ __forceinline__ float lowp_round(float v) {
     if (PREC == kBF16) return __bfloat162float(__float2bfloat16_rn(v));
     uint32_t b;
@@ -367,11 +385,28 @@ __device__ __forceinline__ float lowp_round(float v) {
     return __uint_as_float(b);
 }
 
-// One warp per row.  REF: [x, -nr_hi/2, -nr_lo/2, 1, 1, 0..] and the float32
-// squared norm; QUERY: [x, 1, 1, 0, 0, 0..] (threshold words filled later).
+// Smallest power of two >= x (x > 0, finite).
+__device__ __forceinline__ float pow2_ceil(float x) {
+    return __uint_as_float((__float_as_uint(x) + 0x007fffffu) & 0x7f800000u);
+}
+
+// The per-query B of the hit codes: |acc| = |q.r - ||r||^2/2 + t| is at most
+// ||q|| ||r|| + ||r||^2/2 + |t|; the low-precision operands move that by well
+// under 1%, and B carries 12.5% and a power-of-two round-up on top.
+__device__ __forceinline__ float hit_scale(float nq2, float rmax2, float t) {
+    const float bound = sqrtf(nq2) * sqrtf(rmax2) + 0.5f * rmax2 + fabsf(t);
+    return pow2_ceil(bound * 1.125f + 1e-30f);
+}
+
+// One warp per row.  REF: [x, -nr_hi/2, -nr_lo/2, 1, 1, 0..], the float32
+// squared norm, and the largest squared norm (atomic maximum on the bits of a
+// non-negative float); QUERY: [x, 1, 1, 0, 0, 0..] (threshold words filled
+// later) and, when qscale is given (no threshold pass follows), the hit-code
+// scale for t = 0.
 template <int PREC, bool REF>
 __global__ void prepare_kernel(const float* __restrict__ X, int64_t rows, int32_t d, int32_t kp,
-                               void* __restrict__ out, float* __restrict__ norms) {
+                               void* __restrict__ out, float* __restrict__ norms,
+                               uint32_t* __restrict__ rmax2, float* __restrict__ qscale) {
     const int64_t r = (static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x) / 32;
     const int lane = threadIdx.x % 32;
     if (r >= rows) return;
@@ -379,10 +414,14 @@ __global__ void prepare_kernel(const float* __restrict__ X, int64_t rows, int32_
     const size_t elt = (PREC == kBF16) ? 2 : 4;
     void* row = static_cast<unsigned char*>(out) + static_cast<size_t>(r) * kp * elt;
     float nr = 0.f;
-    if (REF) {
+    if (REF || qscale) {
         for (int t = lane; t < d; t += 32) nr = fmaf(x[t], x[t], nr);
         for (int o = 16; o > 0; o >>= 1) nr += __shfl_xor_sync(0xffffffffu, nr, o);
-        if (lane == 0 && norms) norms[r] = nr;
+    }
+    if (lane == 0) {
+        if (REF && norms) norms[r] = nr;
+        if (REF && rmax2) atomicMax(rmax2, __float_as_uint(nr));
+        if (!REF && qscale) qscale[r] = hit_scale(nr, __uint_as_float(*rmax2), 0.f);
     }
     const float h = -0.5f * nr;
     const float hi = lowp_round<PREC>(h);
@@ -407,11 +446,21 @@ __global__ void prepare_kernel(const float* __restrict__ X, int64_t rows, int32_
 // slightly lower threshold, so never fewer passing references.
 template <int PREC, int VPL>
 __global__ void threshold_kernel(const uint32_t* __restrict__ gmax, int64_t n, int32_t G,
-                                 int32_t cprime, int32_t d, int32_t kp, void* __restrict__ Q_lp) {
+                                 int32_t cprime, int32_t d, int32_t kp, void* __restrict__ Q_lp,
+                                 const uint32_t* __restrict__ rmax2, float* __restrict__ qscale) {
     const int wib = threadIdx.x / 32, lane = threadIdx.x % 32;
     const int64_t q = static_cast<int64_t>(blockIdx.x) * (blockDim.x / 32) + wib;
     if (q >= n) return;
     const uint32_t* src = gmax + q * G;
+    // squared norm of the (low-precision) query row, for the hit-code scale
+    const size_t elt = (PREC == kBF16) ? 2 : 4;
+    void* row = static_cast<unsigned char*>(Q_lp) + static_cast<size_t>(q) * kp * elt;
+    float nq2 = 0.f;
+    for (int t = lane; t < d; t += 32) {
+        const float x = get<PREC>(row, t);
+        nq2 = fmaf(x, x, nq2);
+    }
+    for (int o = 16; o > 0; o >>= 1) nq2 += __shfl_xor_sync(0xffffffffu, nq2, o);
     uint32_t v[VPL];
     uint32_t least = 0xffffffffu;
 #pragma unroll
@@ -435,10 +484,9 @@ __global__ void threshold_kernel(const uint32_t* __restrict__ gmax, int64_t n, i
     const float hi = lowp_round<PREC>(tcol);
     const float lo = lowp_round<PREC>(tcol - hi);
     if (lane == 0) {
-        const size_t elt = (PREC == kBF16) ? 2 : 4;
-        void* row = static_cast<unsigned char*>(Q_lp) + static_cast<size_t>(q) * kp * elt;
         put<PREC>(row, d + 2, hi);
         put<PREC>(row, d + 3, lo);
+        qscale[q] = hit_scale(nq2, __uint_as_float(*rmax2), tcol);
     }
 }
 
@@ -613,19 +661,28 @@ TcPlan tc_plan(int64_t n, int64_t m, int32_t d, int32_t kp, int prec, int32_t c,
 }
 
 cudaError_t launch_prepare_ref(const float* R, int64_t m, int32_t d, int32_t kp, int prec,
-                               void* R_lp, float* norms, cudaStream_t st, int* launches) {
+                               void* R_lp, float* norms, uint32_t* rmax2, cudaStream_t st,
+                               int* launches) {
+    cudaError_t err = cudaMemsetAsync(rmax2, 0, sizeof(uint32_t), st);
+    if (err != cudaSuccess) return err;
     const unsigned grid = static_cast<unsigned>((m * 32 + 255) / 256);
-    if (prec == kBF16) prepare_kernel<kBF16, true><<<grid, 256, 0, st>>>(R, m, d, kp, R_lp, norms);
-    else prepare_kernel<kTF32, true><<<grid, 256, 0, st>>>(R, m, d, kp, R_lp, norms);
+    if (prec == kBF16)
+        prepare_kernel<kBF16, true><<<grid, 256, 0, st>>>(R, m, d, kp, R_lp, norms, rmax2, nullptr);
+    else
+        prepare_kernel<kTF32, true><<<grid, 256, 0, st>>>(R, m, d, kp, R_lp, norms, rmax2, nullptr);
     if (launches) ++*launches;
     return cudaGetLastError();
 }
 
 cudaError_t launch_prepare_query(const float* Q, int64_t n, int32_t d, int32_t kp, int prec,
-                                 void* Q_lp, cudaStream_t st, int* launches) {
+                                 void* Q_lp, const HitScale& qs, cudaStream_t st, int* launches) {
     const unsigned grid = static_cast<unsigned>((n * 32 + 255) / 256);
-    if (prec == kBF16) prepare_kernel<kBF16, false><<<grid, 256, 0, st>>>(Q, n, d, kp, Q_lp, nullptr);
-    else prepare_kernel<kTF32, false><<<grid, 256, 0, st>>>(Q, n, d, kp, Q_lp, nullptr);
+    if (prec == kBF16)
+        prepare_kernel<kBF16, false><<<grid, 256, 0, st>>>(Q, n, d, kp, Q_lp, nullptr,
+                                                            const_cast<uint32_t*>(qs.rmax2), qs.qscale);
+    else
+        prepare_kernel<kTF32, false><<<grid, 256, 0, st>>>(Q, n, d, kp, Q_lp, nullptr,
+                                                            const_cast<uint32_t*>(qs.rmax2), qs.qscale);
     if (launches) ++*launches;
     return cudaGetLastError();
 }
@@ -646,37 +703,40 @@ cudaError_t launch_tc_pilot(const TcPlan& p, const void* Q_lp, int64_t n, const 
 
 template <int PREC, int VPL>
 void launch_threshold_vpl(const TcPlan& p, const uint32_t* gmax, int64_t n, int32_t d, int32_t kp,
-                          void* Q_lp, cudaStream_t st) {
+                          void* Q_lp, const HitScale& qs, cudaStream_t st) {
     constexpr int wpb = 8;
     const unsigned grid = static_cast<unsigned>((n + wpb - 1) / wpb);
-    threshold_kernel<PREC, VPL><<<grid, wpb * 32, 0, st>>>(gmax, n, p.G, p.cprime, d, kp, Q_lp);
+    threshold_kernel<PREC, VPL><<<grid, wpb * 32, 0, st>>>(gmax, n, p.G, p.cprime, d, kp, Q_lp,
+                                                          qs.rmax2, qs.qscale);
 }
 
 template <int PREC>
 cudaError_t launch_threshold_p(const TcPlan& p, const uint32_t* gmax, int64_t n, int32_t d,
-                               int32_t kp, void* Q_lp, cudaStream_t st) {
+                               int32_t kp, void* Q_lp, const HitScale& qs, cudaStream_t st) {
     const int vpl = (p.G + 31) / 32;
-    if (vpl <= 1) launch_threshold_vpl<PREC, 1>(p, gmax, n, d, kp, Q_lp, st);
-    else if (vpl <= 2) launch_threshold_vpl<PREC, 2>(p, gmax, n, d, kp, Q_lp, st);
-    else if (vpl <= 4) launch_threshold_vpl<PREC, 4>(p, gmax, n, d, kp, Q_lp, st);
-    else if (vpl <= 8) launch_threshold_vpl<PREC, 8>(p, gmax, n, d, kp, Q_lp, st);
-    else if (vpl <= 16) launch_threshold_vpl<PREC, 16>(p, gmax, n, d, kp, Q_lp, st);
-    else if (vpl <= 32) launch_threshold_vpl<PREC, 32>(p, gmax, n, d, kp, Q_lp, st);
-    else if (vpl <= 64) launch_threshold_vpl<PREC, 64>(p, gmax, n, d, kp, Q_lp, st);
+    if (vpl <= 1) launch_threshold_vpl<PREC, 1>(p, gmax, n, d, kp, Q_lp, qs, st);
+    else if (vpl <= 2) launch_threshold_vpl<PREC, 2>(p, gmax, n, d, kp, Q_lp, qs, st);
+    else if (vpl <= 4) launch_threshold_vpl<PREC, 4>(p, gmax, n, d, kp, Q_lp, qs, st);
+    else if (vpl <= 8) launch_threshold_vpl<PREC, 8>(p, gmax, n, d, kp, Q_lp, qs, st);
+    else if (vpl <= 16) launch_threshold_vpl<PREC, 16>(p, gmax, n, d, kp, Q_lp, qs, st);
+    else if (vpl <= 32) launch_threshold_vpl<PREC, 32>(p, gmax, n, d, kp, Q_lp, qs, st);
+    else if (vpl <= 64) launch_threshold_vpl<PREC, 64>(p, gmax, n, d, kp, Q_lp, qs, st);
     else return cudaErrorInvalidValue;
     return cudaGetLastError();
 }
 
 cudaError_t launch_tc_threshold(const TcPlan& p, const uint32_t* gmax, int64_t n, int32_t d,
-                                int32_t kp, int prec, void* Q_lp, cudaStream_t st, int* launches) {
+                                int32_t kp, int prec, void* Q_lp, const HitScale& qs,
+                                cudaStream_t st, int* launches) {
     if (launches) ++*launches;
-    if (prec == kBF16) return launch_threshold_p<kBF16>(p, gmax, n, d, kp, Q_lp, st);
-    return launch_threshold_p<kTF32>(p, gmax, n, d, kp, Q_lp, st);
+    if (prec == kBF16) return launch_threshold_p<kBF16>(p, gmax, n, d, kp, Q_lp, qs, st);
+    return launch_threshold_p<kTF32>(p, gmax, n, d, kp, Q_lp, qs, st);
 }
 
 cudaError_t launch_tc_filter(const TcPlan& p, const void* Q_lp, int64_t n, const void* R_lp, int64_t m,
                              int32_t kp, int prec, uint64_t* lists, int32_t* counts,
-                             int32_t* error_flag, cudaStream_t st, int* launches) {
+                             const float* qscale, int32_t* error_flag, cudaStream_t st,
+                             int* launches) {
     CUtensorMap mq, mr;
     if (!make_map(&mq, Q_lp, n, kp, prec, kBlockM, 0) || !make_map(&mr, R_lp, m, kp, prec, p.rb, p.kbs))
         return cudaErrorInvalidValue;
@@ -684,6 +744,7 @@ cudaError_t launch_tc_filter(const TcPlan& p, const void* Q_lp, int64_t n, const
     a.stride = 1;
     a.lists = lists;
     a.counts = counts;
+    a.qscale = qscale;
     if (launches) ++*launches;
     return dispatch<false>(p, prec, mq, mr, a, st);
 }
