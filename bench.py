@@ -38,6 +38,13 @@ METRIC = ("queries/s & %roofline at n=m=38400,d=96,k=20 (BF16+rerank vs FP32); "
           "serve p50/p99")
 WORKLOAD = "uniform_n38400_d96_k20"
 PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
+# DRAM traffic of one tensor-core filter launch on this workload, from one ncu
+# capture (dram__bytes_read.sum + dram__bytes_write.sum: 40.71 + 90.08 MB; see
+# profiles/tc_filter_uniform_n38400_d96_k20.md), valid only for the kernel
+# source it was measured on (sha256 prefix below); otherwise reported as null.
+FILTER_TRAFFIC_BYTES = 130.78e6
+FILTER_TRAFFIC_SRC = "8228d077b31c3d2a"
+
 FALLBACK_PEAKS = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}
 
 
@@ -105,6 +112,19 @@ class Clocks:
         return {"sm_mhz": statistics.median(sm) if sm else None,
                 "sm_max_mhz": max(smax) if smax else None,
                 "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def filter_traffic(precision):
+    """Measured DRAM bytes per filter launch, or None when the kernel source
+    has changed since the measurement (or for another precision)."""
+    import hashlib
+    src = os.path.join(ROOT, "paper_0804_1448_gb300", "csrc", "knn_tc.cu")
+    try:
+        with open(src, "rb") as f:
+            cur = hashlib.sha256(f.read()).hexdigest()[:16]
+    except OSError:
+        return None
+    return FILTER_TRAFFIC_BYTES if (cur == FILTER_TRAFFIC_SRC and precision == "bf16") else None
 
 
 def load_peaks():
@@ -242,7 +262,7 @@ def main():
     peak = peaks.get("bf16_tflops") if args.precision == "bf16" else peaks.get("bf16_tflops") * 1.1 / 2.25
     roofline = {"bound": "tensor", "kernel": "tc_filter", "achieved": achieved, "peak": peak,
                 "unit": "TFLOP/s", "frac": (achieved / peak) if achieved else None,
-                "traffic": None, "peak_source": f"{peak_src} "
+                "traffic": filter_traffic(args.precision), "peak_source": f"{peak_src} "
                 + ("bf16_tflops (burst)" if args.precision == "bf16"
                    else "bf16_tflops x 1.1/2.25 (nominal tf32:bf16 ratio)"),
                 "kernel_ms": filt_avg, "flops_per_launch": flops}
