@@ -37,6 +37,7 @@ if ROOT not in sys.path:
 METRIC = ("queries/s & %roofline at n=m=38400,d=96,k=20 (BF16+rerank vs FP32); "
           "serve p50/p99")
 WORKLOAD = "uniform_n38400_d96_k20"
+SERVE_WORKLOAD = "serve_m4194304_d96"
 PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
 # DRAM traffic of one tensor-core filter launch on this workload, from one ncu
 # capture (dram__bytes_read.sum + dram__bytes_write.sum: 40.71 + 90.08 MB; see
@@ -57,6 +58,8 @@ def parse_args():
     p.add_argument("--precision", choices=["bf16", "tf32"], default="bf16")
     p.add_argument("--cpu-seconds", type=float, default=10.0)
     p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--no-serve", action="store_true")
+    p.add_argument("--serve-requests", type=int, default=48)
     return p.parse_args()
 
 
@@ -181,6 +184,53 @@ def run_reference(args):
             "e2e": {"value": v, "unit": "queries/s", "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
+
+
+def serve_bench(local, args):
+    """Serving form: resident reference set of 4,194,304 points (d = 96,
+    uniform, float32 + bf16 copy), 4 slots sharing it, query batches of
+    log-uniform size in [1, 8192] with k uniform in [1, 256] (Euclidean, bf16
+    + re-rank).  First all requests at once (saturation queries/s), then
+    Poisson arrivals at 30/70/95% of it; p50/p99 latency of each."""
+    import numpy as np
+    import torch
+    from paper_0804_1448_gb300 import inputs, serve
+    w = inputs.WORKLOADS[SERVE_WORKLOAD]
+    R = inputs.workload_refs(SERVE_WORKLOAD)
+    dev = torch.device("cuda", local)
+    pool = torch.from_numpy(inputs.uniform(w["pool"], w["d"], seed=w["seed_q"])).to(dev)
+    srv = serve.Server(torch.from_numpy(R).to(dev), "bf16", slots=4, n_max=8192, k_max=256,
+                       device=local)
+    del R
+
+    def requests(seed, rate):
+        reqs = serve.workload(args.serve_requests, seed, rate)
+        for r in reqs:
+            off = (r.rid * 7919) % (w["pool"] - r.n + 1)
+            r.queries = pool[off:off + r.n]
+        return reqs
+
+    srv.serve(requests(70, None)[:8])                 # warm-up: kernels loaded, slots primed
+    done, sched, _ = srv.serve(requests(71, None))
+    sat = serve.summary(done)
+    mean_n = float(np.mean([r.n for r in done]))
+    loads = []
+    for i, frac in enumerate((0.30, 0.70, 0.95)):
+        rate = frac * sat["queries_per_s"] / mean_n
+        done, sched, _ = srv.serve(requests(72 + i, rate))
+        s = serve.summary(done)
+        loads.append({"offered_frac": frac, "offered_qps": frac * sat["queries_per_s"],
+                      "achieved_qps": s["queries_per_s"], "p50_ms": s["p50_ms"],
+                      "p99_ms": s["p99_ms"], "requests": s["requests"],
+                      "peak_in_flight": sched.peak_running})
+    srv.close()
+    return {"workload": SERVE_WORKLOAD, "m": w["m"], "d": w["d"], "precision": "bf16",
+            "slots": 4, "batch": "log-uniform [1, 8192]", "k": "uniform [1, 256]",
+            "requests_per_run": args.serve_requests,
+            "saturation_qps": sat["queries_per_s"], "saturation_p50_ms": sat["p50_ms"],
+            "saturation_p99_ms": sat["p99_ms"], "loads": loads,
+            "latency": "GPU completion (CUDA event) minus arrival, one clock",
+            "inputs": "reference set and query pool resident on the device"}
 
 
 def main():
@@ -311,6 +361,8 @@ def main():
             "fp32_value": fp32_value, "speedup_vs_fp32": value / fp32_value,
             "stage_ms": prof, "roofline": roofline, "e2e": e2e, "gpu_launches": launches,
             "fallback_queries_total": stats["fallback_queries"], "clocks": clock_info}
+    if not args.no_serve:
+        line["serve"] = serve_bench(local, args)
     if not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(R, Q, k, args.cpu_seconds)
     print(json.dumps(line), flush=True)

@@ -65,7 +65,7 @@ typedef enum {
     KNN_ERR_CUDA = 3,        /* a CUDA call failed; see knn_last_error() */
     KNN_ERR_TIMEOUT = 4,     /* a bounded device-side wait gave up */
     KNN_ERR_NOREF = 5,       /* knn_search before knn_set_reference */
-    KNN_ERR_BUSY = 6,        /* the handle is in use */
+    KNN_ERR_BUSY = 6,        /* the handle, or its shared reference set, is in use */
     KNN_ERR_UNSUPPORTED = 7  /* valid request outside this build's limits (see KNN_K_MAX) */
 } knn_status;
 
@@ -200,6 +200,42 @@ knn_status knn_get_profile(knn_handle h, float* ms, const char** names, int32_t 
 knn_status knn_search_static(const float* R, int64_t m, const float* Q, int64_t n, int32_t d,
                              int32_t k, knn_metric metric, float* dist_out, int32_t* idx_out,
                              void* cuda_stream);
+
+/*
+ * A second handle on the reference set of `src`, for running searches on it
+ * concurrently (each handle has its own stream, workspace and counters; the
+ * device copy of R, its norms and its bf16/tf32 copy are shared, read-only,
+ * and live until the last handle that uses them is destroyed or given a new
+ * reference set).  This is how a serving loop keeps one resident reference
+ * set and overlaps requests on the GPU; the paper searches one query set at a
+ * time and has no counterpart.  opt may be NULL (src's options); a non-NULL
+ * opt must keep src's precision.  A shared handle cannot switch the shared
+ * set to another low-precision copy (knn_set_precision then returns
+ * KNN_ERR_BUSY); knn_set_reference on it detaches it from the shared set.
+ * Errors: KNN_ERR_INVALID (out or src NULL, precision differs, bad option),
+ * KNN_ERR_OOM, KNN_ERR_CUDA.
+ */
+knn_status knn_create_shared(knn_handle* out, knn_handle src, const knn_options* opt);
+
+/*
+ * Bytes of device workspace that knn_search(h, ..., n, d, k, metric, ...,
+ * io_on_device, ...) needs with h's current reference set and precision
+ * (written to *bytes; 0 for n = 0).  Nothing is allocated or launched.  With
+ * knn_reserve, this lets a caller admit work by memory and keep allocation
+ * out of the search path.
+ * Errors: as knn_search's argument checks (KNN_ERR_INVALID, KNN_ERR_NOREF,
+ * KNN_ERR_UNSUPPORTED); KNN_ERR_INVALID when bytes is NULL.
+ */
+knn_status knn_workspace_size(knn_handle h, int64_t n, int32_t d, int32_t k, knn_metric metric,
+                              int io_on_device, int64_t* bytes);
+
+/*
+ * Grow h's workspace now to at least `bytes` (synchronous), so that later
+ * searches needing no more than that allocate nothing.  Never shrinks it.
+ * Errors: KNN_ERR_INVALID (h NULL, bytes < 0), KNN_ERR_OOM (including over
+ * the handle's workspace_limit), KNN_ERR_CUDA.
+ */
+knn_status knn_reserve(knn_handle h, int64_t bytes);
 
 /* Release the handle and everything it owns.  NULL is accepted. */
 knn_status knn_destroy(knn_handle h);

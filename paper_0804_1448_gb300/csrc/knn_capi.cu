@@ -1,9 +1,10 @@
-// knn_capi.cu -- the C ABI declared in include/knn.h: handle, reference set,
-// workspace and the orchestration of one search (select -> finalize ->
-// fallback), all enqueued on one CUDA stream.
+// knn_capi.cu -- the C ABI declared in include/knn.h: handles, reference sets
+// (shareable between handles), workspace and the orchestration of one search
+// (select -> finalize -> fallback), all enqueued on one CUDA stream.
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <memory>
 #include <new>
 #include <string>
 
@@ -20,10 +21,30 @@ constexpr int kMaxStages = 8;
 struct Counters {
     int32_t fallback_count;                 // queued queries of the current search
     int32_t error_flag;                     // set by a kernel whose bounded wait gave up
-    unsigned long long recheck_total;       // float64 re-checked candidates
+    unsigned long long recheck_total;       // re-checked near-tie candidates
     unsigned long long fallback_total;      // queries finished by the fallback
     unsigned long long fallback_reason[4];  // short list, overflow, wide cut, uncertified
-    uint32_t rmax2;                         // largest squared reference norm (float bits)
+};
+
+// A reference set on the device, shared by every handle created from it with
+// knn_create_shared; freed with the last of them.
+struct RefSet {
+    int device = 0;
+    float* R = nullptr;
+    int64_t m = 0;
+    int32_t d = 0;
+    float* r_norms = nullptr;     // ||r||^2 in float32 (padded to whole tiles)
+    void* R_lp = nullptr;         // bf16 / tf32 operand copy
+    int32_t kp = 0;               // padded row length of R_lp
+    int lp_prec = 0;              // 0: none, kTF32, kBF16
+    uint32_t* rmax2 = nullptr;    // device: largest ||r||^2 (float bits)
+    ~RefSet() {
+        cudaSetDevice(device);
+        if (R) cudaFree(R);
+        if (r_norms) cudaFree(r_norms);
+        if (R_lp) cudaFree(R_lp);
+        if (rmax2) cudaFree(rmax2);
+    }
 };
 
 }  // namespace
@@ -34,16 +55,9 @@ struct knn_ctx {
     cudaStream_t stream = nullptr;
     knn_options opt{};
 
-    // reference set (owned)
-    float* R = nullptr;
-    int64_t m = 0;
-    int32_t d = 0;
-    float* r_norms = nullptr;     // ||r||^2 in float32
-    void* R_lp = nullptr;         // bf16 / tf32 operand copy
-    int32_t kp = 0;               // padded row length of R_lp
-    int lp_prec = 0;              // 0: none, kTF32, kBF16
+    std::shared_ptr<RefSet> ref;   // null until a reference set is given
 
-    // workspace (grown on demand)
+    // workspace (grown on demand, or reserved up front with knn_reserve)
     unsigned char* ws = nullptr;
     size_t ws_bytes = 0;
 
@@ -117,36 +131,28 @@ struct Carve {
     }
 };
 
-void free_reference(knn_ctx* h) {
-    if (h->R) cudaFree(h->R);
-    if (h->r_norms) cudaFree(h->r_norms);
-    if (h->R_lp) cudaFree(h->R_lp);
-    h->R = nullptr;
-    h->r_norms = nullptr;
-    h->R_lp = nullptr;
-    h->m = 0;
-    h->d = 0;
-    h->kp = 0;
-    h->lp_prec = 0;
-}
-
 knn_status build_lowp(knn_ctx* h, int prec) {
-    if (h->lp_prec == prec && h->R_lp) return KNN_OK;
-    if (h->R_lp) {
-        KNN_CUDA(h, cudaFree(h->R_lp));
-        h->R_lp = nullptr;
-        h->lp_prec = 0;
+    RefSet& rs = *h->ref;
+    if (rs.lp_prec == prec && rs.R_lp) return KNN_OK;
+    if (h->ref.use_count() > 1) {
+        h->last_error = "the shared reference set holds another low-precision copy";
+        return KNN_ERR_BUSY;
     }
-    const int kp = tc_padded_dim(h->d, prec);
+    if (rs.R_lp) {
+        KNN_CUDA(h, cudaFree(rs.R_lp));
+        rs.R_lp = nullptr;
+        rs.lp_prec = 0;
+    }
+    const int kp = tc_padded_dim(rs.d, prec);
     const size_t elt = (prec == kBF16) ? 2 : 4;
-    KNN_CUDA(h, cudaMalloc(&h->R_lp, static_cast<size_t>(h->m) * kp * elt));
+    KNN_CUDA(h, cudaMalloc(&rs.R_lp, static_cast<size_t>(rs.m) * kp * elt));
     int l = 0;
-    KNN_CUDA(h, launch_prepare_ref(h->R, h->m, h->d, kp, prec, h->R_lp, h->r_norms,
-                                   &h->counters->rmax2, h->stream, &l));
+    KNN_CUDA(h, launch_prepare_ref(rs.R, rs.m, rs.d, kp, prec, rs.R_lp, rs.r_norms, rs.rmax2,
+                                   h->stream, &l));
     h->launches += l;
     KNN_CUDA(h, cudaStreamSynchronize(h->stream));
-    h->kp = kp;
-    h->lp_prec = prec;
+    rs.kp = kp;
+    rs.lp_prec = prec;
     return KNN_OK;
 }
 
@@ -157,6 +163,114 @@ void stage(knn_ctx* h, cudaStream_t st, const char* name) {
     h->stage_names[h->nstages] = name;
     cudaEventRecord(h->ev[h->nstages + 1], st);
     ++h->nstages;
+}
+
+// Everything a search of n queries decides before it launches: the form, the
+// candidate count, the reference splits and the workspace layout.
+struct SearchPlan {
+    bool tensor = false;
+    int prec = 0;
+    int kp = 0;
+    int c = 0;
+    int S = 1;
+    int64_t chunk = 0;
+    TcPlan plan{};
+    int64_t fb_grid = 1;
+    size_t off_cand = 0, off_ql = 0, off_gmax = 0, off_lists = 0, off_counts = 0, off_qs = 0;
+    size_t off_list = 0, off_scr = 0, off_q = 0, off_dist = 0, off_idx = 0;
+    size_t bytes = 0;
+};
+
+knn_status plan_search(const knn_ctx* h, int64_t n, int32_t k, knn_metric metric, int io_on_device,
+                       SearchPlan* sp) {
+    const RefSet& rs = *h->ref;
+    const int64_t m = rs.m;
+    const int32_t d = rs.d;
+    SearchPlan p;
+    p.tensor = (metric == KNN_L2) && h->opt.precision != KNN_FP32;
+    p.prec = p.tensor ? (h->opt.precision == KNN_BF16 ? kBF16 : kTF32) : 0;
+
+    // candidates per query: k plus a margin (float32), rerank_factor * k (tensor cores)
+    if (p.tensor) {
+        p.c = h->opt.rerank_factor * k;
+        if (p.c > (finalize_max_pool() - 32) / 2) p.c = (finalize_max_pool() - 32) / 2;
+        if (p.c < k) return KNN_ERR_UNSUPPORTED;
+    } else {
+        const int margin = k / 4 > 8 ? k / 4 : 8;
+        p.c = k + margin;
+        if (p.c > cc_max_candidates()) p.c = cc_max_candidates();
+        if (p.c > m) p.c = static_cast<int>(m);
+        if (p.c < k) return KNN_ERR_UNSUPPORTED;
+    }
+
+    // float32 path: reference splits so that enough CTAs fill the GPU, each
+    // split much larger than c, all splits' candidates within one finalize pool
+    if (p.tensor) {
+        p.kp = tc_padded_dim(d, p.prec);
+        p.plan = tc_plan(n, m, d, p.kp, p.prec, p.c, h->num_sms);
+        if (p.plan.stages == 0) return KNN_ERR_UNSUPPORTED;
+        p.S = p.plan.S;
+        p.chunk = p.plan.chunk;
+    } else {
+        int S = 1;
+        const int64_t tiles = (n + 63) / 64;
+        const int64_t want = 2LL * h->num_sms;
+        if (tiles < want) S = ceil_div(want, tiles);
+        const int64_t max_by_size = m / (8LL * p.c);
+        if (S > max_by_size) S = static_cast<int>(max_by_size);
+        if (S < 1) S = 1;
+        while (S > 1 && static_cast<int64_t>(S) * p.c > finalize_max_pool()) --S;
+        int64_t chunk = (m + S - 1) / S;
+        chunk = (chunk + 127) / 128 * 128;
+        S = ceil_div(m, chunk);
+        if (static_cast<int64_t>(S) * p.c > finalize_max_pool()) return KNN_ERR_UNSUPPORTED;
+        p.S = S;
+        p.chunk = chunk;
+    }
+
+    // fallback grid: scratch of grid * m doubles, at most 64 MiB
+    p.fb_grid = (64LL << 20) / (8 * m);
+    if (p.fb_grid > 64) p.fb_grid = 64;
+    if (p.fb_grid < 1) p.fb_grid = 1;
+
+    // workspace layout
+    Carve cv;
+    if (p.tensor) {
+        const size_t elt = (p.prec == kBF16) ? 2 : 4;
+        p.off_ql = cv.take(static_cast<size_t>(n) * p.kp * elt);
+        if (p.plan.pilot) p.off_gmax = cv.take(static_cast<size_t>(n) * p.plan.G * 4);
+        p.off_lists = cv.take(static_cast<size_t>(n) * p.S * p.plan.groups * p.plan.cap *
+                              sizeof(uint64_t));
+        p.off_counts = cv.take(static_cast<size_t>(n) * p.S * p.plan.groups * sizeof(int32_t));
+        p.off_qs = cv.take(static_cast<size_t>(n) * sizeof(float));
+    } else {
+        p.off_cand = cv.take(static_cast<size_t>(n) * p.S * p.c * sizeof(uint64_t));
+    }
+    p.off_list = cv.take(static_cast<size_t>(n) * sizeof(int32_t));
+    p.off_scr = cv.take(static_cast<size_t>(p.fb_grid) * m * sizeof(double));
+    if (!io_on_device) {
+        p.off_q = cv.take(static_cast<size_t>(n) * d * sizeof(float));
+        p.off_dist = cv.take(static_cast<size_t>(n) * k * sizeof(float));
+        p.off_idx = cv.take(static_cast<size_t>(n) * k * sizeof(int32_t));
+    }
+    p.bytes = cv.off;
+    *sp = p;
+    return KNN_OK;
+}
+
+knn_status check_search_args(const knn_ctx* h, int64_t n, int32_t d, int32_t k, knn_metric metric) {
+    if (!h) return KNN_ERR_INVALID;
+    if (n < 0 || k < 1 || (metric != KNN_L2 && metric != KNN_L1)) return KNN_ERR_INVALID;
+    if (!h->ref) return KNN_ERR_NOREF;
+    if (d != h->ref->d || k > h->ref->m) return KNN_ERR_INVALID;
+    if (k > KNN_K_MAX) return KNN_ERR_UNSUPPORTED;
+    if (n > 0x7fffffffLL) return KNN_ERR_UNSUPPORTED;
+    return KNN_OK;
+}
+
+bool valid_options(const knn_options& o) {
+    return !(o.precision < KNN_FP32 || o.precision > KNN_BF16 || o.rerank_factor < 1 ||
+             o.rerank_factor > 64 || o.workspace_limit < 0);
 }
 
 }  // namespace
@@ -170,15 +284,7 @@ void knn_options_default(knn_options* opt) {
     opt->workspace_limit = 0;
 }
 
-knn_status knn_create(knn_handle* out, int device, const knn_options* opt) {
-    if (!out) return KNN_ERR_INVALID;
-    *out = nullptr;
-    knn_options o;
-    knn_options_default(&o);
-    if (opt) o = *opt;
-    if (o.precision < KNN_FP32 || o.precision > KNN_BF16 || o.rerank_factor < 1 ||
-        o.rerank_factor > 64 || o.workspace_limit < 0)
-        return KNN_ERR_INVALID;
+static knn_status new_handle(knn_handle* out, int device, const knn_options& o) {
     int count = 0;
     if (cudaGetDeviceCount(&count) != cudaSuccess || device < 0 || device >= count) {
         (void)cudaGetLastError();
@@ -204,11 +310,37 @@ knn_status knn_create(knn_handle* out, int device, const knn_options* opt) {
     return KNN_OK;
 }
 
+knn_status knn_create(knn_handle* out, int device, const knn_options* opt) {
+    if (!out) return KNN_ERR_INVALID;
+    *out = nullptr;
+    knn_options o;
+    knn_options_default(&o);
+    if (opt) o = *opt;
+    if (!valid_options(o)) return KNN_ERR_INVALID;
+    return new_handle(out, device, o);
+}
+
+knn_status knn_create_shared(knn_handle* out, knn_handle src, const knn_options* opt) {
+    if (!out) return KNN_ERR_INVALID;
+    *out = nullptr;
+    if (!src) return KNN_ERR_INVALID;
+    knn_options o = src->opt;
+    if (opt) {
+        if (opt->precision != src->opt.precision) return KNN_ERR_INVALID;
+        o = *opt;
+    }
+    if (!valid_options(o)) return KNN_ERR_INVALID;
+    knn_status s = new_handle(out, src->device, o);
+    if (s != KNN_OK) return s;
+    (*out)->ref = src->ref;
+    return KNN_OK;
+}
+
 knn_status knn_destroy(knn_handle h) {
     if (!h) return KNN_OK;
     cudaSetDevice(h->device);
     if (h->stream) cudaStreamSynchronize(h->stream);
-    free_reference(h);
+    h->ref.reset();
     if (h->ws) cudaFree(h->ws);
     if (h->counters) cudaFree(h->counters);
     for (int i = 0; i <= kMaxStages; ++i)
@@ -222,24 +354,28 @@ knn_status knn_set_reference(knn_handle h, const float* R, int64_t m, int32_t d,
     if (!h || !R || m < 1 || d < 1 || m > 0x7fffffffLL) return KNN_ERR_INVALID;
     KNN_CUDA(h, cudaSetDevice(h->device));
     KNN_CUDA(h, cudaStreamSynchronize(h->stream));
-    free_reference(h);
+    h->ref.reset();   // a shared set stays with the other handles
+    auto rs = std::make_shared<RefSet>();
+    rs->device = h->device;
     const size_t bytes = static_cast<size_t>(m) * d * sizeof(float);
-    KNN_CUDA(h, cudaMalloc(&h->R, bytes));
-    // norms padded to whole 128-reference tiles (zero beyond m): the tensor-core
-    // epilogue reads them in aligned groups without a bounds check
+    KNN_CUDA(h, cudaMalloc(&rs->R, bytes));
+    // norms padded to whole 128-reference tiles (zero beyond m)
     const size_t mpad = static_cast<size_t>((m + 127) / 128 * 128);
-    KNN_CUDA(h, cudaMalloc(&h->r_norms, mpad * sizeof(float)));
-    KNN_CUDA(h, cudaMemsetAsync(h->r_norms, 0, mpad * sizeof(float), h->stream));
-    KNN_CUDA(h, cudaMemcpyAsync(h->R, R, bytes,
+    KNN_CUDA(h, cudaMalloc(&rs->r_norms, mpad * sizeof(float)));
+    KNN_CUDA(h, cudaMalloc(&rs->rmax2, sizeof(uint32_t)));
+    KNN_CUDA(h, cudaMemsetAsync(rs->r_norms, 0, mpad * sizeof(float), h->stream));
+    KNN_CUDA(h, cudaMemsetAsync(rs->rmax2, 0, sizeof(uint32_t), h->stream));
+    KNN_CUDA(h, cudaMemcpyAsync(rs->R, R, bytes,
                                 r_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
                                 h->stream));
     KNN_CUDA(h, cudaStreamSynchronize(h->stream));
-    h->m = m;
-    h->d = d;
+    rs->m = m;
+    rs->d = d;
+    h->ref = std::move(rs);   // the handle is the set's only owner until it is shared
     if (h->opt.precision != KNN_FP32) {
         knn_status s = build_lowp(h, h->opt.precision == KNN_BF16 ? kBF16 : kTF32);
         if (s != KNN_OK) {
-            free_reference(h);
+            h->ref.reset();
             return s;
         }
     }
@@ -249,99 +385,60 @@ knn_status knn_set_reference(knn_handle h, const float* R, int64_t m, int32_t d,
 knn_status knn_set_precision(knn_handle h, int32_t precision) {
     if (!h || precision < KNN_FP32 || precision > KNN_BF16) return KNN_ERR_INVALID;
     KNN_CUDA(h, cudaSetDevice(h->device));
+    if (precision != KNN_FP32 && h->ref) {
+        const int prec = precision == KNN_BF16 ? kBF16 : kTF32;
+        knn_status s = build_lowp(h, prec);
+        if (s != KNN_OK) return s;
+    }
     h->opt.precision = precision;
-    if (precision != KNN_FP32 && h->R) return build_lowp(h, precision == KNN_BF16 ? kBF16 : kTF32);
     return KNN_OK;
+}
+
+knn_status knn_workspace_size(knn_handle h, int64_t n, int32_t d, int32_t k, knn_metric metric,
+                              int io_on_device, int64_t* bytes) {
+    if (!bytes) return KNN_ERR_INVALID;
+    knn_status s = check_search_args(h, n, d, k, metric);
+    if (s != KNN_OK) return s;
+    if (n == 0) {
+        *bytes = 0;
+        return KNN_OK;
+    }
+    SearchPlan sp;
+    s = plan_search(h, n, k, metric, io_on_device, &sp);
+    if (s != KNN_OK) return s;
+    *bytes = static_cast<int64_t>(sp.bytes);
+    return KNN_OK;
+}
+
+knn_status knn_reserve(knn_handle h, int64_t bytes) {
+    if (!h || bytes < 0) return KNN_ERR_INVALID;
+    KNN_CUDA(h, cudaSetDevice(h->device));
+    return ensure_workspace(h, static_cast<size_t>(bytes));
 }
 
 knn_status knn_search(knn_handle h, const float* Q, int64_t n, int32_t d, int32_t k,
                       knn_metric metric, float* dist_out, int32_t* idx_out, int io_on_device,
                       void* cuda_stream) {
-    if (!h) return KNN_ERR_INVALID;
-    if (n < 0 || k < 1 || (metric != KNN_L2 && metric != KNN_L1)) return KNN_ERR_INVALID;
+    knn_status s0 = check_search_args(h, n, d, k, metric);
+    if (s0 != KNN_OK) return s0;
     if (n > 0 && (!Q || !dist_out || !idx_out)) return KNN_ERR_INVALID;
-    if (!h->R) return KNN_ERR_NOREF;
-    if (d != h->d || k > h->m) return KNN_ERR_INVALID;
-    if (k > KNN_K_MAX) return KNN_ERR_UNSUPPORTED;
     if (n == 0) return KNN_OK;
-    if (n > 0x7fffffffLL) return KNN_ERR_UNSUPPORTED;
     KNN_CUDA(h, cudaSetDevice(h->device));
     cudaStream_t st = cuda_stream ? static_cast<cudaStream_t>(cuda_stream) : h->stream;
+    RefSet& rs = *h->ref;
+    const int64_t m = rs.m;
 
-    const int64_t m = h->m;
-    const bool tensor = (metric == KNN_L2) && h->opt.precision != KNN_FP32;
-    const int prec = tensor ? (h->opt.precision == KNN_BF16 ? kBF16 : kTF32) : 0;
-    if (tensor) {
-        knn_status s = build_lowp(h, prec);
+    SearchPlan sp;
+    knn_status s = plan_search(h, n, k, metric, io_on_device, &sp);
+    if (s != KNN_OK) return s;
+    if (sp.tensor) {
+        s = build_lowp(h, sp.prec);
         if (s != KNN_OK) return s;
     }
-
-    // candidates per query: k plus a margin (float32), rerank_factor * k (tensor cores)
-    int c;
-    if (tensor) {
-        c = h->opt.rerank_factor * k;
-        if (c > (finalize_max_pool() - 32) / 2) c = (finalize_max_pool() - 32) / 2;
-        if (c < k) return KNN_ERR_UNSUPPORTED;
-    } else {
-        const int margin = k / 4 > 8 ? k / 4 : 8;
-        c = k + margin;
-        if (c > cc_max_candidates()) c = cc_max_candidates();
-        if (c > m) c = static_cast<int>(m);
-        if (c < k) return KNN_ERR_UNSUPPORTED;
-    }
-
-    // float32 path: reference splits so that enough CTAs fill the GPU, each
-    // split much larger than c, all splits' candidates within one finalize pool
-    int S = 1;
-    int64_t chunk = m;
-    TcPlan plan{};
-    if (tensor) {
-        plan = tc_plan(n, m, d, h->kp, prec, c, h->num_sms);
-        if (plan.stages == 0) return KNN_ERR_UNSUPPORTED;
-        S = plan.S;
-        chunk = plan.chunk;
-    } else {
-        const int64_t tiles = (n + 63) / 64;
-        const int64_t want = 2LL * h->num_sms;
-        if (tiles < want) S = ceil_div(want, tiles);
-        const int64_t max_by_size = m / (8LL * c);
-        if (S > max_by_size) S = static_cast<int>(max_by_size);
-        if (S < 1) S = 1;
-        while (S > 1 && static_cast<int64_t>(S) * c > finalize_max_pool()) --S;
-        chunk = (m + S - 1) / S;
-        chunk = (chunk + 127) / 128 * 128;
-        S = ceil_div(m, chunk);
-        if (static_cast<int64_t>(S) * c > finalize_max_pool()) return KNN_ERR_UNSUPPORTED;
-    }
-
-    // fallback grid: scratch of grid * m doubles, at most 64 MiB
-    int64_t fb_grid = (64LL << 20) / (8 * m);
-    if (fb_grid > 64) fb_grid = 64;
-    if (fb_grid < 1) fb_grid = 1;
-
-    // workspace layout
-    Carve cv;
-    size_t off_cand = 0, off_ql = 0, off_gmax = 0, off_lists = 0, off_counts = 0, off_qs = 0;
-    if (tensor) {
-        off_ql = cv.take(static_cast<size_t>(n) * h->kp * (prec == kBF16 ? 2 : 4));
-        if (plan.pilot) off_gmax = cv.take(static_cast<size_t>(n) * plan.G * 4);
-        off_lists = cv.take(static_cast<size_t>(n) * S * plan.groups * plan.cap * sizeof(uint64_t));
-        off_counts = cv.take(static_cast<size_t>(n) * S * plan.groups * sizeof(int32_t));
-        off_qs = cv.take(static_cast<size_t>(n) * sizeof(float));
-    } else {
-        off_cand = cv.take(static_cast<size_t>(n) * S * c * sizeof(uint64_t));
-    }
-    const size_t off_list = cv.take(static_cast<size_t>(n) * sizeof(int32_t));
-    const size_t off_scr = cv.take(static_cast<size_t>(fb_grid) * m * sizeof(double));
-    size_t off_q = 0, off_dist = 0, off_idx = 0;
-    if (!io_on_device) {
-        off_q = cv.take(static_cast<size_t>(n) * d * sizeof(float));
-        off_dist = cv.take(static_cast<size_t>(n) * k * sizeof(float));
-        off_idx = cv.take(static_cast<size_t>(n) * k * sizeof(int32_t));
-    }
-    knn_status s = ensure_workspace(h, cv.off);
+    s = ensure_workspace(h, sp.bytes);
     if (s != KNN_OK) return s;
     unsigned char* ws = h->ws;
+    const int S = sp.S, c = sp.c;
 
     const float* Qd = Q;
     float* dd = dist_out;
@@ -349,9 +446,9 @@ knn_status knn_search(knn_handle h, const float* Q, int64_t n, int32_t d, int32_
     h->nstages = 0;
     if (h->profiling) cudaEventRecord(h->ev[0], st);
     if (!io_on_device) {
-        Qd = reinterpret_cast<float*>(ws + off_q);
-        dd = reinterpret_cast<float*>(ws + off_dist);
-        id = reinterpret_cast<int32_t*>(ws + off_idx);
+        Qd = reinterpret_cast<float*>(ws + sp.off_q);
+        dd = reinterpret_cast<float*>(ws + sp.off_dist);
+        id = reinterpret_cast<int32_t*>(ws + sp.off_idx);
         KNN_CUDA(h, cudaMemcpyAsync(const_cast<float*>(Qd), Q, static_cast<size_t>(n) * d * 4,
                                     cudaMemcpyHostToDevice, st));
         stage(h, st, "h2d");
@@ -361,26 +458,28 @@ knn_status knn_search(knn_handle h, const float* Q, int64_t n, int32_t d, int32_
     KNN_CUDA(h, cudaMemsetAsync(&ctr->fallback_count, 0, sizeof(int32_t), st));
     int l = 0;
     FinalizeArgs fa{};
-    if (tensor) {
-        void* Ql = ws + off_ql;
-        uint64_t* lists = reinterpret_cast<uint64_t*>(ws + off_lists);
-        int32_t* counts = reinterpret_cast<int32_t*>(ws + off_counts);
+    if (sp.tensor) {
+        const TcPlan& plan = sp.plan;
+        const int prec = sp.prec;
+        void* Ql = ws + sp.off_ql;
+        uint64_t* lists = reinterpret_cast<uint64_t*>(ws + sp.off_lists);
+        int32_t* counts = reinterpret_cast<int32_t*>(ws + sp.off_counts);
         HitScale qs;
-        qs.rmax2 = &ctr->rmax2;
-        qs.qscale = reinterpret_cast<float*>(ws + off_qs);
+        qs.rmax2 = rs.rmax2;
+        qs.qscale = reinterpret_cast<float*>(ws + sp.off_qs);
         HitScale qs_prep = qs;   // the threshold pass sets B when there is one
         if (plan.pilot) qs_prep.qscale = nullptr;
-        KNN_CUDA(h, launch_prepare_query(Qd, n, d, h->kp, prec, Ql, qs_prep, st, &l));
+        KNN_CUDA(h, launch_prepare_query(Qd, n, d, rs.kp, prec, Ql, qs_prep, st, &l));
         stage(h, st, "prepare_q");
         if (plan.pilot) {
-            uint32_t* gmax = reinterpret_cast<uint32_t*>(ws + off_gmax);
-            KNN_CUDA(h, launch_tc_pilot(plan, Ql, n, h->R_lp, m, h->kp, prec, gmax, &ctr->error_flag,
+            uint32_t* gmax = reinterpret_cast<uint32_t*>(ws + sp.off_gmax);
+            KNN_CUDA(h, launch_tc_pilot(plan, Ql, n, rs.R_lp, m, rs.kp, prec, gmax, &ctr->error_flag,
                                         st, &l));
             stage(h, st, "tc_pilot");
-            KNN_CUDA(h, launch_tc_threshold(plan, gmax, n, d, h->kp, prec, Ql, qs, st, &l));
+            KNN_CUDA(h, launch_tc_threshold(plan, gmax, n, d, rs.kp, prec, Ql, qs, st, &l));
             stage(h, st, "tc_threshold");
         }
-        KNN_CUDA(h, launch_tc_filter(plan, Ql, n, h->R_lp, m, h->kp, prec, lists, counts, qs.qscale,
+        KNN_CUDA(h, launch_tc_filter(plan, Ql, n, rs.R_lp, m, rs.kp, prec, lists, counts, qs.qscale,
                                      &ctr->error_flag, st, &l));
         stage(h, st, "tc_filter");
         fa.use_hits = 1;
@@ -394,19 +493,19 @@ knn_status knn_search(knn_handle h, const float* Q, int64_t n, int32_t d, int32_
         fa.cand.c = c;
     } else {
         CandidateSet cs;
-        cs.keys = reinterpret_cast<uint64_t*>(ws + off_cand);
+        cs.keys = reinterpret_cast<uint64_t*>(ws + sp.off_cand);
         cs.n = n;
         cs.S = S;
         cs.c = c;
-        cs.chunk = chunk;
+        cs.chunk = sp.chunk;
         cs.exact = 1;
-        KNN_CUDA(h, launch_cc_select(Qd, n, h->R, m, d, metric, cs, st, &l));
+        KNN_CUDA(h, launch_cc_select(Qd, n, rs.R, m, d, metric, cs, st, &l));
         stage(h, st, "cc_select");
         fa.use_hits = 0;
         fa.cand = cs;
     }
     fa.Q = Qd;
-    fa.R = h->R;
+    fa.R = rs.R;
     fa.n = n;
     fa.m = m;
     fa.d = d;
@@ -415,14 +514,14 @@ knn_status knn_search(knn_handle h, const float* Q, int64_t n, int32_t d, int32_
     fa.dist_out = dd;
     fa.idx_out = id;
     fa.fallback_count = &ctr->fallback_count;
-    fa.fallback_list = reinterpret_cast<int32_t*>(ws + off_list);
+    fa.fallback_list = reinterpret_cast<int32_t*>(ws + sp.off_list);
     fa.recheck_counter = &ctr->recheck_total;
     fa.fallback_total = &ctr->fallback_total;
     fa.fallback_reason = ctr->fallback_reason;
     KNN_CUDA(h, launch_finalize(fa, st, &l));
     stage(h, st, "finalize");
-    KNN_CUDA(h, launch_fallback(fa, reinterpret_cast<double*>(ws + off_scr),
-                                static_cast<int32_t>(fb_grid), st, &l));
+    KNN_CUDA(h, launch_fallback(fa, reinterpret_cast<double*>(ws + sp.off_scr),
+                                static_cast<int32_t>(sp.fb_grid), st, &l));
     stage(h, st, "fallback");
     h->launches += l;
     h->searches += 1;
@@ -508,7 +607,7 @@ const char* knn_status_string(knn_status s) {
         case KNN_ERR_CUDA: return "CUDA error";
         case KNN_ERR_TIMEOUT: return "device wait timed out";
         case KNN_ERR_NOREF: return "no reference set";
-        case KNN_ERR_BUSY: return "handle busy";
+        case KNN_ERR_BUSY: return "reference set or handle busy";
         case KNN_ERR_UNSUPPORTED: return "unsupported by this build";
     }
     return "unknown status";

@@ -57,7 +57,17 @@ WORKLOADS = {
                                               n_centres=1024, sigma=0.05,
                                               seed_centres=7, seed_r=8, seed_q=9,
                                               dist="mixture"),
+    # serving: a resident reference set; requests draw their queries from a
+    # seeded pool (uniform, like the references)
+    "serve_m4194304_d96": dict(m=4194304, d=96, seed_r=6, seed_q=60, pool=65536,
+                               dist="uniform"),
 }
+
+
+def workload_refs(name: str) -> np.ndarray:
+    """The reference set of a named workload."""
+    w = WORKLOADS[name]
+    return uniform(w["m"], w["d"], w["seed_r"])
 
 
 def workload(name: str):

@@ -64,6 +64,10 @@ _SIGS = {
                                        ctypes.POINTER(ctypes.c_char_p), _i32,
                                        ctypes.POINTER(_i32)]),
     "knn_search_static": (ctypes.c_int, [_P, _i64, _P, _i64, _i32, _i32, ctypes.c_int, _P, _P, _P]),
+    "knn_create_shared": (ctypes.c_int, [ctypes.POINTER(_H), _H, ctypes.POINTER(knn_options)]),
+    "knn_workspace_size": (ctypes.c_int, [_H, _i64, _i32, _i32, ctypes.c_int, ctypes.c_int,
+                                          ctypes.POINTER(_i64)]),
+    "knn_reserve": (ctypes.c_int, [_H, _i64]),
     "knn_destroy": (ctypes.c_int, [_H]),
     "knn_status_string": (ctypes.c_char_p, [ctypes.c_int]),
     "knn_last_error": (ctypes.c_char_p, [_H]),
@@ -84,6 +88,9 @@ knn_get_stats = _lib.knn_get_stats
 knn_set_profiling = _lib.knn_set_profiling
 knn_get_profile = _lib.knn_get_profile
 knn_search_static = _lib.knn_search_static
+knn_create_shared = _lib.knn_create_shared
+knn_workspace_size = _lib.knn_workspace_size
+knn_reserve = _lib.knn_reserve
 knn_destroy = _lib.knn_destroy
 knn_status_string = _lib.knn_status_string
 knn_last_error = _lib.knn_last_error
@@ -132,6 +139,30 @@ class Index:
         self.device = device
         self.m = 0
         self.d = 0
+
+    @classmethod
+    def shared(cls, src: "Index") -> "Index":
+        """Another handle on src's reference set (knn_create_shared): its own
+        stream, workspace and counters, the reference data shared."""
+        ix = cls.__new__(cls)
+        h = _H()
+        st = knn_create_shared(ctypes.byref(h), src.h, None)
+        if st != 0:
+            raise KnnError(st, "knn_create_shared")
+        ix.h = h
+        ix.device = src.device
+        ix.m = src.m
+        ix.d = src.d
+        return ix
+
+    def workspace_size(self, n: int, k: int, metric: str = "l2", io_on_device: bool = True) -> int:
+        b = _i64()
+        self._check(knn_workspace_size(self.h, n, self.d, k, METRICS[metric], 1 if io_on_device else 0,
+                                       ctypes.byref(b)), "knn_workspace_size")
+        return int(b.value)
+
+    def reserve(self, nbytes: int):
+        self._check(knn_reserve(self.h, int(nbytes)), "knn_reserve")
 
     def _check(self, st, what):
         if st != 0:
