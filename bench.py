@@ -59,6 +59,7 @@ def parse_args():
     p.add_argument("--cpu-seconds", type=float, default=10.0)
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-serve", action="store_true")
+    p.add_argument("--no-batch", action="store_true")
     p.add_argument("--serve-requests", type=int, default=48)
     return p.parse_args()
 
@@ -233,6 +234,68 @@ def serve_bench(local, args):
             "inputs": "reference set and query pool resident on the device"}
 
 
+def batch_bench(local, args, peak_tflops):
+    """Batching form: 512 independent instances, m uniform in [1000, 200000],
+    n uniform in [16, 4096], d in {32, 64, 128}, k in {1, 10, 50}, float32
+    uniform data (generated on the device from a fixed seed), Euclidean,
+    bf16 + re-rank.  Timed: one graph launch of the autotuned batch against
+    the same instances enqueued one after another, each planned alone."""
+    import numpy as np
+    import torch
+    from paper_0804_1448_gb300 import knn
+    dev = torch.device("cuda", local)
+    g = np.random.Generator(np.random.Philox(5))
+    gen = torch.Generator(device=dev)
+    gen.manual_seed(5)
+    count = 512
+    inst = []
+    flops = 0.0
+    queries = 0
+    for _ in range(count):
+        m = int(g.integers(1000, 200001))
+        n = int(g.integers(16, 4097))
+        d = int(g.choice([32, 64, 128]))
+        k = int(g.choice([1, 10, 50]))
+        R = torch.rand((m, d), generator=gen, device=dev)
+        Q = torch.rand((n, d), generator=gen, device=dev)
+        inst.append(dict(R=R, Q=Q, k=k, dist=torch.empty((n, k), device=dev),
+                         idx=torch.empty((n, k), dtype=torch.int32, device=dev)))
+        flops += 2.0 * n * m * d
+        queries += n
+    ix = knn.Index(local, "bf16")
+    stream = torch.cuda.current_stream(dev)
+
+    def timed(flags, reps):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize(dev)
+        e0.record(stream)
+        for _ in range(reps):
+            ix.search_batch(inst, flags=flags, stream=stream)
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        return e0.elapsed_time(e1) / reps
+
+    ix.search_batch(inst, flags=knn.KNN_BATCH_NO_GRAPH, stream=stream)   # warm-up
+    t_seq = timed(knn.KNN_BATCH_NO_GRAPH, 3)
+    t0 = time.perf_counter()
+    ix.search_batch(inst, flags=knn.KNN_BATCH_AUTOTUNE, stream=stream)   # tunes, captures
+    torch.cuda.synchronize(dev)
+    tune_s = time.perf_counter() - t0
+    tuned = ix.batch_info()
+    t_graph = timed(knn.KNN_BATCH_AUTOTUNE, 5)
+    ix.close()
+    tflops = flops / (t_graph / 1e3) / 1e12
+    return {"workload": "batch_512_uniform", "instances": count, "queries": queries,
+            "flop": flops, "precision": "bf16", "distance": "l2",
+            "graph_ms": t_graph, "queries_per_s": queries / (t_graph / 1e3),
+            "per_instance_ms": t_seq, "per_instance_queries_per_s": queries / (t_seq / 1e3),
+            "speedup_vs_per_instance": t_seq / t_graph,
+            "achieved_tflops": tflops, "frac_of_peak": tflops / peak_tflops if peak_tflops else None,
+            "tuned": {"branches": tuned["branches"], "sm_share": tuned["sm_share"],
+                      "graph_nodes": tuned["graph_nodes"], "launches": tuned["launches"],
+                      "tune_device_ms": tuned["tune_ms"], "tune_wall_s": tune_s}}
+
+
 def main():
     args = parse_args()
     if args.impl == "reference":
@@ -363,6 +426,8 @@ def main():
             "fallback_queries_total": stats["fallback_queries"], "clocks": clock_info}
     if not args.no_serve:
         line["serve"] = serve_bench(local, args)
+    if not args.no_batch:
+        line["batch"] = batch_bench(local, args, peak)
     if not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(R, Q, k, args.cpu_seconds)
     print(json.dumps(line), flush=True)

@@ -237,6 +237,60 @@ knn_status knn_workspace_size(knn_handle h, int64_t n, int32_t d, int32_t k, knn
  */
 knn_status knn_reserve(knn_handle h, int64_t bytes);
 
+/*
+ * Batches: many independent searches (each with its own reference set)
+ * handed over at once.  The paper's problem statement is one search
+ * (Sec. 2.1); a batch is a list of such problems.
+ */
+typedef struct {
+    const float* R;      /* m x d reference set (device) */
+    int64_t m;
+    const float* Q;      /* n x d queries (device); n = 0 is allowed */
+    int64_t n;
+    int32_t d;
+    int32_t k;           /* 1 <= k <= m, k <= KNN_K_MAX */
+    int32_t metric;      /* knn_metric */
+    float* dist_out;     /* n x k (device) */
+    int32_t* idx_out;    /* n x k (device) */
+} knn_instance;
+
+#define KNN_BATCH_AUTOTUNE 1  /* on a batch shape not seen before, time the launch
+                                 configurations and keep the fastest (slower first call) */
+#define KNN_BATCH_NO_GRAPH 2  /* enqueue the instances one after another, each planned
+                                 as a lone search (the one-launch-per-instance form) */
+
+/*
+ * Search every instance of inst[0..count) with the handle's precision and
+ * re-rank factor (the handle's own reference set is not used), results as in
+ * knn_search.  All pointers are device pointers; the call only enqueues work
+ * on cuda_stream (NULL = the handle's stream) and returns (asynchronous).
+ * The instances are planned together, given workspace slices of their own,
+ * and captured into one CUDA graph whose parallel branches run them side by
+ * side (largest first onto the least loaded branch); the graph is cached, so
+ * a repeated batch (same shapes and pointers) is one cudaGraphLaunch.  The
+ * launch configuration (branches, SMs each instance is planned to fill) is
+ * the tuned one for this batch shape when KNN_BATCH_AUTOTUNE found one, else
+ * a default (8 branches, a quarter of the SMs each).  Growing the workspace
+ * drops the cached graphs (they point into it).
+ * Errors: KNN_ERR_INVALID (h NULL, count < 0, inst NULL with count > 0, an
+ * instance with a null pointer, m < 1, d < 1, k < 1, k > m or a bad metric),
+ * KNN_ERR_UNSUPPORTED (k > KNN_K_MAX), KNN_ERR_OOM, KNN_ERR_CUDA.
+ */
+knn_status knn_search_batch(knn_handle h, const knn_instance* inst, int32_t count, int32_t flags,
+                            void* cuda_stream);
+
+/* How the last knn_search_batch ran. */
+typedef struct {
+    int32_t branches;       /* parallel graph branches (1 without a graph) */
+    int32_t sm_share;       /* SMs each instance was planned to fill */
+    int32_t launches;       /* kernels of the batch */
+    int64_t graph_nodes;    /* nodes of its graph (0 without a graph) */
+    int32_t tuned;          /* 1 if that call ran the autotuner */
+    double tune_ms;         /* device time the autotuner spent */
+} knn_batch_info;
+
+knn_status knn_batch_info_get(knn_handle h, knn_batch_info* out);
+
 /* Release the handle and everything it owns.  NULL is accepted. */
 knn_status knn_destroy(knn_handle h);
 

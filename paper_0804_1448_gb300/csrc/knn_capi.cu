@@ -3,8 +3,11 @@
 // (select -> finalize -> fallback), all enqueued on one CUDA stream.
 #include <cstdio>
 #include <cstdlib>
+#include <algorithm>
 #include <cstring>
+#include <map>
 #include <memory>
+#include <vector>
 #include <new>
 #include <string>
 
@@ -71,6 +74,22 @@ struct knn_ctx {
     int nstages = 0;
 
     std::string last_error;
+
+    // batches: captured graphs by batch signature, tuned launch configurations
+    // by batch shape, the streams the captures fork over
+    struct BatchGraph {
+        cudaGraphExec_t exec = nullptr;
+        int branches = 0;
+        int sm_share = 0;
+        int launches = 0;
+        size_t nodes = 0;
+    };
+    std::map<uint64_t, BatchGraph> graphs;
+    std::map<uint64_t, std::pair<int, int>> tuned;   // shape -> (branches, sm_share)
+    cudaStream_t cap_stream = nullptr;
+    cudaStream_t branch[16] = {};
+    cudaEvent_t fork_ev = nullptr, join_ev[16] = {}, t_ev[2] = {};
+    knn_batch_info last_batch{};
 };
 
 namespace {
@@ -94,6 +113,12 @@ bool fault_inject_oom() {
     return v && v[0] == '1';
 }
 
+void drop_graphs(knn_ctx* h) {
+    for (auto& kv : h->graphs)
+        if (kv.second.exec) cudaGraphExecDestroy(kv.second.exec);
+    h->graphs.clear();
+}
+
 // Make sure the handle's workspace holds at least `bytes`.
 knn_status ensure_workspace(knn_ctx* h, size_t bytes) {
     if (bytes <= h->ws_bytes) return KNN_OK;
@@ -105,7 +130,8 @@ knn_status ensure_workspace(knn_ctx* h, size_t bytes) {
         h->last_error = "workspace over the handle's limit";
         return KNN_ERR_OOM;
     }
-    KNN_CUDA(h, cudaStreamSynchronize(h->stream));
+    KNN_CUDA(h, cudaDeviceSynchronize());   // batch graphs may run on other streams
+    drop_graphs(h);                          // they point into the old workspace
     if (h->ws) KNN_CUDA(h, cudaFree(h->ws));
     h->ws = nullptr;
     h->ws_bytes = 0;
@@ -181,14 +207,14 @@ struct SearchPlan {
     size_t bytes = 0;
 };
 
-knn_status plan_search(const knn_ctx* h, int64_t n, int32_t k, knn_metric metric, int io_on_device,
-                       SearchPlan* sp) {
-    const RefSet& rs = *h->ref;
-    const int64_t m = rs.m;
-    const int32_t d = rs.d;
+// sm_share: how many SMs the search should fill on its own (all of them for a
+// lone search; fewer when several run side by side in a batch).
+knn_status plan_search_md(const knn_ctx* h, int64_t m, int32_t d, int precision, int64_t n, int32_t k,
+                          knn_metric metric, int io_on_device, int sm_share, SearchPlan* sp,
+                          int64_t fb_cap_bytes = 64LL << 20) {
     SearchPlan p;
-    p.tensor = (metric == KNN_L2) && h->opt.precision != KNN_FP32;
-    p.prec = p.tensor ? (h->opt.precision == KNN_BF16 ? kBF16 : kTF32) : 0;
+    p.tensor = (metric == KNN_L2) && precision != KNN_FP32;
+    p.prec = p.tensor ? (precision == KNN_BF16 ? kBF16 : kTF32) : 0;
 
     // candidates per query: k plus a margin (float32), rerank_factor * k (tensor cores)
     if (p.tensor) {
@@ -207,14 +233,14 @@ knn_status plan_search(const knn_ctx* h, int64_t n, int32_t k, knn_metric metric
     // split much larger than c, all splits' candidates within one finalize pool
     if (p.tensor) {
         p.kp = tc_padded_dim(d, p.prec);
-        p.plan = tc_plan(n, m, d, p.kp, p.prec, p.c, h->num_sms);
+        p.plan = tc_plan(n, m, d, p.kp, p.prec, p.c, sm_share);
         if (p.plan.stages == 0) return KNN_ERR_UNSUPPORTED;
         p.S = p.plan.S;
         p.chunk = p.plan.chunk;
     } else {
         int S = 1;
         const int64_t tiles = (n + 63) / 64;
-        const int64_t want = 2LL * h->num_sms;
+        const int64_t want = 2LL * sm_share;
         if (tiles < want) S = ceil_div(want, tiles);
         const int64_t max_by_size = m / (8LL * p.c);
         if (S > max_by_size) S = static_cast<int>(max_by_size);
@@ -228,8 +254,8 @@ knn_status plan_search(const knn_ctx* h, int64_t n, int32_t k, knn_metric metric
         p.chunk = chunk;
     }
 
-    // fallback grid: scratch of grid * m doubles, at most 64 MiB
-    p.fb_grid = (64LL << 20) / (8 * m);
+    // fallback grid: scratch of grid * m doubles, at most fb_cap_bytes
+    p.fb_grid = fb_cap_bytes / (8 * m);
     if (p.fb_grid > 64) p.fb_grid = 64;
     if (p.fb_grid < 1) p.fb_grid = 1;
 
@@ -258,6 +284,106 @@ knn_status plan_search(const knn_ctx* h, int64_t n, int32_t k, knn_metric metric
     return KNN_OK;
 }
 
+knn_status plan_search(const knn_ctx* h, int64_t n, int32_t k, knn_metric metric, int io_on_device,
+                       SearchPlan* sp) {
+    return plan_search_md(h, h->ref->m, h->ref->d, h->opt.precision, n, k, metric, io_on_device,
+                          h->num_sms, sp);
+}
+
+// The reference data one search reads: a handle's reference set, or the
+// arrays of a batch instance (prepared inside the batch's own workspace).
+struct RefView {
+    const float* R;
+    int64_t m;
+    int32_t d;
+    void* R_lp;
+    int32_t kp;
+    const uint32_t* rmax2;
+};
+
+// Enqueue the kernels of one planned search on st: Q, dd, id on the device,
+// ws the search's workspace, fallback_count a device int of its own.
+knn_status enqueue_search(knn_ctx* h, const SearchPlan& sp, const RefView& rv, const float* Qd,
+                          int64_t n, int32_t k, knn_metric metric, float* dd, int32_t* id,
+                          unsigned char* ws, int32_t* fallback_count, cudaStream_t st, int* l,
+                          bool stages) {
+    const int64_t m = rv.m;
+    const int32_t d = rv.d;
+    const int S = sp.S, c = sp.c;
+    Counters* ctr = h->counters;
+    auto mark = [&](const char* name) {
+        if (stages) stage(h, st, name);
+    };
+    KNN_CUDA(h, cudaMemsetAsync(fallback_count, 0, sizeof(int32_t), st));
+    FinalizeArgs fa{};
+    if (sp.tensor) {
+        const TcPlan& plan = sp.plan;
+        const int prec = sp.prec;
+        void* Ql = ws + sp.off_ql;
+        uint64_t* lists = reinterpret_cast<uint64_t*>(ws + sp.off_lists);
+        int32_t* counts = reinterpret_cast<int32_t*>(ws + sp.off_counts);
+        HitScale qs;
+        qs.rmax2 = rv.rmax2;
+        qs.qscale = reinterpret_cast<float*>(ws + sp.off_qs);
+        HitScale qs_prep = qs;   // the threshold pass sets B when there is one
+        if (plan.pilot) qs_prep.qscale = nullptr;
+        KNN_CUDA(h, launch_prepare_query(Qd, n, d, rv.kp, prec, Ql, qs_prep, st, l));
+        mark("prepare_q");
+        if (plan.pilot) {
+            uint32_t* gmax = reinterpret_cast<uint32_t*>(ws + sp.off_gmax);
+            KNN_CUDA(h, launch_tc_pilot(plan, Ql, n, rv.R_lp, m, rv.kp, prec, gmax, &ctr->error_flag,
+                                        st, l));
+            mark("tc_pilot");
+            KNN_CUDA(h, launch_tc_threshold(plan, gmax, n, d, rv.kp, prec, Ql, qs, st, l));
+            mark("tc_threshold");
+        }
+        KNN_CUDA(h, launch_tc_filter(plan, Ql, n, rv.R_lp, m, rv.kp, prec, lists, counts, qs.qscale,
+                                     &ctr->error_flag, st, l));
+        mark("tc_filter");
+        fa.use_hits = 1;
+        fa.hits.keys = lists;
+        fa.hits.counts = counts;
+        fa.hits.S = plan.groups * S;   // one list per (split, epilogue column group)
+        fa.hits.cap = plan.cap;
+        fa.hits.c = c;
+        fa.cand.exact = 0;
+        fa.cand.S = 1;
+        fa.cand.c = c;
+    } else {
+        CandidateSet cs;
+        cs.keys = reinterpret_cast<uint64_t*>(ws + sp.off_cand);
+        cs.n = n;
+        cs.S = S;
+        cs.c = c;
+        cs.chunk = sp.chunk;
+        cs.exact = 1;
+        KNN_CUDA(h, launch_cc_select(Qd, n, rv.R, m, d, metric, cs, st, l));
+        mark("cc_select");
+        fa.use_hits = 0;
+        fa.cand = cs;
+    }
+    fa.Q = Qd;
+    fa.R = rv.R;
+    fa.n = n;
+    fa.m = m;
+    fa.d = d;
+    fa.k = k;
+    fa.metric = metric;
+    fa.dist_out = dd;
+    fa.idx_out = id;
+    fa.fallback_count = fallback_count;
+    fa.fallback_list = reinterpret_cast<int32_t*>(ws + sp.off_list);
+    fa.recheck_counter = &ctr->recheck_total;
+    fa.fallback_total = &ctr->fallback_total;
+    fa.fallback_reason = ctr->fallback_reason;
+    KNN_CUDA(h, launch_finalize(fa, st, l));
+    mark("finalize");
+    KNN_CUDA(h, launch_fallback(fa, reinterpret_cast<double*>(ws + sp.off_scr),
+                                static_cast<int32_t>(sp.fb_grid), st, l));
+    mark("fallback");
+    return KNN_OK;
+}
+
 knn_status check_search_args(const knn_ctx* h, int64_t n, int32_t d, int32_t k, knn_metric metric) {
     if (!h) return KNN_ERR_INVALID;
     if (n < 0 || k < 1 || (metric != KNN_L2 && metric != KNN_L1)) return KNN_ERR_INVALID;
@@ -271,6 +397,176 @@ knn_status check_search_args(const knn_ctx* h, int64_t n, int32_t d, int32_t k, 
 bool valid_options(const knn_options& o) {
     return !(o.precision < KNN_FP32 || o.precision > KNN_BF16 || o.rerank_factor < 1 ||
              o.rerank_factor > 64 || o.workspace_limit < 0);
+}
+
+
+// ------------------------------------------------------------------ batches
+
+uint64_t mix64(uint64_t h, uint64_t v) {
+    return h ^ (v + 0x9e3779b97f4a7c15ull + (h << 6) + (h >> 2));
+}
+
+// Shape signature (and, with pointers, the exact batch) of a batch.
+uint64_t batch_signature(const knn_ctx* h, const knn_instance* inst, int32_t count, bool pointers) {
+    uint64_t g = mix64(0x51ed270b27e3c9e5ull, static_cast<uint64_t>(count));
+    g = mix64(g, static_cast<uint64_t>(h->opt.precision) * 131 + h->opt.rerank_factor);
+    for (int32_t i = 0; i < count; ++i) {
+        const knn_instance& x = inst[i];
+        g = mix64(g, static_cast<uint64_t>(x.m));
+        g = mix64(g, static_cast<uint64_t>(x.n));
+        g = mix64(g, (static_cast<uint64_t>(x.d) << 32) | static_cast<uint32_t>(x.k));
+        g = mix64(g, static_cast<uint64_t>(x.metric));
+        if (pointers) {
+            g = mix64(g, reinterpret_cast<uintptr_t>(x.R));
+            g = mix64(g, reinterpret_cast<uintptr_t>(x.Q));
+            g = mix64(g, reinterpret_cast<uintptr_t>(x.dist_out));
+            g = mix64(g, reinterpret_cast<uintptr_t>(x.idx_out));
+        }
+    }
+    return g;
+}
+
+knn_status check_instance(const knn_instance& x) {
+    if (x.n < 0 || x.m < 1 || x.d < 1 || x.k < 1 || x.k > x.m ||
+        (x.metric != KNN_L2 && x.metric != KNN_L1))
+        return KNN_ERR_INVALID;
+    if (!x.R || (x.n > 0 && (!x.Q || !x.dist_out || !x.idx_out))) return KNN_ERR_INVALID;
+    if (x.k > KNN_K_MAX || x.m > 0x7fffffffLL || x.n > 0x7fffffffLL) return KNN_ERR_UNSUPPORTED;
+    return KNN_OK;
+}
+
+// Plans and workspace slices of every instance of a batch.
+struct BatchPlan {
+    std::vector<SearchPlan> sp;
+    std::vector<size_t> base, fbc, lp, rmax;
+    size_t bytes = 0;
+};
+
+knn_status plan_batch(const knn_ctx* h, const knn_instance* inst, int32_t count, int sm_share,
+                      BatchPlan* bp) {
+    Carve cv;
+    bp->sp.resize(count);
+    bp->base.assign(count, 0);
+    bp->fbc.assign(count, 0);
+    bp->lp.assign(count, 0);
+    bp->rmax.assign(count, 0);
+    for (int32_t i = 0; i < count; ++i) {
+        const knn_instance& x = inst[i];
+        if (x.n == 0) continue;
+        SearchPlan& sp = bp->sp[i];
+        knn_status s = plan_search_md(h, x.m, x.d, h->opt.precision, x.n, x.k,
+                                      static_cast<knn_metric>(x.metric), 1, sm_share, &sp,
+                                      4LL << 20);
+        if (s != KNN_OK) return s;
+        bp->base[i] = cv.take(sp.bytes);
+        bp->fbc[i] = cv.take(sizeof(int32_t));
+        if (sp.tensor) {
+            const size_t elt = (sp.prec == kBF16) ? 2 : 4;
+            bp->lp[i] = cv.take(static_cast<size_t>(x.m) * sp.kp * elt);
+            bp->rmax[i] = cv.take(sizeof(uint32_t));
+        }
+    }
+    bp->bytes = cv.off;
+    return KNN_OK;
+}
+
+// Enqueue instance i of a planned batch on st (its low-precision reference
+// copy first, for the tensor-core forms).
+knn_status enqueue_instance(knn_ctx* h, const knn_instance& x, const BatchPlan& bp, int32_t i,
+                            cudaStream_t st, int* l) {
+    if (x.n == 0) return KNN_OK;
+    const SearchPlan& sp = bp.sp[i];
+    unsigned char* ws = h->ws;
+    RefView rv{x.R, x.m, x.d, nullptr, 0, nullptr};
+    if (sp.tensor) {
+        rv.R_lp = ws + bp.lp[i];
+        rv.kp = sp.kp;
+        rv.rmax2 = reinterpret_cast<uint32_t*>(ws + bp.rmax[i]);
+        KNN_CUDA(h, launch_prepare_ref(x.R, x.m, x.d, sp.kp, sp.prec, rv.R_lp, nullptr,
+                                       reinterpret_cast<uint32_t*>(ws + bp.rmax[i]), st, l));
+    }
+    return enqueue_search(h, sp, rv, x.Q, x.n, x.k, static_cast<knn_metric>(x.metric), x.dist_out,
+                          x.idx_out, ws + bp.base[i], reinterpret_cast<int32_t*>(ws + bp.fbc[i]),
+                          st, l, false);
+}
+
+knn_status batch_streams(knn_ctx* h) {
+    if (h->cap_stream) return KNN_OK;
+    KNN_CUDA(h, cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking));
+    for (int b = 0; b < 16; ++b) {
+        KNN_CUDA(h, cudaStreamCreateWithFlags(&h->branch[b], cudaStreamNonBlocking));
+        KNN_CUDA(h, cudaEventCreateWithFlags(&h->join_ev[b], cudaEventDisableTiming));
+    }
+    KNN_CUDA(h, cudaEventCreateWithFlags(&h->fork_ev, cudaEventDisableTiming));
+    KNN_CUDA(h, cudaEventCreate(&h->t_ev[0]));
+    KNN_CUDA(h, cudaEventCreate(&h->t_ev[1]));
+    return KNN_OK;
+}
+
+// Capture the batch into one graph: the instances spread over `branches`
+// parallel branches, largest work first onto the least loaded branch.
+knn_status capture_batch(knn_ctx* h, const knn_instance* inst, int32_t count, const BatchPlan& bp,
+                         int branches, knn_ctx::BatchGraph* out) {
+    knn_status s = batch_streams(h);
+    if (s != KNN_OK) return s;
+    if (branches < 1) branches = 1;
+    if (branches > 16) branches = 16;
+    std::vector<int32_t> order(count);
+    for (int32_t i = 0; i < count; ++i) order[i] = i;
+    auto work = [&](int32_t i) {
+        return static_cast<double>(inst[i].n) * inst[i].m * inst[i].d + 1e6;
+    };
+    std::stable_sort(order.begin(), order.end(),
+                     [&](int32_t a, int32_t b) { return work(a) > work(b); });
+    std::vector<double> load(branches, 0.0);
+    KNN_CUDA(h, cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeRelaxed));
+    cudaError_t err = cudaEventRecord(h->fork_ev, h->cap_stream);
+    for (int b = 0; err == cudaSuccess && b < branches; ++b)
+        err = cudaStreamWaitEvent(h->branch[b], h->fork_ev, 0);
+    int l = 0;
+    s = (err == cudaSuccess) ? KNN_OK : cuda_fail(h, err, "batch fork");
+    for (int32_t t = 0; s == KNN_OK && t < count; ++t) {
+        const int32_t i = order[t];
+        const int b = static_cast<int>(std::min_element(load.begin(), load.end()) - load.begin());
+        load[b] += work(i);
+        s = enqueue_instance(h, inst[i], bp, i, h->branch[b], &l);
+    }
+    // join every branch even after an error, so that the capture can end
+    for (int b = 0; b < branches; ++b) {
+        cudaEventRecord(h->join_ev[b], h->branch[b]);
+        cudaStreamWaitEvent(h->cap_stream, h->join_ev[b], 0);
+    }
+    cudaGraph_t graph = nullptr;
+    err = cudaStreamEndCapture(h->cap_stream, &graph);
+    if (s != KNN_OK || err != cudaSuccess) {
+        if (graph) cudaGraphDestroy(graph);
+        (void)cudaGetLastError();
+        return s != KNN_OK ? s : cuda_fail(h, err, "cudaStreamEndCapture");
+    }
+    size_t nodes = 0;
+    cudaGraphGetNodes(graph, nullptr, &nodes);
+    cudaGraphExec_t exec = nullptr;
+    err = cudaGraphInstantiate(&exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (err != cudaSuccess) return cuda_fail(h, err, "cudaGraphInstantiate");
+    out->exec = exec;
+    out->branches = branches;
+    out->launches = l;
+    out->nodes = nodes;
+    return KNN_OK;
+}
+
+// Plan, size the workspace and capture one configuration.
+knn_status build_batch(knn_ctx* h, const knn_instance* inst, int32_t count, int branches,
+                       int sm_share, knn_ctx::BatchGraph* out) {
+    BatchPlan bp;
+    knn_status s = plan_batch(h, inst, count, sm_share, &bp);
+    if (s != KNN_OK) return s;
+    s = ensure_workspace(h, bp.bytes);
+    if (s != KNN_OK) return s;
+    s = capture_batch(h, inst, count, bp, branches, out);
+    if (s == KNN_OK) out->sm_share = sm_share;
+    return s;
 }
 
 }  // namespace
@@ -341,6 +637,17 @@ knn_status knn_destroy(knn_handle h) {
     cudaSetDevice(h->device);
     if (h->stream) cudaStreamSynchronize(h->stream);
     h->ref.reset();
+    if (h->cap_stream) cudaStreamSynchronize(h->cap_stream);
+    for (int b = 0; b < 16; ++b) if (h->branch[b]) cudaStreamSynchronize(h->branch[b]);
+    drop_graphs(h);
+    for (int b = 0; b < 16; ++b) {
+        if (h->branch[b]) cudaStreamDestroy(h->branch[b]);
+        if (h->join_ev[b]) cudaEventDestroy(h->join_ev[b]);
+    }
+    if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
+    if (h->fork_ev) cudaEventDestroy(h->fork_ev);
+    if (h->t_ev[0]) cudaEventDestroy(h->t_ev[0]);
+    if (h->t_ev[1]) cudaEventDestroy(h->t_ev[1]);
     if (h->ws) cudaFree(h->ws);
     if (h->counters) cudaFree(h->counters);
     for (int i = 0; i <= kMaxStages; ++i)
@@ -438,7 +745,6 @@ knn_status knn_search(knn_handle h, const float* Q, int64_t n, int32_t d, int32_
     s = ensure_workspace(h, sp.bytes);
     if (s != KNN_OK) return s;
     unsigned char* ws = h->ws;
-    const int S = sp.S, c = sp.c;
 
     const float* Qd = Q;
     float* dd = dist_out;
@@ -455,74 +761,10 @@ knn_status knn_search(knn_handle h, const float* Q, int64_t n, int32_t d, int32_
     }
 
     Counters* ctr = h->counters;
-    KNN_CUDA(h, cudaMemsetAsync(&ctr->fallback_count, 0, sizeof(int32_t), st));
     int l = 0;
-    FinalizeArgs fa{};
-    if (sp.tensor) {
-        const TcPlan& plan = sp.plan;
-        const int prec = sp.prec;
-        void* Ql = ws + sp.off_ql;
-        uint64_t* lists = reinterpret_cast<uint64_t*>(ws + sp.off_lists);
-        int32_t* counts = reinterpret_cast<int32_t*>(ws + sp.off_counts);
-        HitScale qs;
-        qs.rmax2 = rs.rmax2;
-        qs.qscale = reinterpret_cast<float*>(ws + sp.off_qs);
-        HitScale qs_prep = qs;   // the threshold pass sets B when there is one
-        if (plan.pilot) qs_prep.qscale = nullptr;
-        KNN_CUDA(h, launch_prepare_query(Qd, n, d, rs.kp, prec, Ql, qs_prep, st, &l));
-        stage(h, st, "prepare_q");
-        if (plan.pilot) {
-            uint32_t* gmax = reinterpret_cast<uint32_t*>(ws + sp.off_gmax);
-            KNN_CUDA(h, launch_tc_pilot(plan, Ql, n, rs.R_lp, m, rs.kp, prec, gmax, &ctr->error_flag,
-                                        st, &l));
-            stage(h, st, "tc_pilot");
-            KNN_CUDA(h, launch_tc_threshold(plan, gmax, n, d, rs.kp, prec, Ql, qs, st, &l));
-            stage(h, st, "tc_threshold");
-        }
-        KNN_CUDA(h, launch_tc_filter(plan, Ql, n, rs.R_lp, m, rs.kp, prec, lists, counts, qs.qscale,
-                                     &ctr->error_flag, st, &l));
-        stage(h, st, "tc_filter");
-        fa.use_hits = 1;
-        fa.hits.keys = lists;
-        fa.hits.counts = counts;
-        fa.hits.S = plan.groups * S;   // one list per (split, epilogue column group)
-        fa.hits.cap = plan.cap;
-        fa.hits.c = c;
-        fa.cand.exact = 0;
-        fa.cand.S = 1;
-        fa.cand.c = c;
-    } else {
-        CandidateSet cs;
-        cs.keys = reinterpret_cast<uint64_t*>(ws + sp.off_cand);
-        cs.n = n;
-        cs.S = S;
-        cs.c = c;
-        cs.chunk = sp.chunk;
-        cs.exact = 1;
-        KNN_CUDA(h, launch_cc_select(Qd, n, rs.R, m, d, metric, cs, st, &l));
-        stage(h, st, "cc_select");
-        fa.use_hits = 0;
-        fa.cand = cs;
-    }
-    fa.Q = Qd;
-    fa.R = rs.R;
-    fa.n = n;
-    fa.m = m;
-    fa.d = d;
-    fa.k = k;
-    fa.metric = metric;
-    fa.dist_out = dd;
-    fa.idx_out = id;
-    fa.fallback_count = &ctr->fallback_count;
-    fa.fallback_list = reinterpret_cast<int32_t*>(ws + sp.off_list);
-    fa.recheck_counter = &ctr->recheck_total;
-    fa.fallback_total = &ctr->fallback_total;
-    fa.fallback_reason = ctr->fallback_reason;
-    KNN_CUDA(h, launch_finalize(fa, st, &l));
-    stage(h, st, "finalize");
-    KNN_CUDA(h, launch_fallback(fa, reinterpret_cast<double*>(ws + sp.off_scr),
-                                static_cast<int32_t>(sp.fb_grid), st, &l));
-    stage(h, st, "fallback");
+    RefView rv{rs.R, rs.m, rs.d, rs.R_lp, rs.kp, rs.rmax2};
+    s = enqueue_search(h, sp, rv, Qd, n, k, metric, dd, id, ws, &ctr->fallback_count, st, &l, true);
+    if (s != KNN_OK) return s;
     h->launches += l;
     h->searches += 1;
 
@@ -541,6 +783,115 @@ knn_status knn_search(knn_handle h, const float* Q, int64_t n, int32_t d, int32_
             return KNN_ERR_TIMEOUT;
         }
     }
+    return KNN_OK;
+}
+
+knn_status knn_search_batch(knn_handle h, const knn_instance* inst, int32_t count, int32_t flags,
+                            void* cuda_stream) {
+    if (!h || count < 0 || (count > 0 && !inst)) return KNN_ERR_INVALID;
+    for (int32_t i = 0; i < count; ++i) {
+        knn_status s = check_instance(inst[i]);
+        if (s != KNN_OK) return s;
+    }
+    if (count == 0) return KNN_OK;
+    KNN_CUDA(h, cudaSetDevice(h->device));
+    cudaStream_t st = cuda_stream ? static_cast<cudaStream_t>(cuda_stream) : h->stream;
+
+    if (flags & KNN_BATCH_NO_GRAPH) {
+        // one instance after another on st, each planned as a lone search
+        BatchPlan bp;
+        knn_status s = plan_batch(h, inst, count, h->num_sms, &bp);
+        if (s != KNN_OK) return s;
+        s = ensure_workspace(h, bp.bytes);
+        if (s != KNN_OK) return s;
+        int l = 0;
+        for (int32_t i = 0; i < count; ++i) {
+            s = enqueue_instance(h, inst[i], bp, i, st, &l);
+            if (s != KNN_OK) return s;
+        }
+        h->launches += l;
+        h->searches += count;
+        h->last_batch = knn_batch_info{1, h->num_sms, l, 0, 0, 0.0};
+        return KNN_OK;
+    }
+
+    const uint64_t exact = batch_signature(h, inst, count, true);
+    const uint64_t shape = batch_signature(h, inst, count, false);
+    auto it = h->graphs.find(exact);
+    if (it == h->graphs.end()) {
+        knn_ctx::BatchGraph best;
+        float tune_ms = 0.f;
+        bool tuned_now = false;
+        auto tk = h->tuned.find(shape);
+        if (tk != h->tuned.end()) {
+            knn_status s = build_batch(h, inst, count, tk->second.first, tk->second.second, &best);
+            if (s != KNN_OK) return s;
+        } else if (flags & KNN_BATCH_AUTOTUNE) {
+            // time every candidate configuration on this batch, keep the fastest;
+            // the workspace is sized for all of them first, so that no capture
+            // moves it under a graph already built
+            const int shares[2] = {h->num_sms, std::max(1, h->num_sms / 4)};
+            const int brs[4] = {1, 4, 8, 16};
+            size_t need = 0;
+            for (int si = 0; si < 2; ++si) {
+                BatchPlan bp;
+                knn_status s = plan_batch(h, inst, count, shares[si], &bp);
+                if (s != KNN_OK) return s;
+                need = std::max(need, bp.bytes);
+            }
+            knn_status sw = ensure_workspace(h, need);
+            if (sw != KNN_OK) return sw;
+            float best_ms = 0.f;
+            for (int si = 0; si < 2; ++si) {
+                for (int bi = 0; bi < 4; ++bi) {
+                    if (bi > 0 && brs[bi] > count) continue;
+                    knn_ctx::BatchGraph g;
+                    knn_status s = build_batch(h, inst, count, brs[bi], shares[si], &g);
+                    if (s != KNN_OK) return s;
+                    KNN_CUDA(h, cudaGraphLaunch(g.exec, st));            // warm
+                    KNN_CUDA(h, cudaEventRecord(h->t_ev[0], st));
+                    KNN_CUDA(h, cudaGraphLaunch(g.exec, st));
+                    KNN_CUDA(h, cudaGraphLaunch(g.exec, st));
+                    KNN_CUDA(h, cudaEventRecord(h->t_ev[1], st));
+                    KNN_CUDA(h, cudaEventSynchronize(h->t_ev[1]));
+                    float ms = 0.f;
+                    KNN_CUDA(h, cudaEventElapsedTime(&ms, h->t_ev[0], h->t_ev[1]));
+                    ms *= 0.5f;
+                    tune_ms += 3.f * ms;
+                    if (!best.exec || ms < best_ms) {
+                        if (best.exec) cudaGraphExecDestroy(best.exec);
+                        best = g;
+                        best_ms = ms;
+                    } else {
+                        cudaGraphExecDestroy(g.exec);
+                    }
+                }
+            }
+            h->tuned[shape] = {best.branches, best.sm_share};
+            tuned_now = true;
+        } else {
+            const int branches = std::min<int32_t>(8, count);
+            knn_status s = build_batch(h, inst, count, branches, std::max(1, h->num_sms / 4), &best);
+            if (s != KNN_OK) return s;
+        }
+        it = h->graphs.emplace(exact, best).first;
+        h->last_batch = knn_batch_info{best.branches, best.sm_share, best.launches,
+                                       static_cast<int64_t>(best.nodes), tuned_now ? 1 : 0,
+                                       static_cast<double>(tune_ms)};
+    } else {
+        const knn_ctx::BatchGraph& g = it->second;
+        h->last_batch = knn_batch_info{g.branches, g.sm_share, g.launches,
+                                       static_cast<int64_t>(g.nodes), 0, 0.0};
+    }
+    KNN_CUDA(h, cudaGraphLaunch(it->second.exec, st));
+    h->launches += it->second.launches;
+    h->searches += count;
+    return KNN_OK;
+}
+
+knn_status knn_batch_info_get(knn_handle h, knn_batch_info* out) {
+    if (!h || !out) return KNN_ERR_INVALID;
+    *out = h->last_batch;
     return KNN_OK;
 }
 

@@ -39,6 +39,23 @@ class knn_options(ctypes.Structure):
                 ("workspace_limit", ctypes.c_int64)]
 
 
+class knn_instance(ctypes.Structure):
+    _fields_ = [("R", ctypes.c_void_p), ("m", ctypes.c_int64), ("Q", ctypes.c_void_p),
+                ("n", ctypes.c_int64), ("d", ctypes.c_int32), ("k", ctypes.c_int32),
+                ("metric", ctypes.c_int32), ("dist_out", ctypes.c_void_p),
+                ("idx_out", ctypes.c_void_p)]
+
+
+class knn_batch_info(ctypes.Structure):
+    _fields_ = [("branches", ctypes.c_int32), ("sm_share", ctypes.c_int32),
+                ("launches", ctypes.c_int32), ("graph_nodes", ctypes.c_int64),
+                ("tuned", ctypes.c_int32), ("tune_ms", ctypes.c_double)]
+
+
+KNN_BATCH_AUTOTUNE = 1
+KNN_BATCH_NO_GRAPH = 2
+
+
 class knn_stats(ctypes.Structure):
     _fields_ = [("searches", ctypes.c_int64), ("kernel_launches", ctypes.c_int64),
                 ("recheck_entries", ctypes.c_int64), ("fallback_queries", ctypes.c_int64),
@@ -68,6 +85,8 @@ _SIGS = {
     "knn_workspace_size": (ctypes.c_int, [_H, _i64, _i32, _i32, ctypes.c_int, ctypes.c_int,
                                           ctypes.POINTER(_i64)]),
     "knn_reserve": (ctypes.c_int, [_H, _i64]),
+    "knn_search_batch": (ctypes.c_int, [_H, ctypes.POINTER(knn_instance), _i32, _i32, _P]),
+    "knn_batch_info_get": (ctypes.c_int, [_H, ctypes.POINTER(knn_batch_info)]),
     "knn_destroy": (ctypes.c_int, [_H]),
     "knn_status_string": (ctypes.c_char_p, [ctypes.c_int]),
     "knn_last_error": (ctypes.c_char_p, [_H]),
@@ -91,6 +110,8 @@ knn_search_static = _lib.knn_search_static
 knn_create_shared = _lib.knn_create_shared
 knn_workspace_size = _lib.knn_workspace_size
 knn_reserve = _lib.knn_reserve
+knn_search_batch = _lib.knn_search_batch
+knn_batch_info_get = _lib.knn_batch_info_get
 knn_destroy = _lib.knn_destroy
 knn_status_string = _lib.knn_status_string
 knn_last_error = _lib.knn_last_error
@@ -219,6 +240,28 @@ class Index:
             idx = torch.empty((n, k), dtype=torch.int32, device=Q.device)
         self.search_into(Q, k, dist, idx, metric, stream)
         return dist, idx
+
+    def search_batch(self, instances, flags: int = 0, stream=None):
+        """knn_search_batch over a list of dicts with device tensors R, Q,
+        dist, idx and ints k (and metric, default l2)."""
+        arr = (knn_instance * len(instances))()
+        for i, x in enumerate(instances):
+            R, Q = x["R"], x["Q"]
+            for t in (R, Q, x["dist"], x["idx"]):
+                if not (t.is_cuda and t.is_contiguous()):
+                    raise ValueError("batch tensors must be contiguous device tensors")
+            arr[i] = knn_instance(R.data_ptr(), R.shape[0], Q.data_ptr(), Q.shape[0], R.shape[1],
+                                  x["k"], METRICS[x.get("metric", "l2")], x["dist"].data_ptr(),
+                                  x["idx"].data_ptr())
+        sp = None
+        if stream is not None:
+            sp = getattr(stream, "cuda_stream", stream) or 1
+        self._check(knn_search_batch(self.h, arr, len(instances), flags, sp), "knn_search_batch")
+
+    def batch_info(self) -> dict:
+        b = knn_batch_info()
+        self._check(knn_batch_info_get(self.h, ctypes.byref(b)), "knn_batch_info_get")
+        return {f: getattr(b, f) for f, _ in knn_batch_info._fields_}
 
     def sync(self):
         self._check(knn_sync(self.h), "knn_sync")
