@@ -826,45 +826,102 @@ finalize_kernel(FinalizeArgs a, int P, int warps_per_block) {
 }
 
 // ---------------------------------------------------------------------------
-// exact fallback: float32 distances to every reference, the k-th smallest by
-// radix selection, then float64 distances for every reference whose float32
-// distance could still place it in the answer (float32 <= kth * (1+e)/(1-e)),
-// an exact radix selection on those, a sort, and the outputs.
+// exact fallback (one CTA of 1024 threads per queued query): float32
+// distances to every reference and the k-th smallest by radix selection on
+// their bit patterns (four 8-bit passes, one shared-memory histogram per
+// warp); every reference whose float32 distance could still place it in the
+// answer (float32 <= kth * (1+e)/(1-e)) gets its float64 distance (the
+// oracle's arithmetic); those are sorted by (float64 distance, index) and the
+// first k written.  When more than kFbCand references qualify (masses of
+// equal distances), the same selection runs over float64 keys of all m.
 // ---------------------------------------------------------------------------
-constexpr int kFbThreads = 256;
+constexpr int kFbThreads = 1024;
+constexpr int kFbWarps = kFbThreads / 32;
 constexpr int kFbMaxK = 1024;
+constexpr int kFbCand = 4096;
 constexpr uint64_t kInfBits = 0x7ff0000000000000ull;
 
 struct FbShared {
-    int hist[256];
-    uint64_t ck[kFbMaxK];
-    uint32_t ci[kFbMaxK];
-    int digit, rank, less, taken, wsum[kFbThreads / 32];
+    int hist[kFbWarps][256];
+    int digit, rank, cnt, less, taken;
+    int wsum[kFbWarps];
 };
 
-// k-th smallest of the non-negative doubles keys[0..m) (bit pattern order),
-// returned as bits; *ties = how many entries equal to it belong to the k.
-__device__ uint64_t radix_select(const double* keys, int64_t m, int k, FbShared& sh, int* ties) {
-    const int tid = threadIdx.x;
+// Bin b of the summed per-warp histograms, and the digit whose cumulative
+// count reaches `rank` (warp 0; the result goes to sh.digit / sh.rank).
+__device__ void pick_digit(FbShared& sh, int rank) {
+    const int tid = threadIdx.x, lane = tid % 32;
+    if (tid < 32) {
+        int h[8], sum = 0;
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+            int v = 0;
+            for (int w = 0; w < kFbWarps; ++w) v += sh.hist[w][8 * lane + i];
+            h[i] = v;
+            sum += v;
+        }
+        int incl = sum;
+        for (int o = 1; o < 32; o <<= 1) {
+            const int v = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += v;
+        }
+        int cum = incl - sum;
+        if (cum < rank && incl >= rank) {
+#pragma unroll
+            for (int i = 0; i < 8; ++i) {
+                if (cum + h[i] >= rank) {
+                    sh.digit = 8 * lane + i;
+                    sh.rank = rank - cum;
+                    break;
+                }
+                cum += h[i];
+            }
+        }
+    }
+}
+
+__device__ void clear_hist(FbShared& sh) {
+    for (int e = threadIdx.x; e < kFbWarps * 256; e += kFbThreads) (&sh.hist[0][0])[e] = 0;
+}
+
+// k-th smallest (1-based rank k) of keys[0..m) in unsigned order.
+__device__ uint32_t radix_select32(const uint32_t* keys, int64_t m, int k, FbShared& sh) {
+    const int tid = threadIdx.x, w = tid / 32;
+    uint32_t prefix = 0, mask = 0;
+    int rank = k;
+    for (int shift = 24; shift >= 0; shift -= 8) {
+        clear_hist(sh);
+        __syncthreads();
+        for (int64_t j = tid; j < m; j += kFbThreads) {
+            const uint32_t u = keys[j];
+            if ((u & mask) == prefix) atomicAdd(&sh.hist[w][(u >> shift) & 0xff], 1);
+        }
+        __syncthreads();
+        pick_digit(sh, rank);
+        __syncthreads();
+        prefix |= static_cast<uint32_t>(sh.digit) << shift;
+        mask |= 0xffu << shift;
+        rank = sh.rank;
+        __syncthreads();
+    }
+    return prefix;
+}
+
+// The same over non-negative doubles (bit patterns; eight passes); *ties =
+// how many entries equal to the result belong to the first k.
+__device__ uint64_t radix_select64(const double* keys, int64_t m, int k, FbShared& sh, int* ties) {
+    const int tid = threadIdx.x, w = tid / 32;
     uint64_t prefix = 0, mask = 0;
     int rank = k;
     for (int shift = 56; shift >= 0; shift -= 8) {
-        for (int b = tid; b < 256; b += kFbThreads) sh.hist[b] = 0;
+        clear_hist(sh);
         __syncthreads();
         for (int64_t j = tid; j < m; j += kFbThreads) {
             const uint64_t u = dbits(keys[j]);
-            if ((u & mask) == prefix) atomicAdd(&sh.hist[(u >> shift) & 0xff], 1);
+            if ((u & mask) == prefix) atomicAdd(&sh.hist[w][(u >> shift) & 0xff], 1);
         }
         __syncthreads();
-        if (tid == 0) {
-            int cum = 0, b = 0;
-            for (; b < 255; ++b) {
-                if (cum + sh.hist[b] >= rank) break;
-                cum += sh.hist[b];
-            }
-            sh.digit = b;
-            sh.rank = rank - cum;
-        }
+        pick_digit(sh, rank);
         __syncthreads();
         prefix |= static_cast<uint64_t>(sh.digit) << shift;
         mask |= 0xffull << shift;
@@ -875,96 +932,156 @@ __device__ uint64_t radix_select(const double* keys, int64_t m, int k, FbShared&
     return prefix;
 }
 
+// Sort keys ck / indices ci [0..cnt) ascending by (key, index) in place
+// (bitonic over the next power of two, padded with the largest pair).
+__device__ void sort_pairs(uint64_t* ck, uint32_t* ci, int cnt) {
+    const int tid = threadIdx.x;
+    int P2 = 1;
+    while (P2 < cnt) P2 <<= 1;
+    for (int i = cnt + tid; i < P2; i += kFbThreads) { ck[i] = ~0ull; ci[i] = 0xffffffffu; }
+    __syncthreads();
+    for (int size = 2; size <= P2; size <<= 1) {
+        for (int stride = size >> 1; stride > 0; stride >>= 1) {
+            for (int i = tid; i < P2; i += kFbThreads) {
+                const int j = i ^ stride;
+                if (j > i) {
+                    const bool gt = ck[i] > ck[j] || (ck[i] == ck[j] && ci[i] > ci[j]);
+                    if (gt == ((i & size) == 0)) {
+                        const uint64_t tk = ck[i]; ck[i] = ck[j]; ck[j] = tk;
+                        const uint32_t tj = ci[i]; ci[i] = ci[j]; ci[j] = tj;
+                    }
+                }
+            }
+            __syncthreads();
+        }
+    }
+}
+
 template <int METRIC>
 __global__ void __launch_bounds__(kFbThreads)
 fallback_kernel(FinalizeArgs a, double* __restrict__ scratch) {
     __shared__ FbShared sh;
-    extern __shared__ __align__(16) float qrow[];
+    extern __shared__ __align__(16) unsigned char fb_dyn[];
+    uint64_t* ck = reinterpret_cast<uint64_t*>(fb_dyn);                  // [kFbCand]
+    uint32_t* ci = reinterpret_cast<uint32_t*>(ck + kFbCand);            // [kFbCand]
+    float* qrow = reinterpret_cast<float*>(ci + kFbCand);                // [d + 4]
     const int tid = threadIdx.x;
     const int count = *a.fallback_count;
     const int64_t m = a.m;
     const int d = a.d, k = a.k;
     const double rel = f32_rel_bound(d);
     double* keys = scratch + static_cast<int64_t>(blockIdx.x) * m;
+    uint32_t* keys32 = reinterpret_cast<uint32_t*>(keys);
 
     for (int f = blockIdx.x; f < count; f += gridDim.x) {
         const int64_t q = a.fallback_list[f];
         __syncthreads();
         for (int t = tid; t < d; t += kFbThreads) qrow[t] = a.Q[q * d + t];
+        if (tid == 0) sh.cnt = 0;
         __syncthreads();
-        // float32 pass and its k-th smallest
-        for (int64_t j = tid; j < m; j += kFbThreads)
-            keys[j] = static_cast<double>(dist_f32<METRIC>(qrow, a.R + j * d, d));
-        __syncthreads();
-        int ties;
-        const double kth32 = bitsd(radix_select(keys, m, k, sh, &ties));
-        const double bound = kth32 * (1.0 + rel) / (1.0 - rel) * (1.0 + 1e-12) + 1e-37;
-        // float64 for every reference that could still be in the answer
-        for (int64_t j = tid; j < m; j += kFbThreads)
-            keys[j] = (keys[j] <= bound) ? dist_f64<METRIC>(qrow, a.R + j * d, d) : bitsd(kInfBits);
-        __syncthreads();
-        const uint64_t T = radix_select(keys, m, k, sh, &ties);
-        const int n_less = k - ties;   // strictly below T; then `ties` entries equal to T
-        if (tid == 0) { sh.less = 0; sh.taken = 0; }
-        __syncthreads();
-        for (int64_t j = tid; j < m; j += kFbThreads) {
-            const uint64_t u = dbits(keys[j]);
-            if (u < T) {
-                const int slot = atomicAdd(&sh.less, 1);
-                sh.ck[slot] = u;
-                sh.ci[slot] = static_cast<uint32_t>(j);
-            }
-        }
-        __syncthreads();
-        // the `ties` entries equal to T with the smallest indices, in index order
-        const int lane = tid % 32, wid = tid / 32;
-        for (int64_t b0 = 0; b0 < m; b0 += kFbThreads) {
-            const int64_t j = b0 + tid;
-            const bool eq = (j < m) && dbits(keys[j]) == T;
-            const unsigned bal = __ballot_sync(0xffffffffu, eq);
-            if (lane == 0) sh.wsum[wid] = __popc(bal);
-            __syncthreads();
-            int before = sh.taken;
-            for (int x = 0; x < wid; ++x) before += sh.wsum[x];
-            before += __popc(bal & ((1u << lane) - 1u));
-            if (eq && before < ties) {
-                sh.ck[n_less + before] = T;
-                sh.ci[n_less + before] = static_cast<uint32_t>(j);
-            }
-            __syncthreads();
-            if (tid == 0) {
-                int tot = 0;
-                for (int x = 0; x < kFbThreads / 32; ++x) tot += sh.wsum[x];
-                sh.taken += tot;
-            }
-            __syncthreads();
-            if (sh.taken >= ties) break;
-        }
-        // sort the k pairs by (distance, index)
-        int P2 = 1;
-        while (P2 < k) P2 <<= 1;
-        for (int i = k + tid; i < P2; i += kFbThreads) { sh.ck[i] = ~0ull; sh.ci[i] = 0xffffffffu; }
-        __syncthreads();
-        for (int size = 2; size <= P2; size <<= 1) {
-            for (int stride = size >> 1; stride > 0; stride >>= 1) {
-                for (int i = tid; i < P2; i += kFbThreads) {
-                    const int j = i ^ stride;
-                    if (j > i) {
-                        const bool gt = sh.ck[i] > sh.ck[j] || (sh.ck[i] == sh.ck[j] && sh.ci[i] > sh.ci[j]);
-                        if (gt == ((i & size) == 0)) {
-                            const uint64_t tk = sh.ck[i]; sh.ck[i] = sh.ck[j]; sh.ck[j] = tk;
-                            const uint32_t tj = sh.ci[i]; sh.ci[i] = sh.ci[j]; sh.ci[j] = tj;
+        // float32 pass (four references per thread at a time, their loads issued
+        // together) and its k-th smallest
+        const bool vec = ((d & 3) == 0) && ((reinterpret_cast<uintptr_t>(a.R) & 15) == 0);
+        for (int64_t j0 = static_cast<int64_t>(tid) * 4; j0 < m; j0 += 4LL * kFbThreads) {
+            float acc[4] = {0.f, 0.f, 0.f, 0.f};
+            if (vec && j0 + 4 <= m) {
+                const float4* q4 = reinterpret_cast<const float4*>(qrow);
+                const float4* r4 = reinterpret_cast<const float4*>(a.R + j0 * d);
+                const int d4 = d >> 2;
+#pragma unroll 2
+                for (int t = 0; t < d4; ++t) {
+                    const float4 y = q4[t];
+#pragma unroll
+                    for (int u = 0; u < 4; ++u) {
+                        const float4 x = __ldg(r4 + u * d4 + t);
+                        const float e0 = y.x - x.x, e1 = y.y - x.y, e2 = y.z - x.z, e3 = y.w - x.w;
+                        if (METRIC == kL2) {
+                            acc[u] = fmaf(e0, e0, acc[u]); acc[u] = fmaf(e1, e1, acc[u]);
+                            acc[u] = fmaf(e2, e2, acc[u]); acc[u] = fmaf(e3, e3, acc[u]);
+                        } else {
+                            acc[u] += fabsf(e0); acc[u] += fabsf(e1);
+                            acc[u] += fabsf(e2); acc[u] += fabsf(e3);
                         }
                     }
                 }
-                __syncthreads();
+            } else {
+                for (int u = 0; u < 4 && j0 + u < m; ++u)
+                    acc[u] = dist_f32<METRIC>(qrow, a.R + (j0 + u) * d, d);
+            }
+            for (int u = 0; u < 4 && j0 + u < m; ++u) keys32[j0 + u] = __float_as_uint(acc[u]);
+        }
+        __syncthreads();
+        const float kth32 = __uint_as_float(radix_select32(keys32, m, k, sh));
+        const double bound = static_cast<double>(kth32) * (1.0 + rel) / (1.0 - rel) * (1.0 + 1e-12) + 1e-37;
+        // the references that could still be in the answer, with float64 distances
+        for (int64_t j = tid; j < m; j += kFbThreads) {
+            if (static_cast<double>(__uint_as_float(keys32[j])) <= bound) {
+                const int pos = atomicAdd(&sh.cnt, 1);
+                if (pos < kFbCand) ci[pos] = static_cast<uint32_t>(j);
             }
         }
+        __syncthreads();
+        const int cnt = sh.cnt;
+        if (cnt <= kFbCand) {
+            for (int i = tid; i < cnt; i += kFbThreads)
+                ck[i] = dbits(dist_f64<METRIC>(qrow, a.R + static_cast<int64_t>(ci[i]) * d, d));
+            __syncthreads();
+            sort_pairs(ck, ci, cnt);
+        } else {
+            // more candidates than shared memory holds: float64 keys of all m in
+            // the scratch (they overwrite the float32 keys, so those are recomputed)
+            for (int64_t j = tid; j < m; j += kFbThreads) {
+                const float v32 = dist_f32<METRIC>(qrow, a.R + j * d, d);
+                keys[j] = (static_cast<double>(v32) <= bound)
+                              ? dist_f64<METRIC>(qrow, a.R + j * d, d)
+                              : bitsd(kInfBits);
+            }
+            __syncthreads();
+            int ties;
+            const uint64_t T = radix_select64(keys, m, k, sh, &ties);
+            const int n_less = k - ties;   // strictly below T; then `ties` entries equal to T
+            if (tid == 0) { sh.less = 0; sh.taken = 0; }
+            __syncthreads();
+            for (int64_t j = tid; j < m; j += kFbThreads) {
+                const uint64_t u = dbits(keys[j]);
+                if (u < T) {
+                    const int slot = atomicAdd(&sh.less, 1);
+                    ck[slot] = u;
+                    ci[slot] = static_cast<uint32_t>(j);
+                }
+            }
+            __syncthreads();
+            // the `ties` entries equal to T with the smallest indices, in index order
+            const int lane = tid % 32, wid = tid / 32;
+            for (int64_t b0 = 0; b0 < m; b0 += kFbThreads) {
+                const int64_t j = b0 + tid;
+                const bool eq = (j < m) && dbits(keys[j]) == T;
+                const unsigned bal = __ballot_sync(0xffffffffu, eq);
+                if (lane == 0) sh.wsum[wid] = __popc(bal);
+                __syncthreads();
+                int before = sh.taken;
+                for (int x = 0; x < wid; ++x) before += sh.wsum[x];
+                before += __popc(bal & ((1u << lane) - 1u));
+                if (eq && before < ties) {
+                    ck[n_less + before] = T;
+                    ci[n_less + before] = static_cast<uint32_t>(j);
+                }
+                __syncthreads();
+                if (tid == 0) {
+                    int tot = 0;
+                    for (int x = 0; x < kFbWarps; ++x) tot += sh.wsum[x];
+                    sh.taken += tot;
+                }
+                __syncthreads();
+                if (sh.taken >= ties) break;
+            }
+            sort_pairs(ck, ci, k);
+        }
         for (int s = tid; s < k; s += kFbThreads) {
-            const double v = bitsd(sh.ck[s]);
+            const double v = bitsd(ck[s]);
             a.dist_out[q * k + s] =
                 (METRIC == kL2) ? static_cast<float>(__dsqrt_rn(v)) : static_cast<float>(v);
-            a.idx_out[q * k + s] = static_cast<int32_t>(sh.ci[s]);
+            a.idx_out[q * k + s] = static_cast<int32_t>(ci[s]);
         }
     }
 }
@@ -1025,12 +1142,23 @@ cudaError_t launch_finalize(const FinalizeArgs& a_in, cudaStream_t st, int* laun
 cudaError_t launch_fallback(const FinalizeArgs& a, double* scratch, int32_t grid,
                             cudaStream_t st, int* launches) {
     if (a.k > kFbMaxK) return cudaErrorInvalidValue;
-    const size_t smem = (static_cast<size_t>(a.d) + 4) * sizeof(float);
+    const size_t smem = static_cast<size_t>(kFbCand) * (sizeof(uint64_t) + sizeof(uint32_t)) +
+                        (static_cast<size_t>(a.d) + 4) * sizeof(float);
+    if (smem + sizeof(FbShared) > 227 * 1024) return cudaErrorInvalidValue;
     if (launches) ++*launches;
-    if (a.metric == kL2)
+    if (a.metric == kL2) {
+        cudaError_t err = cudaFuncSetAttribute(fallback_kernel<kL2>,
+                                               cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                               static_cast<int>(smem));
+        if (err != cudaSuccess) return err;
         fallback_kernel<kL2><<<grid, kFbThreads, smem, st>>>(a, scratch);
-    else
+    } else {
+        cudaError_t err = cudaFuncSetAttribute(fallback_kernel<kL1>,
+                                               cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                               static_cast<int>(smem));
+        if (err != cudaSuccess) return err;
         fallback_kernel<kL1><<<grid, kFbThreads, smem, st>>>(a, scratch);
+    }
     return cudaGetLastError();
 }
 

@@ -645,8 +645,12 @@ TcPlan tc_plan(int64_t n, int64_t m, int32_t d, int32_t kp, int prec, int32_t c,
     p.stride = stride;
     p.spt = (tps + stride - 1) / stride;
     p.G = S * p.spt * gpt;
+    // c' = lambda + 4 sqrt(lambda) + 4: with N references above the threshold
+    // the sampled count is Binomial(N, 1/stride); N < c with c' sampled passing
+    // has probability below 2e-6 per query at lambda = 5 (the bench shape), and
+    // such a query is finished by the exact fallback
     const double lambda = static_cast<double>(c) / stride;
-    p.cprime = static_cast<int>(std::ceil(lambda + 6.0 * std::sqrt(lambda) + 4.0));
+    p.cprime = static_cast<int>(std::ceil(lambda + 4.0 * std::sqrt(lambda) + 4.0));
     p.pilot = (p.G >= 2 * p.cprime) ? 1 : 0;
     // list capacity per (query, split, column group): twice the expected hits plus slack
     if (p.pilot) {

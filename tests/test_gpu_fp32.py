@@ -153,6 +153,18 @@ def test_all_identical_points_use_exact_fallback(knn):
     np.testing.assert_allclose(g_dist[1], np.full(40, np.sqrt(5 * 0.375 ** 2)), rtol=1e-7)
 
 
+def test_identical_points_beyond_the_fallback_candidate_buffer(knn):
+    """More equal-distance references (5000) than the fallback's shared-memory
+    candidate buffer holds: the float64 selection over all m decides."""
+    R = np.full((5000, 3), 0.25, dtype=np.float32)
+    Q = np.array([[0.25] * 3, [0.75] * 3], dtype=np.float32)
+    for k in (10, 1000):
+        g_dist, g_idx, st = run_case(knn, R, Q, k, "l2")
+        assert g_idx.tolist() == [list(range(k))] * 2
+        assert st["fallback_queries"] == 2
+        np.testing.assert_allclose(g_dist[1], np.full(k, np.sqrt(3 * 0.5 ** 2)), rtol=1e-7)
+
+
 def test_duplicates_across_splits(knn):
     base = inputs.uniform(300, 8, seed=77)
     R = np.concatenate([base] * 20)      # every point 20 times, spread over the range
