@@ -38,8 +38,13 @@ extern "C" {
 
 typedef struct knn_ctx* knn_handle; /* opaque; owned by the library */
 
-/* Distances named in Sec. 2.1 ("the Euclidean or the Manhattan distance"). */
-typedef enum { KNN_L2 = 0, KNN_L1 = 1 } knn_metric;
+/*
+ * Distances: the two Sec. 2.1 names ("the Euclidean or the Manhattan
+ * distance"), and the Chebyshev (L-infinity) distance max_t |q_t - r_t|,
+ * another norm-induced distance of the same problem statement.  Manhattan and
+ * Chebyshev searches run in KNN_FP32 whatever the handle's precision.
+ */
+typedef enum { KNN_L2 = 0, KNN_L1 = 1, KNN_LINF = 2 } knn_metric;
 
 /*
  * Arithmetic of the distance stage.
@@ -50,11 +55,12 @@ typedef enum { KNN_L2 = 0, KNN_L1 = 1 } knn_metric;
  *             accumulation, the norms are added in the epilogue
  *             (||q||^2 + ||r||^2 - 2 q.r), the best rerank_factor * k
  *             candidates per query are re-ranked with exact float32
- *             differences.  Manhattan distance ignores this setting and
- *             runs in KNN_FP32.
+ *             differences.  Manhattan and Chebyshev distances ignore this
+ *             setting and run in KNN_FP32.
  * In every mode, candidates whose float32 distances lie within the float32
- * rounding bound of each other around the returned list are re-checked in
- * float64 on the GPU, so ties are resolved by the exact distance.
+ * rounding bound of each other around the returned list are re-checked on the
+ * GPU (a float-float sum, and the oracle's float64 arithmetic where that
+ * cannot separate them), so ties are resolved by the exact distance.
  */
 typedef enum { KNN_FP32 = 0, KNN_TF32 = 1, KNN_BF16 = 2 } knn_precision;
 

@@ -386,7 +386,8 @@ knn_status enqueue_search(knn_ctx* h, const SearchPlan& sp, const RefView& rv, c
 
 knn_status check_search_args(const knn_ctx* h, int64_t n, int32_t d, int32_t k, knn_metric metric) {
     if (!h) return KNN_ERR_INVALID;
-    if (n < 0 || k < 1 || (metric != KNN_L2 && metric != KNN_L1)) return KNN_ERR_INVALID;
+    if (n < 0 || k < 1 || (metric != KNN_L2 && metric != KNN_L1 && metric != KNN_LINF))
+        return KNN_ERR_INVALID;
     if (!h->ref) return KNN_ERR_NOREF;
     if (d != h->ref->d || k > h->ref->m) return KNN_ERR_INVALID;
     if (k > KNN_K_MAX) return KNN_ERR_UNSUPPORTED;
@@ -428,7 +429,7 @@ uint64_t batch_signature(const knn_ctx* h, const knn_instance* inst, int32_t cou
 
 knn_status check_instance(const knn_instance& x) {
     if (x.n < 0 || x.m < 1 || x.d < 1 || x.k < 1 || x.k > x.m ||
-        (x.metric != KNN_L2 && x.metric != KNN_L1))
+        (x.metric != KNN_L2 && x.metric != KNN_L1 && x.metric != KNN_LINF))
         return KNN_ERR_INVALID;
     if (!x.R || (x.n > 0 && (!x.Q || !x.dist_out || !x.idx_out))) return KNN_ERR_INVALID;
     if (x.k > KNN_K_MAX || x.m > 0x7fffffffLL || x.n > 0x7fffffffLL) return KNN_ERR_UNSUPPORTED;

@@ -132,7 +132,8 @@ cc_select_kernel(const float* __restrict__ Q, int64_t n, const float* __restrict
                     for (int j = 0; j < S::CN; ++j) {
                         const float diff = qv[i] - rv[j];
                         if (METRIC == kL2) acc[i][j] = fmaf(diff, diff, acc[i][j]);
-                        else acc[i][j] += fabsf(diff);
+                        else if (METRIC == kL1) acc[i][j] += fabsf(diff);
+                        else acc[i][j] = fmaxf(acc[i][j], fabsf(diff));
                     }
             }
         }
@@ -200,8 +201,11 @@ cudaError_t launch_cc_select(const float* Q, int64_t n, const float* R, int64_t 
     if (metric == kL2)
         return wide ? launch_rows<kL2, 64>(Q, n, R, m, d, cand, st)
                     : launch_rows<kL2, 16>(Q, n, R, m, d, cand, st);
-    return wide ? launch_rows<kL1, 64>(Q, n, R, m, d, cand, st)
-                : launch_rows<kL1, 16>(Q, n, R, m, d, cand, st);
+    if (metric == kL1)
+        return wide ? launch_rows<kL1, 64>(Q, n, R, m, d, cand, st)
+                    : launch_rows<kL1, 16>(Q, n, R, m, d, cand, st);
+    return wide ? launch_rows<kLinf, 64>(Q, n, R, m, d, cand, st)
+                : launch_rows<kLinf, 16>(Q, n, R, m, d, cand, st);
 }
 
 }  // namespace knn

@@ -55,6 +55,19 @@ __host__ __device__ inline double ff_rel_bound(int d) {
     return e * e * 2.8421709430404007e-14 + e * 1.1102230246251565e-16;
 }
 
+// One coordinate's contribution: squared (L2), absolute value added (L1) or
+// maximum of absolute values (L-infinity, Chebyshev).
+template <int METRIC>
+__device__ __forceinline__ float acc_f32(float acc, float diff) {
+    if (METRIC == kL2) return fmaf(diff, diff, acc);
+    if (METRIC == kL1) return acc + fabsf(diff);
+    return fmaxf(acc, fabsf(diff));
+}
+template <int METRIC>
+__device__ __forceinline__ float combine_f32(float a, float b) {
+    return METRIC == kLinf ? fmaxf(a, b) : a + b;
+}
+
 template <int METRIC>
 __device__ __forceinline__ float dist_f32(const float* q, const float* __restrict__ r, int d) {
     float acc = 0.f;
@@ -65,21 +78,14 @@ __device__ __forceinline__ float dist_f32(const float* q, const float* __restric
         for (int t = 0; t < d / 4; ++t) {
             const float4 x = __ldg(r4 + t);
             const float4 y = q4[t];
-            const float e0 = y.x - x.x, e1 = y.y - x.y, e2 = y.z - x.z, e3 = y.w - x.w;
-            if (METRIC == kL2) {
-                acc = fmaf(e0, e0, acc); acc = fmaf(e1, e1, acc);
-                acc = fmaf(e2, e2, acc); acc = fmaf(e3, e3, acc);
-            } else {
-                acc += fabsf(e0); acc += fabsf(e1); acc += fabsf(e2); acc += fabsf(e3);
-            }
+            acc = acc_f32<METRIC>(acc, y.x - x.x);
+            acc = acc_f32<METRIC>(acc, y.y - x.y);
+            acc = acc_f32<METRIC>(acc, y.z - x.z);
+            acc = acc_f32<METRIC>(acc, y.w - x.w);
         }
         return acc;
     }
-    for (int t = 0; t < d; ++t) {
-        const float diff = q[t] - __ldg(r + t);
-        if (METRIC == kL2) acc = fmaf(diff, diff, acc);
-        else acc += fabsf(diff);
-    }
+    for (int t = 0; t < d; ++t) acc = acc_f32<METRIC>(acc, q[t] - __ldg(r + t));
     return acc;
 }
 
@@ -90,7 +96,8 @@ __device__ __forceinline__ double dist_f64(const float* q, const float* __restri
     for (int t = 0; t < d; ++t) {
         const double diff = __dsub_rn(static_cast<double>(q[t]), static_cast<double>(__ldg(r + t)));
         if (METRIC == kL2) acc = __dadd_rn(acc, __dmul_rn(diff, diff));
-        else acc = __dadd_rn(acc, fabs(diff));
+        else if (METRIC == kL1) acc = __dadd_rn(acc, fabs(diff));
+        else acc = fmax(acc, fabs(diff));
     }
     return acc;
 }
@@ -121,13 +128,23 @@ __device__ __forceinline__ void ff_term(float& H, float& Lo, float x, float y) {
         p = neg ? -s : s;
         t = neg ? -e : e;
     }
+    if (METRIC == kLinf) {
+        // the exact |x - y| = p + t; keep the larger pair (both normalised)
+        if (p > H || (p == H && t > Lo)) { H = p; Lo = t; }
+        return;
+    }
     float hs, he;
     two_sum(H, p, hs, he);
     H = hs;
     Lo = __fadd_rn(Lo, __fadd_rn(t, he));
 }
 
+template <int METRIC = kL2>
 __device__ __forceinline__ void ff_combine(float& H, float& Lo, float H2, float Lo2) {
+    if (METRIC == kLinf) {
+        if (H2 > H || (H2 == H && Lo2 > Lo)) { H = H2; Lo = Lo2; }
+        return;
+    }
     float s, e;
     two_sum(H, H2, s, e);
     H = s;
@@ -267,23 +284,19 @@ __device__ void exact_keys(uint64_t* keys, int cnt, const float* __restrict__ R,
 #pragma unroll
                     for (int u = 0; u < G; ++u) {
                         const float4 r = x[u][v];
-                        const float e0f = y.x - r.x, e1 = y.y - r.y, e2 = y.z - r.z, e3 = y.w - r.w;
-                        if (METRIC == kL2) {
-                            acc[u] = fmaf(e0f, e0f, acc[u]); acc[u] = fmaf(e1, e1, acc[u]);
-                            acc[u] = fmaf(e2, e2, acc[u]); acc[u] = fmaf(e3, e3, acc[u]);
-                        } else {
-                            acc[u] += fabsf(e0f); acc[u] += fabsf(e1);
-                            acc[u] += fabsf(e2); acc[u] += fabsf(e3);
-                        }
+                        acc[u] = acc_f32<METRIC>(acc[u], y.x - r.x);
+                        acc[u] = acc_f32<METRIC>(acc[u], y.y - r.y);
+                        acc[u] = acc_f32<METRIC>(acc[u], y.z - r.z);
+                        acc[u] = acc_f32<METRIC>(acc[u], y.w - r.w);
                     }
                 }
             }
 #pragma unroll
             for (int u = 0; u < G; ++u) {
                 float v = acc[u];
-                v += __shfl_xor_sync(0xffffffffu, v, 4);
-                v += __shfl_xor_sync(0xffffffffu, v, 2);
-                v += __shfl_xor_sync(0xffffffffu, v, 1);
+                v = combine_f32<METRIC>(v, __shfl_xor_sync(0xffffffffu, v, 4));
+                v = combine_f32<METRIC>(v, __shfl_xor_sync(0xffffffffu, v, 2));
+                v = combine_f32<METRIC>(v, __shfl_xor_sync(0xffffffffu, v, 1));
                 const int e = e0 + 4 * u + g;
                 if (sub == 0 && raw[u] != kEmptyKey)
                     keys[e] = make_key(v, static_cast<uint32_t>(raw[u]));
@@ -331,7 +344,7 @@ __device__ void refine_ff(const WarpScratch& w, int nr, const float* __restrict_
             for (int o = 4; o > 0; o >>= 1) {
                 const float H2 = __shfl_xor_sync(0xffffffffu, H, o);
                 const float L2 = __shfl_xor_sync(0xffffffffu, Lo, o);
-                ff_combine(H, Lo, H2, L2);
+                ff_combine<METRIC>(H, Lo, H2, L2);
             }
             if (sub == 0 && p >= 0) w.d64[p] = ff_pack(H, Lo);
         }
@@ -994,14 +1007,10 @@ fallback_kernel(FinalizeArgs a, double* __restrict__ scratch) {
 #pragma unroll
                     for (int u = 0; u < 4; ++u) {
                         const float4 x = __ldg(r4 + u * d4 + t);
-                        const float e0 = y.x - x.x, e1 = y.y - x.y, e2 = y.z - x.z, e3 = y.w - x.w;
-                        if (METRIC == kL2) {
-                            acc[u] = fmaf(e0, e0, acc[u]); acc[u] = fmaf(e1, e1, acc[u]);
-                            acc[u] = fmaf(e2, e2, acc[u]); acc[u] = fmaf(e3, e3, acc[u]);
-                        } else {
-                            acc[u] += fabsf(e0); acc[u] += fabsf(e1);
-                            acc[u] += fabsf(e2); acc[u] += fabsf(e3);
-                        }
+                        acc[u] = acc_f32<METRIC>(acc[u], y.x - x.x);
+                        acc[u] = acc_f32<METRIC>(acc[u], y.y - x.y);
+                        acc[u] = acc_f32<METRIC>(acc[u], y.z - x.z);
+                        acc[u] = acc_f32<METRIC>(acc[u], y.w - x.w);
                     }
                 }
             } else {
@@ -1136,8 +1145,21 @@ cudaError_t launch_finalize(const FinalizeArgs& a_in, cudaStream_t st, int* laun
     const int nv = (aligned && (a.d & 3) == 0 && a.d <= 128) ? (a.d + 31) / 32 : 0;
     if (launches) ++*launches;
     if (a.metric == kL2) return launch_finalize_m<kL2>(a, nv, P, wpb, smem, grid, st);
-    return launch_finalize_m<kL1>(a, nv, P, wpb, smem, grid, st);
+    if (a.metric == kL1) return launch_finalize_m<kL1>(a, nv, P, wpb, smem, grid, st);
+    return launch_finalize_m<kLinf>(a, nv, P, wpb, smem, grid, st);
 }
+
+template <int METRIC>
+cudaError_t launch_fallback_m(const FinalizeArgs& a, double* scratch, int32_t grid, size_t smem,
+                              cudaStream_t st) {
+    cudaError_t err = cudaFuncSetAttribute(fallback_kernel<METRIC>,
+                                           cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                           static_cast<int>(smem));
+    if (err != cudaSuccess) return err;
+    fallback_kernel<METRIC><<<grid, kFbThreads, smem, st>>>(a, scratch);
+    return cudaGetLastError();
+}
+
 
 cudaError_t launch_fallback(const FinalizeArgs& a, double* scratch, int32_t grid,
                             cudaStream_t st, int* launches) {
@@ -1146,20 +1168,9 @@ cudaError_t launch_fallback(const FinalizeArgs& a, double* scratch, int32_t grid
                         (static_cast<size_t>(a.d) + 4) * sizeof(float);
     if (smem + sizeof(FbShared) > 227 * 1024) return cudaErrorInvalidValue;
     if (launches) ++*launches;
-    if (a.metric == kL2) {
-        cudaError_t err = cudaFuncSetAttribute(fallback_kernel<kL2>,
-                                               cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                               static_cast<int>(smem));
-        if (err != cudaSuccess) return err;
-        fallback_kernel<kL2><<<grid, kFbThreads, smem, st>>>(a, scratch);
-    } else {
-        cudaError_t err = cudaFuncSetAttribute(fallback_kernel<kL1>,
-                                               cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                               static_cast<int>(smem));
-        if (err != cudaSuccess) return err;
-        fallback_kernel<kL1><<<grid, kFbThreads, smem, st>>>(a, scratch);
-    }
-    return cudaGetLastError();
+    if (a.metric == kL2) return launch_fallback_m<kL2>(a, scratch, grid, smem, st);
+    if (a.metric == kL1) return launch_fallback_m<kL1>(a, scratch, grid, smem, st);
+    return launch_fallback_m<kLinf>(a, scratch, grid, smem, st);
 }
 
 }  // namespace knn

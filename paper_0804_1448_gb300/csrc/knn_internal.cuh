@@ -24,7 +24,7 @@
 
 namespace knn {
 
-enum Metric : int { kL2 = 0, kL1 = 1 };
+enum Metric : int { kL2 = 0, kL1 = 1, kLinf = 2 };
 
 constexpr uint64_t kEmptyKey = ~0ull;  // sentinel for an empty candidate slot
 

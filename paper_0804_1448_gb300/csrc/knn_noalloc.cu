@@ -75,7 +75,8 @@ using namespace knn;
 extern "C" knn_status knn_search_static(const float* R, int64_t m, const float* Q, int64_t n,
                                         int32_t d, int32_t k, knn_metric metric, float* dist_out,
                                         int32_t* idx_out, void* cuda_stream) {
-    if (m < 1 || n < 0 || d < 1 || k < 1 || k > m || (metric != KNN_L2 && metric != KNN_L1))
+    if (m < 1 || n < 0 || d < 1 || k < 1 || k > m ||
+        (metric != KNN_L2 && metric != KNN_L1 && metric != KNN_LINF))
         return KNN_ERR_INVALID;
     if (!R || (n > 0 && (!Q || !dist_out || !idx_out))) return KNN_ERR_INVALID;
     if (k > KNN_K_MAX || m > 0x7fffffffLL || n > 0x7fffffffLL) return KNN_ERR_UNSUPPORTED;

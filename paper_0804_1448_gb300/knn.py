@@ -26,7 +26,8 @@ _lib = ctypes.CDLL(LIB_PATH)
 
 KNN_L2, KNN_L1 = 0, 1
 KNN_FP32, KNN_TF32, KNN_BF16 = 0, 1, 2
-METRICS = {"l2": KNN_L2, "l1": KNN_L1}
+KNN_LINF = 2
+METRICS = {"l2": KNN_L2, "l1": KNN_L1, "linf": KNN_LINF}
 PRECISIONS = {"fp32": KNN_FP32, "tf32": KNN_TF32, "bf16": KNN_BF16}
 STATUS = {0: "KNN_OK", 1: "KNN_ERR_INVALID", 2: "KNN_ERR_OOM", 3: "KNN_ERR_CUDA",
           4: "KNN_ERR_TIMEOUT", 5: "KNN_ERR_NOREF", 6: "KNN_ERR_BUSY",

@@ -51,14 +51,14 @@ def check(knn, R, Q, k, metric, device_io=True):
     return rows, exact, st
 
 
-@pytest.mark.parametrize("metric", ["l2", "l1"])
+@pytest.mark.parametrize("metric", ["l2", "l1", "linf"])
 def test_uniform_n1200_d8_k20(knn, metric):
     R, Q, k = inputs.workload("uniform_n1200_d8_k20")
     rows, exact, _ = check(knn, R, Q, k, metric)
     assert rows == 1200
 
 
-@pytest.mark.parametrize("metric", ["l2", "l1"])
+@pytest.mark.parametrize("metric", ["l2", "l1", "linf"])
 @pytest.mark.parametrize("n,m,d,k", [
     (1, 1, 1, 1),            # single point
     (7, 300, 3, 5),          # n below one query tile
@@ -86,7 +86,7 @@ def test_host_and_device_io_agree(knn):
 def test_queries_drawn_from_reference(knn):
     R = inputs.uniform(5000, 12, seed=15)
     Q = R[::37].copy()
-    for metric in ("l2", "l1"):
+    for metric in ("l2", "l1", "linf"):
         g_dist, g_idx, _ = run_case(knn, R, Q, 10, metric)
         assert np.all(g_dist[:, 0] == 0.0)
         np.testing.assert_array_equal(g_idx[:, 0], np.arange(0, 5000, 37))
@@ -98,7 +98,7 @@ def test_lattice_ties(knn):
     the smaller-index rule exactly."""
     R = inputs.lattice(9, 3)            # 729 points
     Q = inputs.lattice(9, 3)[::5] + np.float32(0.5) * (np.arange(3) == 0)
-    for metric in ("l2", "l1"):
+    for metric in ("l2", "l1", "linf"):
         for k in (1, 6, 27, 100):
             m = R.shape[0]
             g_dist, g_idx, _ = run_case(knn, R, Q, k, metric)
@@ -121,8 +121,11 @@ def near_tie_ladder(d, metric, n_q=12, rungs=48, m_far=1500, step=3e-6, seed=123
         if metric == "l2":
             u /= np.linalg.norm(u, axis=1, keepdims=True)
             s = 0.5 * np.sqrt(1.0 + step * np.arange(rungs))
-        else:
+        elif metric == "l1":
             u /= np.abs(u).sum(axis=1, keepdims=True)
+            s = 0.5 * (1.0 + step * np.arange(rungs))
+        else:
+            u /= np.abs(u).max(axis=1, keepdims=True)
             s = 0.5 * (1.0 + step * np.arange(rungs))
         rows.append((Q[i].astype(np.float64) + s[:, None] * u).astype(np.float32))
     R = np.concatenate(rows)
@@ -130,7 +133,7 @@ def near_tie_ladder(d, metric, n_q=12, rungs=48, m_far=1500, step=3e-6, seed=123
     return np.ascontiguousarray(R[perm]), Q
 
 
-@pytest.mark.parametrize("metric", ["l2", "l1"])
+@pytest.mark.parametrize("metric", ["l2", "l1", "linf"])
 @pytest.mark.parametrize("d", [96, 33])
 def test_near_tie_ladder_exact_order(knn, metric, d):
     """Distances 3e-6 apart: beyond float32's resolution at this d, so the
@@ -169,7 +172,7 @@ def test_duplicates_across_splits(knn):
     base = inputs.uniform(300, 8, seed=77)
     R = np.concatenate([base] * 20)      # every point 20 times, spread over the range
     Q = base[:40].copy()
-    for metric in ("l2", "l1"):
+    for metric in ("l2", "l1", "linf"):
         rows, exact, st = check(knn, R, Q, 30, metric)
         g_dist, g_idx, _ = run_case(knn, R, Q, 30, metric)
         o_dist, o_idx = oracle.knn(R, Q, 30, metric)
@@ -186,7 +189,7 @@ def test_prefix_property(knn):
         np.testing.assert_array_equal(d_k, d_big[:, :k])
 
 
-@pytest.mark.parametrize("metric", ["l2", "l1"])
+@pytest.mark.parametrize("metric", ["l2", "l1", "linf"])
 def test_uniform_n38400_d96_k20_sampled(knn, metric):
     """Full-size Table-1 shape (N = 38400, D = 96, k = 20): all queries run on
     the GPU in one call; 96 sampled rows are checked against the oracle."""

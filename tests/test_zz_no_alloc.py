@@ -41,7 +41,7 @@ def static_search(torch, knn, Rd, Qd, k, metric):
     return dist.cpu().numpy(), idx.cpu().numpy()
 
 
-@pytest.mark.parametrize("metric", ["l2", "l1"])
+@pytest.mark.parametrize("metric", ["l2", "l1", "linf"])
 def test_two_calls_match_knn_search(env, metric):
     torch, knn = env
     R = inputs.uniform(5000, 24, seed=401)
