@@ -175,6 +175,23 @@ knn_status knn_get_profile(knn_handle h, float* ms, const char** names, int32_t 
                            int32_t* count);
 
 /*
+ * Self-join with self-exclusion: for every point r_i of the current reference
+ * set, its k nearest OTHER reference points (index i itself left out; other
+ * points equal to r_i stay, at distance 0).  This is the neighbour relation of
+ * the entropy estimate of Sec. 2.2 (rho_k(y_i) is the distance from y_i to
+ * its k-th nearest neighbour among the other points).  Writes m x k outputs
+ * (device pointers, knn_search's conventions and precision); asynchronous on
+ * cuda_stream (NULL = the handle's stream).  Runs as a search of R against
+ * itself for k + 1 neighbours and a device pass that drops each row's own
+ * index (or, when more than k equal points precede it, the last entry).
+ * Errors: KNN_ERR_INVALID (null pointer, k < 1, k + 1 > m, bad metric),
+ * KNN_ERR_NOREF, KNN_ERR_UNSUPPORTED (k + 1 > KNN_K_MAX), KNN_ERR_OOM,
+ * KNN_ERR_CUDA.
+ */
+knn_status knn_search_self(knn_handle h, int32_t k, knn_metric metric, float* dist_out,
+                           int32_t* idx_out, void* cuda_stream);
+
+/*
  * The float32 search of knn_search (distance from coordinate differences,
  * float64 re-check of near ties, exact fallback) for callers that cannot
  * allocate device memory when they search: code running while a CUDA graph is

@@ -896,6 +896,46 @@ knn_status knn_batch_info_get(knn_handle h, knn_batch_info* out) {
     return KNN_OK;
 }
 
+knn_status knn_search_self(knn_handle h, int32_t k, knn_metric metric, float* dist_out,
+                           int32_t* idx_out, void* cuda_stream) {
+    if (!h || !dist_out || !idx_out) return KNN_ERR_INVALID;
+    if (!h->ref) return KNN_ERR_NOREF;
+    if (k < 1 || static_cast<int64_t>(k) + 1 > h->ref->m) return KNN_ERR_INVALID;
+    knn_status s = check_search_args(h, h->ref->m, h->ref->d, k + 1, metric);
+    if (s != KNN_OK) return s;
+    KNN_CUDA(h, cudaSetDevice(h->device));
+    cudaStream_t st = cuda_stream ? static_cast<cudaStream_t>(cuda_stream) : h->stream;
+    RefSet& rs = *h->ref;
+    const int64_t n = rs.m;
+    SearchPlan sp;
+    s = plan_search(h, n, k + 1, metric, 1, &sp);
+    if (s != KNN_OK) return s;
+    if (sp.tensor) {
+        s = build_lowp(h, sp.prec);
+        if (s != KNN_OK) return s;
+    }
+    // the (k+1)-neighbour rows go to workspace after the search's own slices
+    Carve cv;
+    cv.off = sp.bytes;
+    const size_t off_d = cv.take(static_cast<size_t>(n) * (k + 1) * sizeof(float));
+    const size_t off_i = cv.take(static_cast<size_t>(n) * (k + 1) * sizeof(int32_t));
+    s = ensure_workspace(h, cv.off);
+    if (s != KNN_OK) return s;
+    unsigned char* ws = h->ws;
+    float* dtmp = reinterpret_cast<float*>(ws + off_d);
+    int32_t* itmp = reinterpret_cast<int32_t*>(ws + off_i);
+    int l = 0;
+    h->nstages = 0;
+    RefView rv{rs.R, rs.m, rs.d, rs.R_lp, rs.kp, rs.rmax2};
+    s = enqueue_search(h, sp, rv, rs.R, n, k + 1, metric, dtmp, itmp, ws, &h->counters->fallback_count,
+                       st, &l, false);
+    if (s != KNN_OK) return s;
+    KNN_CUDA(h, launch_drop_self(dtmp, itmp, n, k, dist_out, idx_out, st, &l));
+    h->launches += l;
+    h->searches += 1;
+    return KNN_OK;
+}
+
 knn_status knn_sync(knn_handle h) {
     if (!h) return KNN_ERR_INVALID;
     KNN_CUDA(h, cudaSetDevice(h->device));

@@ -1097,6 +1097,32 @@ fallback_kernel(FinalizeArgs a, double* __restrict__ scratch) {
 
 }  // namespace
 
+// Self-join: row i of the (k+1)-neighbour result without reference i (or
+// without its last entry when i is not among them).  One thread per row.
+__global__ void drop_self_kernel(const float* __restrict__ din, const int32_t* __restrict__ iin,
+                                 int64_t n, int32_t k, float* __restrict__ dout,
+                                 int32_t* __restrict__ iout) {
+    const int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const float* dr = din + i * (k + 1);
+    const int32_t* ir = iin + i * (k + 1);
+    int o = 0;
+    for (int s = 0; s <= k && o < k; ++s) {
+        if (ir[s] == static_cast<int32_t>(i)) continue;
+        dout[i * k + o] = dr[s];
+        iout[i * k + o] = ir[s];
+        ++o;
+    }
+}
+
+cudaError_t launch_drop_self(const float* din, const int32_t* iin, int64_t n, int32_t k, float* dout,
+                             int32_t* iout, cudaStream_t st, int* launches) {
+    const unsigned grid = static_cast<unsigned>((n + 255) / 256);
+    if (launches) ++*launches;
+    drop_self_kernel<<<grid, 256, 0, st>>>(din, iin, n, k, dout, iout);
+    return cudaGetLastError();
+}
+
 int finalize_max_pool() { return kMaxPool; }
 
 template <int METRIC, int NV>

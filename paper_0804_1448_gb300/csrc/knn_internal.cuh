@@ -124,6 +124,11 @@ int cc_max_candidates();
 cudaError_t launch_finalize(const FinalizeArgs& a, cudaStream_t st, int* launches);
 int finalize_max_pool();   // largest S*c one finalize pass handles
 
+// Self-join rows: the n x (k+1) result of searching R against itself, minus
+// each row's own index (or its last entry), into n x k outputs.
+cudaError_t launch_drop_self(const float* din, const int32_t* iin, int64_t n, int32_t k, float* dout,
+                             int32_t* iout, cudaStream_t st, int* launches);
+
 // Exact float64 pass for the queued queries.  scratch holds grid*m doubles.
 cudaError_t launch_fallback(const FinalizeArgs& a, double* scratch, int32_t grid,
                             cudaStream_t st, int* launches);

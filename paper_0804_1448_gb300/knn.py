@@ -87,6 +87,7 @@ _SIGS = {
                                           ctypes.POINTER(_i64)]),
     "knn_reserve": (ctypes.c_int, [_H, _i64]),
     "knn_search_batch": (ctypes.c_int, [_H, ctypes.POINTER(knn_instance), _i32, _i32, _P]),
+    "knn_search_self": (ctypes.c_int, [_H, _i32, ctypes.c_int, _P, _P, _P]),
     "knn_batch_info_get": (ctypes.c_int, [_H, ctypes.POINTER(knn_batch_info)]),
     "knn_destroy": (ctypes.c_int, [_H]),
     "knn_status_string": (ctypes.c_char_p, [ctypes.c_int]),
@@ -112,6 +113,7 @@ knn_create_shared = _lib.knn_create_shared
 knn_workspace_size = _lib.knn_workspace_size
 knn_reserve = _lib.knn_reserve
 knn_search_batch = _lib.knn_search_batch
+knn_search_self = _lib.knn_search_self
 knn_batch_info_get = _lib.knn_batch_info_get
 knn_destroy = _lib.knn_destroy
 knn_status_string = _lib.knn_status_string
@@ -240,6 +242,19 @@ class Index:
             dist = torch.empty((n, k), dtype=torch.float32, device=Q.device)
             idx = torch.empty((n, k), dtype=torch.int32, device=Q.device)
         self.search_into(Q, k, dist, idx, metric, stream)
+        return dist, idx
+
+    def search_self(self, k: int, metric: str = "l2", stream=None):
+        """knn_search_self: for every reference point its k nearest other
+        reference points; (dist, idx) device tensors m x k."""
+        import torch
+        dist = torch.empty((self.m, k), dtype=torch.float32, device=f"cuda:{self.device}")
+        idx = torch.empty((self.m, k), dtype=torch.int32, device=f"cuda:{self.device}")
+        sp = None
+        if stream is not None:
+            sp = getattr(stream, "cuda_stream", stream) or 1
+        self._check(knn_search_self(self.h, k, METRICS[metric], dist.data_ptr(), idx.data_ptr(), sp),
+                    "knn_search_self")
         return dist, idx
 
     def search_batch(self, instances, flags: int = 0, stream=None):
