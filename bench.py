@@ -60,6 +60,8 @@ def parse_args():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-serve", action="store_true")
     p.add_argument("--no-batch", action="store_true")
+    p.add_argument("--sweep", action="store_true",
+                   help="Table 1 grid (N x D, k = 20) instead of the bench line")
     p.add_argument("--serve-requests", type=int, default=48)
     return p.parse_args()
 
@@ -296,10 +298,77 @@ def batch_bench(local, args, peak_tflops):
                       "tune_device_ms": tuned["tune_ms"], "tune_wall_s": tune_s}}
 
 
+# Table 1 of the paper, BF-CUDA seconds (8800 GTX, float32, host<->device copies
+# included), by D then N.
+TABLE1_N = (1200, 2400, 4800, 9600, 19200, 38400)
+TABLE1_BF_CUDA = {
+    8: (0.02, 0.10, 0.38, 1.71, 7.93, 31.41),
+    16: (0.02, 0.10, 0.38, 1.78, 7.98, 31.31),
+    32: (0.02, 0.11, 0.40, 1.81, 8.35, 33.40),
+    64: (0.03, 0.12, 0.44, 2.00, 9.52, 37.61),
+    80: (0.03, 0.12, 0.46, 2.05, 9.93, 39.98),
+    96: (0.03, 0.13, 0.48, 2.07, 10.41, 43.74),
+}
+
+
+def sweep(args):
+    """The Table 1 grid: N = n = m in TABLE1_N, D in {8, 16, 32, 64, 80, 96},
+    k = 20, uniform [0,1) points, Euclidean.  Per point: the bf16 and float32
+    searches with inputs resident on the device (CUDA events, median of 5),
+    and the bf16 search end to end through the C ABI with host buffers (the
+    paper's BF-CUDA times include the copies)."""
+    import numpy as np
+    import torch
+    from paper_0804_1448_gb300 import inputs, knn
+    dev = torch.device("cuda", 0)
+    stream = torch.cuda.current_stream(dev)
+    rows = []
+    for D in sorted(TABLE1_BF_CUDA):
+        for ni, N in enumerate(TABLE1_N):
+            R = inputs.uniform(N, D, seed=1000 + D)
+            Q = inputs.uniform(N, D, seed=2000 + D)
+            Rd, Qd = torch.from_numpy(R).to(dev), torch.from_numpy(Q).to(dev)
+            dist = torch.empty((N, 20), device=dev)
+            idx = torch.empty((N, 20), dtype=torch.int32, device=dev)
+            row = {"N": N, "D": D, "paper_bf_cuda_s": TABLE1_BF_CUDA[D][ni]}
+            for prec in ("bf16", "fp32"):
+                ix = knn.Index(0, prec)
+                ix.set_reference(Rd)
+                for _ in range(2):
+                    ix.search_into(Qd, 20, dist, idx, "l2", stream)
+                times = []
+                for _ in range(5):
+                    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                    e0.record(stream)
+                    ix.search_into(Qd, 20, dist, idx, "l2", stream)
+                    e1.record(stream)
+                    torch.cuda.synchronize(dev)
+                    times.append(e0.elapsed_time(e1))
+                row[f"{prec}_device_ms"] = float(np.median(times))
+                if prec == "bf16":
+                    Qh = torch.from_numpy(Q).pin_memory()
+                    dh = torch.empty((N, 20), dtype=torch.float32).pin_memory()
+                    ih = torch.empty((N, 20), dtype=torch.int32).pin_memory()
+                    ix.search_into(Qh, 20, dh, ih, "l2")
+                    t = []
+                    for _ in range(5):
+                        t0 = time.perf_counter()
+                        ix.search_into(Qh, 20, dh, ih, "l2")
+                        t.append(time.perf_counter() - t0)
+                    row["bf16_e2e_ms"] = float(np.median(t) * 1e3)
+                ix.close()
+            row["speedup_e2e_vs_paper"] = row["paper_bf_cuda_s"] * 1e3 / row["bf16_e2e_ms"]
+            rows.append(row)
+    print(json.dumps({"sweep": "table1", "k": 20, "distance": "l2", "rows": rows}), flush=True)
+
+
 def main():
     args = parse_args()
     if args.impl == "reference":
         run_reference(args)
+        return
+    if args.sweep:
+        sweep(args)
         return
     world, rank, local = dist_env()
     import numpy as np

@@ -642,16 +642,24 @@ TcPlan tc_plan(int64_t n, int64_t m, int32_t d, int32_t kp, int prec, int32_t c,
     int stride = 4096 / kTileN;
     while (tiles_total * gpt / stride > 1024) stride *= 2;
     const int tps = static_cast<int>(chunk / kTileN);
-    p.stride = stride;
-    p.spt = (tps + stride - 1) / stride;
-    p.G = S * p.spt * gpt;
     // c' = lambda + 4 sqrt(lambda) + 4: with N references above the threshold
     // the sampled count is Binomial(N, 1/stride); N < c with c' sampled passing
     // has probability below 2e-6 per query at lambda = 5 (the bench shape), and
-    // such a query is finished by the exact fallback
-    const double lambda = static_cast<double>(c) / stride;
-    p.cprime = static_cast<int>(std::ceil(lambda + 4.0 * std::sqrt(lambda) + 4.0));
-    p.pilot = (p.G >= 2 * p.cprime) ? 1 : 0;
+    // such a query is finished by the exact fallback.  The c'-th largest of G
+    // group maxima needs G comfortably above c': sample denser (halve the
+    // stride) until G >= c' + 8, and run no pilot (every reference appended)
+    // only when even every tile does not give that many groups.
+    for (;;) {
+        p.stride = stride;
+        p.spt = (tps + stride - 1) / stride;
+        p.G = S * p.spt * gpt;
+        const double lambda = static_cast<double>(c) / stride;
+        p.cprime = static_cast<int>(std::ceil(lambda + 4.0 * std::sqrt(lambda) + 4.0));
+        if (p.G >= p.cprime + 8 || stride == 1 || p.G > 1024) break;
+        stride /= 2;
+    }
+    // the threshold kernel holds at most 64 x 32 group maxima per query
+    p.pilot = (p.G >= p.cprime + 8 && p.G <= 2048) ? 1 : 0;
     // list capacity per (query, split, column group): twice the expected hits plus slack
     if (p.pilot) {
         const int64_t expect = static_cast<int64_t>(p.cprime) * stride;
