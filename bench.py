@@ -346,6 +346,10 @@ def sweep(args):
                     times.append(e0.elapsed_time(e1))
                 row[f"{prec}_device_ms"] = float(np.median(times))
                 if prec == "bf16":
+                    st = ix.stats()
+                    row["bf16_fallback_queries_per_search"] = st["fallback_queries"] / 7.0
+                    row["bf16_fallback_reasons"] = [st["fallback_short_list"], st["fallback_overflow"],
+                                                    st["fallback_wide_cut"], st["fallback_uncertified"]]
                     Qh = torch.from_numpy(Q).pin_memory()
                     dh = torch.empty((N, 20), dtype=torch.float32).pin_memory()
                     ih = torch.empty((N, 20), dtype=torch.int32).pin_memory()

@@ -159,6 +159,7 @@ struct TcPlan {
     int32_t cprime;      // order statistic of the group maxima used as threshold
     int32_t pilot;       // 0: no pilot, every reference is appended
     int32_t cap;         // list capacity per (query, split, column group)
+    int32_t raw;         // filter stages hit values as float32 (else 16-bit codes)
     size_t smem_filter;
 };
 TcPlan tc_plan(int64_t n, int64_t m, int32_t d, int32_t kp, int prec, int32_t c, int num_sms);

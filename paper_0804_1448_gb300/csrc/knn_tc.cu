@@ -65,10 +65,13 @@ constexpr uint32_t kTmemCols = 2 * kTileN;          // two accumulators
 constexpr int kMaxStages = 12;
 constexpr size_t kSmemLimit = 232448;
 constexpr int kAugCols = 4;
-// Words per thread in the hit-staging area: a slice's 32 values packed to
-// their upper 16 bits (16 words) + pad, so that eight lanes' 16-byte stores
-// fall on distinct banks.
+// Words per thread in the hit-staging area.  Codes: a slice's 32 values
+// packed to their upper 16 bits (16 words) + pad, so that eight lanes'
+// 16-byte stores fall on distinct banks.  Raw: the 32 float32 values, each
+// 16-byte quarter stored only by lanes with a hit in it (few per store, so
+// bank conflicts do not arise).
 constexpr int kStageWords = 20;
+constexpr int kStageWordsRaw = 32;
 
 struct TcArgs {
     int64_t n, m;
@@ -92,10 +95,11 @@ struct TcArgs {
 
 // A: the query tile, kb K blocks (resident); B: a ring of `stages` stages of
 // kTileN references x kbs K blocks; hit staging (filter only); barriers.
-__host__ __device__ constexpr size_t tc_smem_bytes(int kb, int kbs, int stages, bool pilot) {
+__host__ __device__ constexpr size_t tc_smem_bytes(int kb, int kbs, int stages, bool pilot,
+                                                   bool raw = false) {
     return 1024 + static_cast<size_t>(kQTileBytes) * kb +
            static_cast<size_t>(kRTileBytes) * kbs * stages +
-           (pilot ? 0 : static_cast<size_t>(kEpi) * kStageWords * 4) + 512;
+           (pilot ? 0 : static_cast<size_t>(kEpi) * (raw ? kStageWordsRaw : kStageWords) * 4) + 512;
 }
 
 // Hit values are kept as a 16-bit code of acc: with B a power of two and
@@ -121,6 +125,24 @@ __device__ __forceinline__ void append(uint64_t* list, int& cnt, int cap, uint32
     ++cnt;
 }
 
+// Raw staging: the list key of one hit from its float32 acc x, as bits 8..23
+// of 3B - x (in (2B, 4B) for |x| < B, one binade): it falls with acc in steps
+// of B 2^-14, like 0xffff minus the code above.
+__device__ __forceinline__ void append_raw(uint64_t* list, int& cnt, int cap, float b3, float x,
+                                           uint32_t j) {
+    const uint32_t hi = __byte_perm(__float_as_uint(b3 - x), 0u, 0x4421);
+    if (cnt < cap) list[cnt] = (static_cast<uint64_t>(hi) << 32) | j;
+    ++cnt;
+}
+
+// Store v to [addr] only when sel != 0 (a predicated 16-byte shared store).
+__device__ __forceinline__ void st_shared_if(uint32_t sel, uint32_t addr, uint32_t v0, uint32_t v1,
+                                             uint32_t v2, uint32_t v3) {
+    asm volatile("{\n .reg .pred p;\n setp.ne.b32 p, %0, 0;\n"
+                 " @p st.shared.v4.b32 [%1], {%2, %3, %4, %5};\n}"
+                 :: "r"(sel), "r"(addr), "r"(v0), "r"(v1), "r"(v2), "r"(v3) : "memory");
+}
+
 // MMAs of one 128-byte K block of one reference tile.  Fully unrolled over the
 // four 32-byte K steps (a runtime guard skips steps past the data): issue from
 // the single MMA thread must keep pace with the tensor core.  Descriptors
@@ -137,7 +159,7 @@ __device__ __forceinline__ void issue_kblock(uint32_t d_tmem, uint64_t a_desc, u
 
 // KBT > 0: whole-tile stages of exactly KBT K blocks (compile-time, unrolled);
 // KBT == 0: any K-block count, whole-tile or single-K-block stages.
-template <int PREC, bool PILOT, int KBT>
+template <int PREC, bool PILOT, int KBT, bool RAW>
 __global__ void __launch_bounds__(kThreads, 1)
 tc_kernel(const __grid_constant__ CUtensorMap tmap_q, const __grid_constant__ CUtensorMap tmap_r,
           TcArgs a) {
@@ -152,7 +174,8 @@ tc_kernel(const __grid_constant__ CUtensorMap tmap_q, const __grid_constant__ CU
     unsigned char* sA = smem;
     unsigned char* sB = sA + static_cast<size_t>(KB) * kQTileBytes;
     uint32_t* stage = reinterpret_cast<uint32_t*>(sB + NST * stage_bytes);
-    uint64_t* bars = reinterpret_cast<uint64_t*>(stage + (PILOT ? 0 : kEpi * kStageWords));
+    constexpr int kSW = RAW ? kStageWordsRaw : kStageWords;
+    uint64_t* bars = reinterpret_cast<uint64_t*>(stage + (PILOT ? 0 : kEpi * kSW));
     uint64_t* full = bars;
     uint64_t* empty = bars + kMaxStages;
     uint64_t* a_full = bars + 2 * kMaxStages;
@@ -278,13 +301,15 @@ tc_kernel(const __grid_constant__ CUtensorMap tmap_q, const __grid_constant__ CU
         const int64_t q = q0 + row;
         const bool active = q < a.n;
         const uint32_t lane_addr = tmem + (static_cast<uint32_t>(quarter * 32) << 16);
-        uint32_t* st = stage + et * kStageWords;
+        uint32_t* st = stage + et * kSW;
         constexpr int gpt = kTileN / 32;            // groups of 32 references per tile
         uint64_t* list = nullptr;
         uint32_t* gout = nullptr;
         if (PILOT) gout = a.gmax + q * a.G + static_cast<int64_t>(split) * a.spt * gpt;
         else list = a.lists + ((q * a.S + split) * kGroups + cg) * static_cast<int64_t>(a.cap);
         const uint32_t off3b = __float_as_uint((!PILOT && active) ? 3.f * a.qscale[q] : 0.f);
+        const uint32_t st_addr = smem_u32(st);
+        const uint32_t all_pass = a.append_all ? 0xffffffffu : 0u;
         int cnt = 0;
         for (int g = 0; g < nt; ++g) {
             const int buf = g & 1;
@@ -317,6 +342,36 @@ tc_kernel(const __grid_constant__ CUtensorMap tmap_q, const __grid_constant__ CU
 #pragma unroll
                         for (int u = 0; u < w2; ++u) v[u] = fmaxf(v[u], v[u + w2]);
                     if (active && nvalid > 0) gout[g * gpt + cg * 2 + sl] = ord_f32(v[0]);
+                } else if (RAW) {
+                    // sign bits, bit 31-u for element u, as four independent chains
+                    uint32_t m4[4] = {0u, 0u, 0u, 0u};
+#pragma unroll
+                    for (int u = 0; u < 8; ++u)
+#pragma unroll
+                        for (int h = 0; h < 4; ++h) m4[h] = __funnelshift_l(r[8 * h + u], m4[h], 1);
+                    const uint32_t sm = (m4[0] << 24) | (m4[1] << 16) | (m4[2] << 8) | m4[3];
+                    // a pass is acc >= 0: bit 31-u of `hits` is element u
+                    uint32_t hits = ~sm | all_pass;
+                    if (nvalid < 32) hits &= nvalid > 0 ? (0xffffffffu << (32 - nvalid)) : 0u;
+                    if (!active) hits = 0;
+                    if (hits) {
+                        // the values of the quarters holding a hit go to this
+                        // thread's staging words, which the loop reads back by index
+#pragma unroll
+                        for (int h = 0; h < 8; ++h)
+                            st_shared_if(hits & (0xf0000000u >> (4 * h)), st_addr + 16 * h,
+                                         r[4 * h], r[4 * h + 1], r[4 * h + 2], r[4 * h + 3]);
+                        const float b3 = __uint_as_float(off3b);
+                        const float* stf = reinterpret_cast<const float*>(st) + 31;
+                        const uint32_t jb = static_cast<uint32_t>(j0) + 31u;
+                        do {
+                            uint32_t p;
+                            asm("bfind.u32 %0, %1;" : "=r"(p) : "r"(hits));   // element 31-p
+                            hits ^= 1u << p;
+                            append_raw(list, cnt, a.cap, b3, stf[-static_cast<int>(p)], jb - p);
+                        } while (hits);
+                    }
+                    __syncwarp();
                 } else {
                     // sign bits, bit 31-u for element u, as four independent chains
                     uint32_t m4[4] = {0u, 0u, 0u, 0u};
@@ -534,11 +589,11 @@ bool make_map(CUtensorMap* map, const void* base, int64_t rows, int kp, int prec
 }
 
 
-template <int PREC, bool PILOT, int KBT>
+template <int PREC, bool PILOT, int KBT, bool RAW = false>
 cudaError_t launch_kernel(const TcPlan& p, const CUtensorMap& mq, const CUtensorMap& mr,
                           const TcArgs& a, cudaStream_t st) {
-    auto kern = tc_kernel<PREC, PILOT, KBT>;
-    const size_t smem = tc_smem_bytes(p.kb, p.kbs, p.stages, PILOT);
+    auto kern = tc_kernel<PREC, PILOT, KBT, RAW>;
+    const size_t smem = tc_smem_bytes(p.kb, p.kbs, p.stages, PILOT, RAW);
     cudaError_t err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                            static_cast<int>(smem));
     if (err != cudaSuccess) return err;
@@ -551,6 +606,15 @@ template <int PREC, bool PILOT>
 cudaError_t dispatch_kb(const TcPlan& p, const CUtensorMap& mq, const CUtensorMap& mr,
                         const TcArgs& a, cudaStream_t st) {
     if (p.kbs == p.kb) {   // whole-tile stages: unrolled issue for the common row lengths
+        if constexpr (!PILOT) {
+            if (p.raw) {
+                switch (p.kb) {
+                    case 1: return launch_kernel<PREC, false, 1, true>(p, mq, mr, a, st);
+                    case 2: return launch_kernel<PREC, false, 2, true>(p, mq, mr, a, st);
+                    default: break;
+                }
+            }
+        }
         switch (p.kb) {
             case 1: return launch_kernel<PREC, PILOT, 1>(p, mq, mr, a, st);
             case 2: return launch_kernel<PREC, PILOT, 2>(p, mq, mr, a, st);
@@ -605,10 +669,12 @@ TcPlan tc_plan(int64_t n, int64_t m, int32_t d, int32_t kp, int prec, int32_t c,
     p.stages = 0;
     // whole-tile stages (one TMA box and one wait per tile) when two fit,
     // else single-K-block stages, as many as fit
+    // (raw hit staging with them when it also fits: rows of up to 2 K blocks)
     for (int s = 4; s >= 2 && p.stages == 0; --s)
         if (tc_smem_bytes(p.kb, p.kb, s, false) <= kSmemLimit) {
             p.kbs = p.kb;
             p.stages = s;
+            p.raw = (p.kb <= 2 && tc_smem_bytes(p.kb, p.kb, s, false, true) <= kSmemLimit) ? 1 : 0;
         }
     for (int s = kMaxStages; s >= 2 && p.stages == 0; --s)
         if (tc_smem_bytes(p.kb, 1, s, false) <= kSmemLimit) {
@@ -649,26 +715,52 @@ TcPlan tc_plan(int64_t n, int64_t m, int32_t d, int32_t kp, int prec, int32_t c,
     // group maxima needs G comfortably above c': sample denser (halve the
     // stride) until G >= c' + 8, and run no pilot (every reference appended)
     // only when even every tile does not give that many groups.
+    // lambda counts the sampled references among the c best: c times the
+    // sampled fraction of the tiles (each split samples its tiles 0, stride,
+    // 2 stride, ...; a short split samples a larger share of its tiles).
+    // The group slots of a short split's missing tiles, and groups past the
+    // end of the data, hold no maximum: gvalid counts the real groups.
+    int64_t gvalid = 0;
     for (;;) {
         p.stride = stride;
         p.spt = (tps + stride - 1) / stride;
         p.G = S * p.spt * gpt;
-        const double lambda = static_cast<double>(c) / stride;
+        int64_t sampled = 0;
+        gvalid = 0;
+        for (int s = 0; s < S; ++s) {
+            const int64_t rows = std::min<int64_t>(m - s * chunk, chunk);
+            const int64_t tiles = (rows + kTileN - 1) / kTileN;
+            for (int64_t t = 0; t < tiles; t += stride) {
+                const int64_t v = std::min<int64_t>(rows - t * kTileN, kTileN);
+                sampled += v;
+                gvalid += (v + 31) / 32;
+            }
+        }
+        const double lambda = static_cast<double>(c) * static_cast<double>(sampled) / static_cast<double>(m);
         p.cprime = static_cast<int>(std::ceil(lambda + 4.0 * std::sqrt(lambda) + 4.0));
-        if (p.G >= p.cprime + 8 || stride == 1 || p.G > 1024) break;
+        if (gvalid >= p.cprime + 8 || stride == 1 || p.G > 1024) break;
         stride /= 2;
     }
     // the threshold kernel holds at most 64 x 32 group maxima per query
-    p.pilot = (p.G >= p.cprime + 8 && p.G <= 2048) ? 1 : 0;
-    // list capacity per (query, split, column group): twice the expected hits plus slack
+    p.pilot = (gvalid >= p.cprime + 8 && p.G <= 2048) ? 1 : 0;
+    // list capacity per (query, split, column group).  The threshold is the
+    // c'-th largest of gvalid group maxima (groups of 32): a fraction
+    // pg = c'/gvalid of the groups reach it, so about f = 1 - (1 - pg)^(1/32)
+    // of all references pass, m f in all.  That count varies from query to
+    // query with the order statistic (about 1/sqrt(c') relative) and its
+    // split over the lists: 2.5 times the mean per list plus 48 keeps
+    // overflows (sent to the exact fallback) rare.
     if (p.pilot) {
-        const int64_t expect = static_cast<int64_t>(p.cprime) * stride;
-        int64_t cap = (2 * expect + kGroups * S - 1) / (kGroups * S) + 64;
+        const double pg = std::min(1.0, static_cast<double>(p.cprime) / static_cast<double>(gvalid));
+        const double f = 1.0 - std::pow(1.0 - pg, 1.0 / 32.0);
+        const double per_list = static_cast<double>(m) * f / (kGroups * S);
+        int64_t cap = static_cast<int64_t>(std::ceil(2.5 * per_list)) + 48;
+        if (cap > chunk / kGroups) cap = chunk / kGroups;
         p.cap = static_cast<int32_t>((cap + 31) / 32 * 32);
     } else {
         p.cap = static_cast<int32_t>(chunk / kGroups);
     }
-    p.smem_filter = tc_smem_bytes(p.kb, p.kbs, p.stages, false);
+    p.smem_filter = tc_smem_bytes(p.kb, p.kbs, p.stages, false, p.raw != 0);
     return p;
 }
 
