@@ -135,6 +135,14 @@ __device__ __forceinline__ void append_raw(uint64_t* list, int& cnt, int cap, fl
     ++cnt;
 }
 
+// Position of the highest set bit of x, in 0..31 (31 when x == 0: a valid
+// staging index whose result the caller discards).
+__device__ __forceinline__ uint32_t bfind31(uint32_t x) {
+    uint32_t p;
+    asm("bfind.u32 %0, %1;" : "=r"(p) : "r"(x));
+    return p & 31u;
+}
+
 // Store v to [addr] only when sel != 0 (a predicated 16-byte shared store).
 __device__ __forceinline__ void st_shared_if(uint32_t sel, uint32_t addr, uint32_t v0, uint32_t v1,
                                              uint32_t v2, uint32_t v3) {
@@ -310,6 +318,7 @@ tc_kernel(const __grid_constant__ CUtensorMap tmap_q, const __grid_constant__ CU
         const uint32_t off3b = __float_as_uint((!PILOT && active) ? 3.f * a.qscale[q] : 0.f);
         const uint32_t st_addr = smem_u32(st);
         const uint32_t all_pass = a.append_all ? 0xffffffffu : 0u;
+        const uint32_t live = active ? 0xffffffffu : 0u;
         int cnt = 0;
         for (int g = 0; g < nt; ++g) {
             const int buf = g & 1;
@@ -317,6 +326,9 @@ tc_kernel(const __grid_constant__ CUtensorMap tmap_q, const __grid_constant__ CU
             if (!__all_sync(0xffffffffu, ok)) { fail(); break; }
             tc_fence_after();
             const int64_t jt = r_begin + static_cast<int64_t>(g) * stride * kTileN + cg * kGroupCols;
+            // valid columns of this warp's 64 (fewer only in a split's last tile)
+            const int lim = static_cast<int>(min(max(r_end - jt, static_cast<int64_t>(0)),
+                                                 static_cast<int64_t>(kGroupCols)));
             // both 32-column slices into registers, then release the accumulator
             uint32_t ra[32], rb[32];
             const uint32_t col0 = lane_addr + buf * kTileN + cg * kGroupCols;
@@ -343,35 +355,49 @@ tc_kernel(const __grid_constant__ CUtensorMap tmap_q, const __grid_constant__ CU
                         for (int u = 0; u < w2; ++u) v[u] = fmaxf(v[u], v[u + w2]);
                     if (active && nvalid > 0) gout[g * gpt + cg * 2 + sl] = ord_f32(v[0]);
                 } else if (RAW) {
-                    // sign bits, bit 31-u for element u, as four independent chains
-                    uint32_t m4[4] = {0u, 0u, 0u, 0u};
+                    // sign bits, bit 31-u for element u, as two independent chains
+                    uint32_t m0 = 0u, m1 = 0u;
 #pragma unroll
-                    for (int u = 0; u < 8; ++u)
-#pragma unroll
-                        for (int h = 0; h < 4; ++h) m4[h] = __funnelshift_l(r[8 * h + u], m4[h], 1);
-                    const uint32_t sm = (m4[0] << 24) | (m4[1] << 16) | (m4[2] << 8) | m4[3];
-                    // a pass is acc >= 0: bit 31-u of `hits` is element u
-                    uint32_t hits = ~sm | all_pass;
-                    if (nvalid < 32) hits &= nvalid > 0 ? (0xffffffffu << (32 - nvalid)) : 0u;
-                    if (!active) hits = 0;
-                    if (hits) {
-                        // the values of the quarters holding a hit go to this
-                        // thread's staging words, which the loop reads back by index
-#pragma unroll
-                        for (int h = 0; h < 8; ++h)
-                            st_shared_if(hits & (0xf0000000u >> (4 * h)), st_addr + 16 * h,
-                                         r[4 * h], r[4 * h + 1], r[4 * h + 2], r[4 * h + 3]);
-                        const float b3 = __uint_as_float(off3b);
-                        const float* stf = reinterpret_cast<const float*>(st) + 31;
-                        const uint32_t jb = static_cast<uint32_t>(j0) + 31u;
-                        do {
-                            uint32_t p;
-                            asm("bfind.u32 %0, %1;" : "=r"(p) : "r"(hits));   // element 31-p
-                            hits ^= 1u << p;
-                            append_raw(list, cnt, a.cap, b3, stf[-static_cast<int>(p)], jb - p);
-                        } while (hits);
+                    for (int u = 0; u < 16; ++u) {
+                        m0 = __funnelshift_l(r[u], m0, 1);
+                        m1 = __funnelshift_l(r[16 + u], m1, 1);
                     }
-                    __syncwarp();
+                    const uint32_t sm = (m0 << 16) | m1;
+                    // a pass is acc >= 0: bit 31-u of `hits` is element u
+                    uint32_t hits = (~sm | all_pass) & live;
+                    if (lim < kGroupCols) {   // warp-uniform: the last tile of a split
+                        const int nv = min(max(lim - 32 * sl, 0), 32);
+                        hits &= nv > 0 ? (0xffffffffu << (32 - nv)) : 0u;
+                    }
+                    // the values of the quarters holding a hit go to this
+                    // thread's staging words, which the appends read back by index
+#pragma unroll
+                    for (int h = 0; h < 8; ++h)
+                        st_shared_if(hits & (0xf0000000u >> (4 * h)), st_addr + 16 * h,
+                                     r[4 * h], r[4 * h + 1], r[4 * h + 2], r[4 * h + 3]);
+                    const float b3 = __uint_as_float(off3b);
+                    const float* stf = reinterpret_cast<const float*>(st) + 31;
+                    const uint32_t jb = static_cast<uint32_t>(j0) + 31u;
+                    // two appends by every lane, predicated (most slices give
+                    // some lane two hits), their staging loads issued together;
+                    // a loop for the rare third and later
+                    {
+                        const uint32_t p0 = bfind31(hits);
+                        const uint32_t h1 = hits & ~(1u << p0);
+                        const uint32_t p1 = bfind31(h1);
+                        const float x0 = stf[-static_cast<int>(p0)];
+                        const float x1 = stf[-static_cast<int>(p1)];
+                        if (hits != 0u) append_raw(list, cnt, a.cap, b3, x0, jb - p0);
+                        if (h1 != 0u) append_raw(list, cnt, a.cap, b3, x1, jb - p1);
+                        hits = h1 & ~(1u << p1);
+                    }
+                    while (hits) {
+                        const uint32_t p = bfind31(hits);
+                        hits ^= 1u << p;
+                        append_raw(list, cnt, a.cap, b3, stf[-static_cast<int>(p)], jb - p);
+                    }
+                    // (each thread reads back only its own staging words: no
+                    // warp barrier; the next tile's vote reconverges the warp)
                 } else {
                     // sign bits, bit 31-u for element u, as four independent chains
                     uint32_t m4[4] = {0u, 0u, 0u, 0u};
