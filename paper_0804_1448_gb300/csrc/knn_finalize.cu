@@ -244,12 +244,36 @@ __device__ __forceinline__ WarpScratch carve(unsigned char* base, int P, int L, 
     return w;
 }
 
+// Two-lane float32 arithmetic (one instruction for a pair of coordinates):
+// the differences of (a0, a1) and (b0, b1), the fused square-accumulate of a
+// pair of differences, and the sum of a pair.
+__device__ __forceinline__ uint64_t f2_sub(float a0, float a1, float b0, float b1) {
+    uint64_t d;
+    asm("{\n .reg .b64 p, q;\n mov.b64 p, {%1, %2};\n mov.b64 q, {%3, %4};\n"
+        " sub.rn.f32x2 %0, p, q;\n}"
+        : "=l"(d) : "f"(a0), "f"(a1), "f"(b0), "f"(b1));
+    return d;
+}
+__device__ __forceinline__ uint64_t f2_sqacc(uint64_t diff, uint64_t acc) {
+    uint64_t r;
+    asm("fma.rn.f32x2 %0, %1, %1, %2;" : "=l"(r) : "l"(diff), "l"(acc));
+    return r;
+}
+__device__ __forceinline__ float f2_sum(uint64_t v) {
+    float lo, hi;
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(v));
+    return lo + hi;
+}
+
 // Replace raw reference indices keys[0..cnt) (kEmptyKey = none) by exact
 // float32 keys.  NV > 0 (d % 4 == 0, d <= 128, NV = ceil(d/32)): eight lanes
 // share one candidate, lane `sub` taking float4 number sub + 8v (v < NV) of
 // the row, so one warp instruction reads four rows in 128-byte segments;
 // every lane issues the loads of G candidates before using any of them, and
-// three shuffles finish each sum.  NV == 0: one lane per candidate.
+// three shuffles finish each sum.  Euclidean: the lane's coordinates go
+// through two-lane float32 instructions, as four partial sums (x, y, z, w
+// columns) added at the end; the rounding bound of the float32 distance holds
+// for any order of the additions.  NV == 0: one lane per candidate.
 template <int METRIC, int NV>
 __device__ void exact_keys(uint64_t* keys, int cnt, const float* __restrict__ R, int d,
                            const float* qrow, int lane) {
@@ -274,20 +298,41 @@ __device__ void exact_keys(uint64_t* keys, int cnt, const float* __restrict__ R,
                 }
             }
             float acc[G];
+            if constexpr (METRIC == kL2) {
+                uint64_t s01[G], s23[G];
 #pragma unroll
-            for (int u = 0; u < G; ++u) acc[u] = 0.f;
+                for (int u = 0; u < G; ++u) s01[u] = s23[u] = 0ull;
 #pragma unroll
-            for (int v = 0; v < NV; ++v) {
-                const int t = sub + 8 * v;
-                if (t < d4) {
-                    const float4 y = q4[t];
+                for (int v = 0; v < NV; ++v) {
+                    const int t = sub + 8 * v;
+                    if (t < d4) {
+                        const float4 y = q4[t];
 #pragma unroll
-                    for (int u = 0; u < G; ++u) {
-                        const float4 r = x[u][v];
-                        acc[u] = acc_f32<METRIC>(acc[u], y.x - r.x);
-                        acc[u] = acc_f32<METRIC>(acc[u], y.y - r.y);
-                        acc[u] = acc_f32<METRIC>(acc[u], y.z - r.z);
-                        acc[u] = acc_f32<METRIC>(acc[u], y.w - r.w);
+                        for (int u = 0; u < G; ++u) {
+                            const float4 r = x[u][v];
+                            s01[u] = f2_sqacc(f2_sub(y.x, y.y, r.x, r.y), s01[u]);
+                            s23[u] = f2_sqacc(f2_sub(y.z, y.w, r.z, r.w), s23[u]);
+                        }
+                    }
+                }
+#pragma unroll
+                for (int u = 0; u < G; ++u) acc[u] = f2_sum(s01[u]) + f2_sum(s23[u]);
+            } else {
+#pragma unroll
+                for (int u = 0; u < G; ++u) acc[u] = 0.f;
+#pragma unroll
+                for (int v = 0; v < NV; ++v) {
+                    const int t = sub + 8 * v;
+                    if (t < d4) {
+                        const float4 y = q4[t];
+#pragma unroll
+                        for (int u = 0; u < G; ++u) {
+                            const float4 r = x[u][v];
+                            acc[u] = acc_f32<METRIC>(acc[u], y.x - r.x);
+                            acc[u] = acc_f32<METRIC>(acc[u], y.y - r.y);
+                            acc[u] = acc_f32<METRIC>(acc[u], y.z - r.z);
+                            acc[u] = acc_f32<METRIC>(acc[u], y.w - r.w);
+                        }
                     }
                 }
             }
