@@ -13,11 +13,18 @@
 //              group of 32 references (t = 0); a per-query order statistic of
 //              these group maxima is a threshold that at least c' references
 //              (sampled ones) pass, and about c'*stride references overall;
-//   filter  -- on every tile, the sign bit of acc says whether the reference
+//   filter  -- on every tile, the sign of acc says whether the reference
 //              passes the query's threshold (acc >= 0); passing references are
-//              appended, with their acc, to the query's list.  A funnel shift
-//              per element collects the sign bits, so the common case costs one
-//              instruction per distance.
+//              appended, with their acc, to the query's list.  Half of a
+//              slice's signs are collected by funnel shifts (integer pipe), the
+//              other half by saturated multiplies packed with two-lane Horner
+//              steps (float pipe), so the common case costs about one
+//              instruction per distance, split over two pipes.  The values of
+//              the few passing ones reach the dynamically indexed append
+//              through shared memory: only 16-byte quarters holding a hit are
+//              stored (predicated).  The key is (16-bit code of acc, index);
+//              with long rows (smaller staging area) all 32 values are staged,
+//              as codes packed two to a word.
 // The lists then go to the finalize stage (knn_finalize.cu), which keeps the
 // best c by acc, re-ranks them with exact float32 differences, and checks the
 // list was neither too short nor overflowed.
@@ -102,7 +109,8 @@ __host__ __device__ constexpr size_t tc_smem_bytes(int kb, int kbs, int stages, 
            (pilot ? 0 : static_cast<size_t>(kEpi) * (raw ? kStageWordsRaw : kStageWords) * 4) + 512;
 }
 
-// Hit values are kept as a 16-bit code of acc: with B a power of two and
+// Long rows (K-block stages): hit values are kept as a 16-bit code of acc,
+// so a slice's 32 values stage in 64 bytes per thread.  With B a power of two and
 // |acc| < B, acc + 3B lies in [2B, 4B), one binade, so bits 8..23 of its
 // float32 pattern (the low exponent bit, constant there, and the top 15
 // mantissa bits) grow with acc in steps of B 2^-14.  The list key is
@@ -133,6 +141,29 @@ __device__ __forceinline__ void append_raw(uint64_t* list, int& cnt, int cap, fl
     const uint32_t hi = __byte_perm(__float_as_uint(b3 - x), 0u, 0x4421);
     if (cnt < cap) list[cnt] = (static_cast<uint64_t>(hi) << 32) | j;
     ++cnt;
+}
+
+// Float-pipe pieces of the filter's pass test: fails_f(x) = 1.0 when the
+// float32 x (given as bits) is negative and normal, else 0.0 (one saturated
+// multiply); horner4(h, a, b) = 4 h + (a, b) on a pair of floats (one
+// two-lane fused multiply-add); packed_bits(h) = the integer 2 lo + hi (at
+// most 16 bits, exact in float32) read from the mantissa of 2 lo + hi + 2^23.
+__device__ __forceinline__ float fails_f(uint32_t x) {
+    float r;
+    asm("mul.rn.ftz.sat.f32 %0, %1, 0fFE800000;" : "=f"(r) : "f"(__uint_as_float(x)));
+    return r;
+}
+__device__ __forceinline__ uint64_t horner4(uint64_t h, float a, float b) {
+    uint64_t r;
+    asm("{\n .reg .b64 ab, four;\n mov.b64 ab, {%2, %3};\n mov.b64 four, {%4, %4};\n"
+        " fma.rn.f32x2 %0, %1, four, ab;\n}"
+        : "=l"(r) : "l"(h), "f"(a), "f"(b), "f"(4.0f));
+    return r;
+}
+__device__ __forceinline__ uint32_t packed_bits(uint64_t h) {
+    float lo, hi;
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(h));
+    return __float_as_uint(fmaf(lo, 2.f, hi + 8388608.f));
 }
 
 // Position of the highest set bit of x, in 0..31 (31 when x == 0: a valid
@@ -338,37 +369,41 @@ tc_kernel(const __grid_constant__ CUtensorMap tmap_q, const __grid_constant__ CU
             tc_fence_before();
             __syncwarp();
             if (lane == 0) mbar_arrive(&t_empty[buf]);
+            if constexpr (!PILOT && RAW) {
+                // "fails" bits of both slices first (four independent chains),
+                // bit 31-u for element u.  Elements 0..15: sign bits by funnel
+                // shifts (integer pipe).  Elements 16..31 on the float pipe,
+                // which is otherwise idle here: -acc * 2^126 saturated is 1 for a
+                // negative normal acc and 0 otherwise (so -0 and negative
+                // subnormals pass too: a superset of the sign test); two-lane
+                // Horner steps times 4 pack them, and 2 lo + hi + 2^23 holds the
+                // 16 bits in its mantissa.
+                uint32_t ma = 0u, mb = 0u;
+                uint64_t ha = 0ull, hb = 0ull;
 #pragma unroll
-            for (int sl = 0; sl < 2; ++sl) {
-                const uint32_t (&r)[32] = sl ? rb : ra;
-                const int64_t j0 = jt + sl * 32;
-                const int64_t left = r_end - j0;
-                const int nvalid = left <= 0 ? 0 : (left >= 32 ? 32 : static_cast<int>(left));
-                if (PILOT) {
-                    float v[32];
+                for (int u = 0; u < 16; ++u) {
+                    ma = __funnelshift_l(ra[u], ma, 1);
+                    mb = __funnelshift_l(rb[u], mb, 1);
+                }
 #pragma unroll
-                    for (int u = 0; u < 32; ++u)
-                        v[u] = u < nvalid ? __uint_as_float(r[u]) : __int_as_float(0xff800000);
+                for (int i = 0; i < 8; ++i) {
+                    ha = horner4(ha, fails_f(ra[16 + 2 * i]), fails_f(ra[17 + 2 * i]));
+                    hb = horner4(hb, fails_f(rb[16 + 2 * i]), fails_f(rb[17 + 2 * i]));
+                }
+                // a pass is acc >= 0: bit 31-u of hits2[sl] is element u of slice sl
+                uint32_t hits2[2] = {(~__byte_perm(packed_bits(ha), ma, 0x5410) | all_pass) & live,
+                                     (~__byte_perm(packed_bits(hb), mb, 0x5410) | all_pass) & live};
+                if (lim < kGroupCols) {   // warp-uniform: the last tile of a split
 #pragma unroll
-                    for (int w2 = 16; w2 > 0; w2 >>= 1)
-#pragma unroll
-                        for (int u = 0; u < w2; ++u) v[u] = fmaxf(v[u], v[u + w2]);
-                    if (active && nvalid > 0) gout[g * gpt + cg * 2 + sl] = ord_f32(v[0]);
-                } else if (RAW) {
-                    // sign bits, bit 31-u for element u, as two independent chains
-                    uint32_t m0 = 0u, m1 = 0u;
-#pragma unroll
-                    for (int u = 0; u < 16; ++u) {
-                        m0 = __funnelshift_l(r[u], m0, 1);
-                        m1 = __funnelshift_l(r[16 + u], m1, 1);
-                    }
-                    const uint32_t sm = (m0 << 16) | m1;
-                    // a pass is acc >= 0: bit 31-u of `hits` is element u
-                    uint32_t hits = (~sm | all_pass) & live;
-                    if (lim < kGroupCols) {   // warp-uniform: the last tile of a split
+                    for (int sl = 0; sl < 2; ++sl) {
                         const int nv = min(max(lim - 32 * sl, 0), 32);
-                        hits &= nv > 0 ? (0xffffffffu << (32 - nv)) : 0u;
+                        hits2[sl] &= nv > 0 ? (0xffffffffu << (32 - nv)) : 0u;
                     }
+                }
+#pragma unroll
+                for (int sl = 0; sl < 2; ++sl) {
+                    const uint32_t (&r)[32] = sl ? rb : ra;
+                    uint32_t hits = hits2[sl];
                     // the values of the quarters holding a hit go to this
                     // thread's staging words, which the appends read back by index
 #pragma unroll
@@ -377,7 +412,7 @@ tc_kernel(const __grid_constant__ CUtensorMap tmap_q, const __grid_constant__ CU
                                      r[4 * h], r[4 * h + 1], r[4 * h + 2], r[4 * h + 3]);
                     const float b3 = __uint_as_float(off3b);
                     const float* stf = reinterpret_cast<const float*>(st) + 31;
-                    const uint32_t jb = static_cast<uint32_t>(j0) + 31u;
+                    const uint32_t jb = static_cast<uint32_t>(jt) + 32u * sl + 31u;
                     // two appends by every lane, predicated (most slices give
                     // some lane two hits), their staging loads issued together;
                     // a loop for the rare third and later
@@ -398,37 +433,56 @@ tc_kernel(const __grid_constant__ CUtensorMap tmap_q, const __grid_constant__ CU
                     }
                     // (each thread reads back only its own staging words: no
                     // warp barrier; the next tile's vote reconverges the warp)
-                } else {
-                    // sign bits, bit 31-u for element u, as four independent chains
-                    uint32_t m4[4] = {0u, 0u, 0u, 0u};
+                }
+            } else {
 #pragma unroll
-                    for (int u = 0; u < 8; ++u)
+                for (int sl = 0; sl < 2; ++sl) {
+                    const uint32_t (&r)[32] = sl ? rb : ra;
+                    const int64_t j0 = jt + sl * 32;
+                    const int64_t left = r_end - j0;
+                    const int nvalid = left <= 0 ? 0 : (left >= 32 ? 32 : static_cast<int>(left));
+                    if (PILOT) {
+                        float v[32];
 #pragma unroll
-                        for (int h = 0; h < 4; ++h) m4[h] = __funnelshift_l(r[8 * h + u], m4[h], 1);
-                    const uint32_t sm = (m4[0] << 24) | (m4[1] << 16) | (m4[2] << 8) | m4[3];
-                    // a pass is acc >= 0; bit u of `hits` is element u after the reversal
-                    uint32_t hits = __brev(a.append_all ? 0xffffffffu : ~sm);
-                    hits &= nvalid >= 32 ? 0xffffffffu : ((1u << nvalid) - 1u);
-                    if (!active) hits = 0;
-                    // the append loop reads the hit values with a dynamic index, which
-                    // registers do not allow: their upper halves go through shared memory
-                    if (hits) {
+                        for (int u = 0; u < 32; ++u)
+                            v[u] = u < nvalid ? __uint_as_float(r[u]) : __int_as_float(0xff800000);
 #pragma unroll
-                        for (int h = 0; h < 4; ++h)
-                            reinterpret_cast<uint4*>(st)[h] = make_uint4(
-                                hit_code2(r[8 * h + 0], r[8 * h + 1], off3b),
-                                hit_code2(r[8 * h + 2], r[8 * h + 3], off3b),
-                                hit_code2(r[8 * h + 4], r[8 * h + 5], off3b),
-                                hit_code2(r[8 * h + 6], r[8 * h + 7], off3b));
-                        const uint32_t jb = static_cast<uint32_t>(j0);
-                        const uint16_t* st16 = reinterpret_cast<const uint16_t*>(st);
-                        do {
-                            const int u = __ffs(hits) - 1;
-                            hits &= hits - 1;
-                            append(list, cnt, a.cap, st16[u], jb + u);
-                        } while (hits);
+                        for (int w2 = 16; w2 > 0; w2 >>= 1)
+#pragma unroll
+                            for (int u = 0; u < w2; ++u) v[u] = fmaxf(v[u], v[u + w2]);
+                        if (active && nvalid > 0) gout[g * gpt + cg * 2 + sl] = ord_f32(v[0]);
+                    } else {
+                        // sign bits, bit 31-u for element u, as four independent chains
+                        uint32_t m4[4] = {0u, 0u, 0u, 0u};
+#pragma unroll
+                        for (int u = 0; u < 8; ++u)
+#pragma unroll
+                            for (int h = 0; h < 4; ++h) m4[h] = __funnelshift_l(r[8 * h + u], m4[h], 1);
+                        const uint32_t sm = (m4[0] << 24) | (m4[1] << 16) | (m4[2] << 8) | m4[3];
+                        // a pass is acc >= 0; bit u of `hits` is element u after the reversal
+                        uint32_t hits = __brev(a.append_all ? 0xffffffffu : ~sm);
+                        hits &= nvalid >= 32 ? 0xffffffffu : ((1u << nvalid) - 1u);
+                        if (!active) hits = 0;
+                        // the append loop reads the hit values with a dynamic index, which
+                        // registers do not allow: their upper halves go through shared memory
+                        if (hits) {
+#pragma unroll
+                            for (int h = 0; h < 4; ++h)
+                                reinterpret_cast<uint4*>(st)[h] = make_uint4(
+                                    hit_code2(r[8 * h + 0], r[8 * h + 1], off3b),
+                                    hit_code2(r[8 * h + 2], r[8 * h + 3], off3b),
+                                    hit_code2(r[8 * h + 4], r[8 * h + 5], off3b),
+                                    hit_code2(r[8 * h + 6], r[8 * h + 7], off3b));
+                            const uint32_t jb = static_cast<uint32_t>(j0);
+                            const uint16_t* st16 = reinterpret_cast<const uint16_t*>(st);
+                            do {
+                                const int u = __ffs(hits) - 1;
+                                hits &= hits - 1;
+                                append(list, cnt, a.cap, st16[u], jb + u);
+                            } while (hits);
+                        }
+                        __syncwarp();
                     }
-                    __syncwarp();
                 }
             }
         }
