@@ -788,16 +788,17 @@ TcPlan tc_plan(int64_t n, int64_t m, int32_t d, int32_t kp, int prec, int32_t c,
     int stride = 4096 / kTileN;
     while (tiles_total * gpt / stride > 1024) stride *= 2;
     const int tps = static_cast<int>(chunk / kTileN);
-    // c' = lambda + 4 sqrt(lambda) + 4: with N references above the threshold
-    // the sampled count is Binomial(N, 1/stride); N < c with c' sampled passing
-    // has probability below 2e-6 per query at lambda = 5 (the bench shape), and
-    // such a query is finished by the exact fallback.  The c'-th largest of G
+    // c' = lambda + 4 sqrt(lambda) + 4, lambda = the expected number of
+    // sampled references among the c best (c times the sampled fraction: each
+    // split samples its tiles 0, stride, 2 stride, ..., so a short split
+    // samples a larger share).  At least c' sampled references pass the
+    // threshold; were fewer than c to pass overall, all would be among the c
+    // best, so at least c' of the c best were sampled: a Poisson(lambda) tail,
+    // about 4e-6 per query at lambda = 5.3, c' = 19 (n = m = 38400, k = 20).
+    // Such a query is finished by the exact fallback.  The c'-th largest of G
     // group maxima needs G comfortably above c': sample denser (halve the
     // stride) until G >= c' + 8, and run no pilot (every reference appended)
     // only when even every tile does not give that many groups.
-    // lambda counts the sampled references among the c best: c times the
-    // sampled fraction of the tiles (each split samples its tiles 0, stride,
-    // 2 stride, ...; a short split samples a larger share of its tiles).
     // The group slots of a short split's missing tiles, and groups past the
     // end of the data, hold no maximum: gvalid counts the real groups.
     int64_t gvalid = 0;
