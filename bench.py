@@ -62,6 +62,8 @@ def parse_args():
     p.add_argument("--no-batch", action="store_true")
     p.add_argument("--sweep", action="store_true",
                    help="Table 1 grid (N x D, k = 20) instead of the bench line")
+    p.add_argument("--configs", action="store_true",
+                   help="timings of the other forms and shapes (configs 1-3) instead of the bench line")
     p.add_argument("--serve-requests", type=int, default=48)
     return p.parse_args()
 
@@ -311,6 +313,83 @@ TABLE1_BF_CUDA = {
 }
 
 
+def configs(args):
+    """Timings of the forms and shapes beside the bench line, one JSON line:
+    config 1 (n = m = 1200, d = 8, k = 20: float32 CUDA-core and bf16 forms,
+    and the oracle on the host cores over all 1200 queries), config 2
+    (n = m = 38400, d = 96, k = 20: float32 Euclidean and Manhattan, bf16 and
+    tf32) and config 3 (m = 2^20, n = 16384, d = 128, k = 100, Gaussian
+    mixture: float32, bf16 and tf32, 400 re-rank candidates).  Device times
+    with inputs resident (CUDA events, median of `reps`), L2 flushed before
+    each.  Accuracy against the oracle is the tests' job (tests/test_gpu_tc.py,
+    tests/test_gpu_mixture.py)."""
+    import numpy as np
+    import torch
+    from paper_0804_1448_gb300 import inputs, knn
+    dev = torch.device("cuda", 0)
+    stream = torch.cuda.current_stream(dev)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    peaks, _ = load_peaks()
+
+    def timed(R, Q, k, precision, metric, reps):
+        ix = knn.Index(0, precision, rerank_factor=4)
+        ix.set_reference(R)
+        dist = torch.empty((Q.shape[0], k), device=dev)
+        idx = torch.empty((Q.shape[0], k), dtype=torch.int32, device=dev)
+        ix.search_into(Q, k, dist, idx, metric, stream)
+        ix.set_profiling(True)
+        times, prof = [], []
+        for _ in range(reps):
+            flush.zero_()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            ix.search_into(Q, k, dist, idx, metric, stream)
+            e1.record(stream)
+            torch.cuda.synchronize(dev)
+            times.append(e0.elapsed_time(e1))
+            prof.append(ix.profile())
+        st = ix.stats()
+        ix.close()
+        ms = float(np.median(times))
+        out = {"ms": ms, "queries_per_s": Q.shape[0] / (ms / 1e3),
+               "fallback_queries": st["fallback_queries"]}
+        filt = [pp.get("tc_filter") for pp in prof if pp.get("tc_filter")]
+        if filt:
+            fms = float(np.median(filt))
+            tfl = 2.0 * Q.shape[0] * R.shape[0] * R.shape[1] / (fms / 1e3) / 1e12
+            pk = peaks["bf16_tflops"] * (0.5 if precision == "tf32" else 1.0)
+            out.update({"filter_ms": fms, "filter_tflops": tfl, "filter_frac": tfl / pk})
+        return out
+
+    res = {}
+    import oracle
+    R, Q, k = inputs.workload("uniform_n1200_d8_k20")
+    Rd, Qd = torch.from_numpy(R).to(dev), torch.from_numpy(Q).to(dev)
+    t0 = time.perf_counter()
+    oracle.knn(R, Q, k, "l2")
+    dt = time.perf_counter() - t0
+    res["uniform_n1200_d8_k20"] = {
+        "fp32_l2": timed(Rd, Qd, k, "fp32", "l2", 20), "bf16_l2": timed(Rd, Qd, k, "bf16", "l2", 20),
+        "cpu_baseline": {"value": Q.shape[0] / dt, "unit": "queries/s", "cores": oracle.max_threads(),
+                         "kind": "oracle", "sample": f"all {Q.shape[0]} queries ({dt:.2f} s)"}}
+    R, Q, k = inputs.workload(WORKLOAD)
+    Rd, Qd = torch.from_numpy(R).to(dev), torch.from_numpy(Q).to(dev)
+    res[WORKLOAD] = {"fp32_l2": timed(Rd, Qd, k, "fp32", "l2", 5),
+                     "fp32_l1": timed(Rd, Qd, k, "fp32", "l1", 5),
+                     "bf16_l2": timed(Rd, Qd, k, "bf16", "l2", 10),
+                     "tf32_l2": timed(Rd, Qd, k, "tf32", "l2", 10)}
+    name = "mixture_m1048576_n16384_d128_k100"
+    R, Q, k = inputs.workload(name)
+    Rd, Qd = torch.from_numpy(R).to(dev), torch.from_numpy(Q).to(dev)
+    del R, Q
+    res[name] = {"fp32_l2": timed(Rd, Qd, k, "fp32", "l2", 3),
+                 "bf16_l2": timed(Rd, Qd, k, "bf16", "l2", 5),
+                 "tf32_l2": timed(Rd, Qd, k, "tf32", "l2", 5)}
+    print(json.dumps({"configs": res, "peaks": {"bf16_tflops": peaks["bf16_tflops"],
+                                                "tf32": "half the bf16 peak (nominal ratio)"}}),
+          flush=True)
+
+
 def sweep(args):
     """The Table 1 grid: N = n = m in TABLE1_N, D in {8, 16, 32, 64, 80, 96},
     k = 20, uniform [0,1) points, Euclidean.  Per point: the bf16 and float32
@@ -370,6 +449,9 @@ def main():
     args = parse_args()
     if args.impl == "reference":
         run_reference(args)
+        return
+    if args.configs:
+        configs(args)
         return
     if args.sweep:
         sweep(args)

@@ -198,7 +198,9 @@ __device__ __forceinline__ void issue_kblock(uint32_t d_tmem, uint64_t a_desc, u
 
 // KBT > 0: whole-tile stages of exactly KBT K blocks (compile-time, unrolled);
 // KBT == 0: any K-block count, whole-tile or single-K-block stages.
-template <int PREC, bool PILOT, int KBT, bool RAW>
+// EPI (filter epilogue): 0 = 16-bit codes staged (long rows), 1 = raw values
+// staged by quarters holding a hit, 2 = raw, every reference appended (no pilot).
+template <int PREC, bool PILOT, int KBT, int EPI>
 __global__ void __launch_bounds__(kThreads, 1)
 tc_kernel(const __grid_constant__ CUtensorMap tmap_q, const __grid_constant__ CUtensorMap tmap_r,
           TcArgs a) {
@@ -213,6 +215,7 @@ tc_kernel(const __grid_constant__ CUtensorMap tmap_q, const __grid_constant__ CU
     unsigned char* sA = smem;
     unsigned char* sB = sA + static_cast<size_t>(KB) * kQTileBytes;
     uint32_t* stage = reinterpret_cast<uint32_t*>(sB + NST * stage_bytes);
+    constexpr bool RAW = EPI != 0;
     constexpr int kSW = RAW ? kStageWordsRaw : kStageWords;
     uint64_t* bars = reinterpret_cast<uint64_t*>(stage + (PILOT ? 0 : kEpi * kSW));
     uint64_t* full = bars;
@@ -370,6 +373,35 @@ tc_kernel(const __grid_constant__ CUtensorMap tmap_q, const __grid_constant__ CU
             __syncwarp();
             if (lane == 0) mbar_arrive(&t_empty[buf]);
             if constexpr (!PILOT && RAW) {
+              if constexpr (EPI == 2) {
+                // no pilot (too few references for one): every valid reference
+                // is appended in column order, two keys per 16-byte store.  A
+                // list holds exactly its column group's chunk / 4 columns, and
+                // every slice before the last starts at a multiple of 32 keys,
+                // so the stores stay inside it and 16-byte aligned.
+                if (active) {
+                    const float b3 = __uint_as_float(off3b);
+#pragma unroll
+                    for (int sl = 0; sl < 2; ++sl) {
+                        const uint32_t (&r)[32] = sl ? rb : ra;
+                        const int nv = min(max(lim - 32 * sl, 0), 32);
+                        const uint32_t j0 = static_cast<uint32_t>(jt) + 32u * sl;
+                        uint4* dst = reinterpret_cast<uint4*>(list + cnt);
+#pragma unroll
+                        for (int u = 0; u < 32; u += 2) {
+                            if (u < nv) {
+                                const uint32_t c0 = __byte_perm(
+                                    __float_as_uint(b3 - __uint_as_float(r[u])), 0u, 0x4421);
+                                const uint32_t c1 = __byte_perm(
+                                    __float_as_uint(b3 - __uint_as_float(r[u + 1])), 0u, 0x4421);
+                                if (u + 1 < nv) dst[u / 2] = make_uint4(j0 + u, c0, j0 + u + 1, c1);
+                                else list[cnt + u] = (static_cast<uint64_t>(c0) << 32) | (j0 + u);
+                            }
+                        }
+                        cnt += nv;
+                    }
+                }
+              } else {
                 // "fails" bits of both slices first (four independent chains),
                 // bit 31-u for element u.  Elements 0..15: sign bits by funnel
                 // shifts (integer pipe).  Elements 16..31 on the float pipe,
@@ -434,6 +466,7 @@ tc_kernel(const __grid_constant__ CUtensorMap tmap_q, const __grid_constant__ CU
                     // (each thread reads back only its own staging words: no
                     // warp barrier; the next tile's vote reconverges the warp)
                 }
+              }
             } else {
 #pragma unroll
                 for (int sl = 0; sl < 2; ++sl) {
@@ -669,11 +702,11 @@ bool make_map(CUtensorMap* map, const void* base, int64_t rows, int kp, int prec
 }
 
 
-template <int PREC, bool PILOT, int KBT, bool RAW = false>
+template <int PREC, bool PILOT, int KBT, int EPI = 0>
 cudaError_t launch_kernel(const TcPlan& p, const CUtensorMap& mq, const CUtensorMap& mr,
                           const TcArgs& a, cudaStream_t st) {
-    auto kern = tc_kernel<PREC, PILOT, KBT, RAW>;
-    const size_t smem = tc_smem_bytes(p.kb, p.kbs, p.stages, PILOT, RAW);
+    auto kern = tc_kernel<PREC, PILOT, KBT, EPI>;
+    const size_t smem = tc_smem_bytes(p.kb, p.kbs, p.stages, PILOT, EPI != 0);
     cudaError_t err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                            static_cast<int>(smem));
     if (err != cudaSuccess) return err;
@@ -687,10 +720,17 @@ cudaError_t dispatch_kb(const TcPlan& p, const CUtensorMap& mq, const CUtensorMa
                         const TcArgs& a, cudaStream_t st) {
     if (p.kbs == p.kb) {   // whole-tile stages: unrolled issue for the common row lengths
         if constexpr (!PILOT) {
-            if (p.raw) {
+            if (p.raw && p.pilot) {
                 switch (p.kb) {
-                    case 1: return launch_kernel<PREC, false, 1, true>(p, mq, mr, a, st);
-                    case 2: return launch_kernel<PREC, false, 2, true>(p, mq, mr, a, st);
+                    case 1: return launch_kernel<PREC, false, 1, 1>(p, mq, mr, a, st);
+                    case 2: return launch_kernel<PREC, false, 2, 1>(p, mq, mr, a, st);
+                    default: break;
+                }
+            }
+            if (p.raw) {   // every reference appended
+                switch (p.kb) {
+                    case 1: return launch_kernel<PREC, false, 1, 2>(p, mq, mr, a, st);
+                    case 2: return launch_kernel<PREC, false, 2, 2>(p, mq, mr, a, st);
                     default: break;
                 }
             }
@@ -700,6 +740,10 @@ cudaError_t dispatch_kb(const TcPlan& p, const CUtensorMap& mq, const CUtensorMa
             case 2: return launch_kernel<PREC, PILOT, 2>(p, mq, mr, a, st);
             default: break;
         }
+    }
+    if constexpr (!PILOT) {
+        if (p.raw && p.pilot) return launch_kernel<PREC, false, 0, 1>(p, mq, mr, a, st);
+        if (p.raw) return launch_kernel<PREC, false, 0, 2>(p, mq, mr, a, st);   // every reference
     }
     return launch_kernel<PREC, PILOT, 0>(p, mq, mr, a, st);
 }
@@ -756,11 +800,20 @@ TcPlan tc_plan(int64_t n, int64_t m, int32_t d, int32_t kp, int prec, int32_t c,
             p.stages = s;
             p.raw = (p.kb <= 2 && tc_smem_bytes(p.kb, p.kb, s, false, true) <= kSmemLimit) ? 1 : 0;
         }
-    for (int s = kMaxStages; s >= 2 && p.stages == 0; --s)
-        if (tc_smem_bytes(p.kb, 1, s, false) <= kSmemLimit) {
+    if (p.stages == 0) {
+        // one K block per stage; raw hit staging when it leaves at least three
+        // stages (or as many as the codes would)
+        int s_codes = 0, s_raw = 0;
+        for (int s = kMaxStages; s >= 2 && s_codes == 0; --s)
+            if (tc_smem_bytes(p.kb, 1, s, false) <= kSmemLimit) s_codes = s;
+        for (int s = kMaxStages; s >= 2 && s_raw == 0; --s)
+            if (tc_smem_bytes(p.kb, 1, s, false, true) <= kSmemLimit) s_raw = s;
+        if (s_codes > 0) {
             p.kbs = 1;
-            p.stages = s;
+            p.raw = (s_raw >= 3 || (s_raw > 0 && s_raw == s_codes)) ? 1 : 0;
+            p.stages = p.raw ? s_raw : s_codes;
         }
+    }
     if (p.stages == 0) return p;   // operand rows too long for shared memory
     const int64_t qtiles = (n + kBlockM - 1) / kBlockM;
     // reference splits: the fewest whose CTAs fill at least 85% of the last wave
