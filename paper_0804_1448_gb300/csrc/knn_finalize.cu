@@ -33,6 +33,7 @@ namespace {
 
 constexpr int kMaxPool = 4096;
 constexpr int kRegPool = 128;            // pools up to 4 x 32 keys: prefix selection in registers
+constexpr int kSortedStripe = 48;        // larger pools up to 48 x 32 keys: per-lane sorted stripes
 constexpr int kRegHits = 16;             // hit-list entries per lane held in registers
 constexpr int kStage = 32 * kRegHits;    // hit lists up to this length are staged in shared memory
 constexpr int kBins = 64;
@@ -723,6 +724,35 @@ finalize_kernel(FinalizeArgs a, int P, int warps_per_block) {
             if (kr[0] == win) {
                 w.sorted[L] = win;
                 kr[0] = kr[1]; kr[1] = kr[2]; kr[2] = kr[3]; kr[3] = kEmptyKey;
+            }
+            prev = win;
+            ++L;
+        }
+    } else if (pool <= 32 * kSortedStripe) {
+        // each lane sorts its stripe keys[lane + 32 j] in place (insertion
+        // sort, at most kSortedStripe keys); then the owner of each warp
+        // minimum just steps to the next key of its stripe
+        const int nl = (pool - lane + 31) / 32;
+        for (int j = 1; j < nl; ++j) {
+            const uint64_t x = w.keys[lane + 32 * j];
+            int i = j - 1;
+            while (i >= 0 && w.keys[lane + 32 * i] > x) {
+                w.keys[lane + 32 * (i + 1)] = w.keys[lane + 32 * i];
+                --i;
+            }
+            w.keys[lane + 32 * (i + 1)] = x;
+        }
+        int pos = 0;
+        uint64_t lmin = nl > 0 ? w.keys[lane] : kEmptyKey;
+        while (true) {
+            const uint64_t win = warp_min_key(lmin);
+            if (win == kEmptyKey) break;
+            if (L >= k && !near_tie(key_dist(prev), key_dist(win), relf)) break;
+            if (L == Lcap) { truncated = true; break; }
+            if (lmin == win) {
+                w.sorted[L] = win;
+                ++pos;
+                lmin = pos < nl ? w.keys[lane + 32 * pos] : kEmptyKey;
             }
             prev = win;
             ++L;
