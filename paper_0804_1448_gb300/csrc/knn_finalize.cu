@@ -495,15 +495,21 @@ __device__ __forceinline__ void hit_totals(const FinalizeArgs& a, int64_t q, int
 // -3 (the cut kept more than P) to send the query to the exact fallback.
 // Lists of up to kStage entries are copied once into shared memory (8-byte
 // asynchronous copies, all in flight together) and their keys held in
-// registers; longer ones are re-read from global memory at every pass.
-template <int METRIC, int NV, bool STAGED>
+// registers (MODE 1).  Lists that fit the warp's whole key and staging area
+// (keys[P] and the staging words are adjacent) are copied there and every
+// pass reads shared memory; the kept indices are compacted in place, each
+// written at or before the position it was read from (MODE 2).  Longer ones
+// are re-read from global memory at every pass (MODE 0).
+template <int METRIC, int NV, int MODE>
 __device__ int gather_hits_impl(const FinalizeArgs& a, int64_t q, int P, WarpScratch& w, int lane,
                                 int total) {
+    constexpr bool STAGED = MODE != 0;
     const HitLists& hl = a.hits;
     const int S = hl.S, cap = hl.cap, c = hl.c;
     const uint64_t* base = hl.keys + q * static_cast<int64_t>(S) * cap;
     const int32_t* cnts = hl.counts + q * static_cast<int64_t>(S);
-    uint32_t hv[STAGED ? kRegHits : 1];   // high words of the staged keys (order of the score)
+    uint32_t hv[MODE == 1 ? kRegHits : 1];   // high words of the staged keys (order of the score)
+    uint64_t* const dst = MODE == 2 ? w.keys : w.stage;
     if constexpr (STAGED) {
         int o = 0;
         for (int s0 = 0; s0 < S; s0 += 32) {
@@ -518,25 +524,29 @@ __device__ int gather_hits_impl(const FinalizeArgs& a, int64_t q, int P, WarpScr
                 const int cs = __shfl_sync(0xffffffffu, mine, s);
                 const int os = o + __shfl_sync(0xffffffffu, incl, s) - cs;
                 const uint64_t* sp = base + static_cast<int64_t>(s0 + s) * cap;
-                for (int x = lane; x < cs; x += 32) cp_async8(w.stage + os + x, sp + x);
+                for (int x = lane; x < cs; x += 32) cp_async8(dst + os + x, sp + x);
             }
             o += __shfl_sync(0xffffffffu, incl, 31);
         }
         cp_async_wait_all();
         __syncwarp();
+        if constexpr (MODE == 1) {
 #pragma unroll
-        for (int i = 0; i < kRegHits; ++i) {
-            const int e = i * 32 + lane;
-            hv[i] = (e < total) ? static_cast<uint32_t>(w.stage[e] >> 32) : 0u;
+            for (int i = 0; i < kRegHits; ++i) {
+                const int e = i * 32 + lane;
+                hv[i] = (e < total) ? static_cast<uint32_t>(w.stage[e] >> 32) : 0u;
+            }
         }
     }
     float vmin = __int_as_float(0x7f800000), vmax = -vmin;
     // visit every entry: f(score) for the staged registers, or f(key) re-read
     auto for_each = [&](auto&& f) {
-        if constexpr (STAGED) {
+        if constexpr (MODE == 1) {
 #pragma unroll
             for (int i = 0; i < kRegHits; ++i)
                 if (i * 32 + lane < total) f(hit_val(hv[i]));
+        } else if constexpr (MODE == 2) {
+            for (int e = lane; e < total; e += 32) f(hit_val(static_cast<uint32_t>(w.keys[e] >> 32)));
         } else {
             for (int s = 0; s < S; ++s) {
                 const int cs = min(cnts[s], cap);
@@ -585,7 +595,20 @@ __device__ int gather_hits_impl(const FinalizeArgs& a, int64_t q, int P, WarpScr
         return bb < cut1 || (bb == cut1 && (b2.inv == 0.f || b2.bin(v) <= cut2));
     };
     int kept = 0;
-    if constexpr (STAGED) {
+    if constexpr (MODE == 2) {
+        // in place: every lane reads its entry before any lane writes, and a
+        // kept entry goes to a position at or before the one it came from
+        for (int e0 = 0; e0 < total; e0 += 32) {
+            const int e = e0 + lane;
+            const uint64_t key = e < total ? w.keys[e] : 0ull;
+            const bool take = e < total && keep(hit_val(static_cast<uint32_t>(key >> 32)));
+            const unsigned bal = __ballot_sync(0xffffffffu, take);
+            __syncwarp();
+            const int pos = kept + __popc(bal & ((1u << lane) - 1u));
+            if (take && pos < P) w.keys[pos] = static_cast<uint32_t>(key);
+            kept += __popc(bal);
+        }
+    } else if constexpr (MODE == 1) {
         // compact the kept reference indices into w.keys in entry order (ballots)
 #pragma unroll
         for (int i = 0; i < kRegHits; ++i) {
@@ -666,6 +689,10 @@ finalize_kernel(FinalizeArgs a, int P, int warps_per_block) {
     const bool staged = a.use_hits != 0;
     WarpScratch w = carve(smem_raw + warp_scratch_bytes(P, Lcap, S, d, staged) * warp, P, Lcap, S,
                           staged);
+    // entries that fit keys[P] and the staging area behind it (contiguous)
+    const size_t union_bytes = prefix_bytes(Lcap) > (staged ? static_cast<size_t>(kStage) * 8 : 0)
+                                   ? prefix_bytes(Lcap) : static_cast<size_t>(kStage) * 8;
+    const int stage_all = static_cast<int>((align16(static_cast<size_t>(P) * 8) + union_bytes) / 8);
     // the query row: its loads are issued before the hit-list sizes are read
     const float* qg = a.Q + q * d;
     float4 qv = make_float4(0.f, 0.f, 0.f, 0.f);
@@ -689,8 +716,9 @@ finalize_kernel(FinalizeArgs a, int P, int warps_per_block) {
     } else {
         if (over) pool = -2;
         else if (total < a.hits.c && total < a.m) pool = -1;
-        else if (total <= kStage) pool = gather_hits_impl<METRIC, NV, true>(a, q, P, w, lane, total);
-        else pool = gather_hits_impl<METRIC, NV, false>(a, q, P, w, lane, total);
+        else if (total <= kStage) pool = gather_hits_impl<METRIC, NV, 1>(a, q, P, w, lane, total);
+        else if (total <= stage_all) pool = gather_hits_impl<METRIC, NV, 2>(a, q, P, w, lane, total);
+        else pool = gather_hits_impl<METRIC, NV, 0>(a, q, P, w, lane, total);
         if (pool < 0) {
             if (lane == 0) queue_fallback(a, q, -pool - 1);
             return;
