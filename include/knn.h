@@ -40,11 +40,14 @@ typedef struct knn_ctx* knn_handle; /* opaque; owned by the library */
 
 /*
  * Distances: the two Sec. 2.1 names ("the Euclidean or the Manhattan
- * distance"), and the Chebyshev (L-infinity) distance max_t |q_t - r_t|,
- * another norm-induced distance of the same problem statement.  Manhattan and
- * Chebyshev searches run in KNN_FP32 whatever the handle's precision.
+ * distance"), and two more the same passage admits: the Chebyshev
+ * (L-infinity) distance max_t |q_t - r_t|, and the Mahalanobis distance
+ * sqrt((q - r)^T S^-1 (q - r)) for the inverse covariance S^-1 given with
+ * knn_set_mahalanobis.  Manhattan and Chebyshev searches run in KNN_FP32
+ * whatever the handle's precision; a Mahalanobis search is a Euclidean search
+ * of whitened points (below) in the handle's precision.
  */
-typedef enum { KNN_L2 = 0, KNN_L1 = 1, KNN_LINF = 2 } knn_metric;
+typedef enum { KNN_L2 = 0, KNN_L1 = 1, KNN_LINF = 2, KNN_MAHALANOBIS = 3 } knn_metric;
 
 /*
  * Arithmetic of the distance stage.
@@ -122,8 +125,9 @@ knn_status knn_set_reference(knn_handle h, const float* R, int64_t m, int32_t d,
  * cuda_stream: a cudaStream_t, or NULL for the handle's own stream.
  * n = 0 is a no-op returning KNN_OK.
  * Errors: KNN_ERR_INVALID (null pointer with n > 0, n < 0, k < 1, k > m,
- * d != the reference dimension, bad metric), KNN_ERR_UNSUPPORTED
- * (k > KNN_K_MAX), KNN_ERR_NOREF, KNN_ERR_OOM, KNN_ERR_CUDA.
+ * d != the reference dimension, bad metric, KNN_MAHALANOBIS without a
+ * matrix of dimension d), KNN_ERR_UNSUPPORTED (k > KNN_K_MAX), KNN_ERR_NOREF,
+ * KNN_ERR_OOM, KNN_ERR_CUDA.
  */
 knn_status knn_search(knn_handle h, const float* Q, int64_t n, int32_t d, int32_t k,
                       knn_metric metric, float* dist_out, int32_t* idx_out,
@@ -143,6 +147,25 @@ knn_status knn_sync(knn_handle h);
  * Errors: KNN_ERR_INVALID, KNN_ERR_OOM, KNN_ERR_CUDA.
  */
 knn_status knn_set_precision(knn_handle h, int32_t precision);
+
+/*
+ * The matrix of the Mahalanobis distance (KNN_MAHALANOBIS, Sec. 2.1):
+ * S_inv is a HOST pointer to a d x d symmetric positive definite matrix, the
+ * inverse covariance, row-major double (the lower triangle is read).  The
+ * library factors it once, S_inv = L L^T (Cholesky, in double on the host),
+ * keeps L on the device in float32, and answers KNN_MAHALANOBIS searches as
+ * Euclidean searches of whitened points x' = L^T x: the reference set is
+ * whitened on the first such search after knn_set_reference or this call (a
+ * second float32 copy, m x d, owned by this handle), the queries on every
+ * search.  Each whitened coordinate is computed with a compensated dot
+ * product and rounded once, so returned distances are those of the exact
+ * quadratic form to within float32 rounding of the whitened coordinates.
+ * S_inv = NULL forgets the matrix.  KNN_MAHALANOBIS is not available to
+ * knn_search_batch, knn_search_self or knn_search_static.  Synchronous.
+ * Errors: KNN_ERR_INVALID (d < 1, S_inv not positive definite or not finite),
+ * KNN_ERR_UNSUPPORTED (d above 224), KNN_ERR_OOM, KNN_ERR_CUDA.
+ */
+knn_status knn_set_mahalanobis(knn_handle h, const double* S_inv, int32_t d);
 
 /* Counters since knn_create (reading them synchronises the handle's work). */
 typedef struct {
@@ -185,8 +208,8 @@ knn_status knn_get_profile(knn_handle h, float* ms, const char** names, int32_t 
  * itself for k + 1 neighbours and a device pass that drops each row's own
  * index (or, when more than k equal points precede it, the last entry).
  * Errors: KNN_ERR_INVALID (null pointer, k < 1, k + 1 > m, bad metric),
- * KNN_ERR_NOREF, KNN_ERR_UNSUPPORTED (k + 1 > KNN_K_MAX), KNN_ERR_OOM,
- * KNN_ERR_CUDA.
+ * KNN_ERR_NOREF, KNN_ERR_UNSUPPORTED (k + 1 > KNN_K_MAX, KNN_MAHALANOBIS),
+ * KNN_ERR_OOM, KNN_ERR_CUDA.
  */
 knn_status knn_search_self(knn_handle h, int32_t k, knn_metric metric, float* dist_out,
                            int32_t* idx_out, void* cuda_stream);

@@ -59,6 +59,8 @@ def _lib(mutant: int = 0) -> ctypes.CDLL:
         lib.oracle_knn_subset.restype = ctypes.c_int
         lib.oracle_key_pairs.argtypes = [p, i64, p, i64, i32, i32, p, p, i64, p]
         lib.oracle_key_pairs.restype = ctypes.c_int
+        lib.oracle_knn_mahalanobis.argtypes = [p, i64, p, i64, i32, p, i32, p, p, i32]
+        lib.oracle_knn_mahalanobis.restype = ctypes.c_int
         lib.oracle_max_threads.restype = ctypes.c_int
         _LIBS[mutant] = lib
         return lib
@@ -125,3 +127,22 @@ def key_pairs(R, Q, qi, rj, metric: str = "l2"):
     if rc != 0:
         raise ValueError(f"oracle_key_pairs failed with code {rc}")
     return out
+
+
+def knn_mahalanobis(R, Q, M, k: int, nthreads: int = 0, mutant: int = 0):
+    """k nearest neighbours under the Mahalanobis distance sqrt(delta^T M delta)
+    (M: d x d symmetric positive definite, the inverse covariance).  Returns
+    (dist float64 [n,k], idx int32 [n,k]), ascending by (distance, index)."""
+    R, Q = _f32(R), _f32(Q)
+    m, d = R.shape
+    n = Q.shape[0]
+    M = np.ascontiguousarray(M, dtype=np.float64)
+    if Q.shape[1] != d or M.shape != (d, d):
+        raise ValueError("R, Q and M differ in dimension")
+    dist = np.empty((n, k), dtype=np.float64)
+    idx = np.empty((n, k), dtype=np.int32)
+    rc = _lib(mutant).oracle_knn_mahalanobis(_ptr(R), m, _ptr(Q), n, d, _ptr(M), k,
+                                             _ptr(dist), _ptr(idx), nthreads)
+    if rc != 0:
+        raise ValueError(f"oracle_knn_mahalanobis failed with code {rc}")
+    return dist, idx

@@ -27,6 +27,11 @@
  *     to one double, so ordering on the square is the exact order);
  *   - Manhattan distance is sum_t |q_t - r_t|; infinity-norm distance is
  *     max_t |q_t - r_t| (the paper names both as admissible distances);
+ *   - Mahalanobis distance (also named there) is sqrt(delta^T M delta) for
+ *     delta = q - r and a given symmetric positive definite M (the inverse
+ *     covariance), evaluated straight from that definition in double:
+ *     sum over a of delta_a * (sum over b of M[a][b] * delta_b), both sums in
+ *     ascending index order; the sort compares the quadratic form;
  *   - step 2 is a FULL sort of all m pairs (key, j) with ties broken by the
  *     smaller index j -- the paper's step 2 sorts everything, and the
  *     tie rule makes the result unique;
@@ -183,6 +188,71 @@ int oracle_knn_subset(const float* R, int64_t m, const float* Q, int64_t n, int3
     int rc = oracle_knn(R, m, Qs, nsel, d, k, metric, dist_out, idx_out, nthreads);
     free(Qs);
     return rc;
+}
+
+/* The quadratic form delta^T M delta of one query and one reference, M a
+ * d x d row-major double matrix (the Mahalanobis key; see the header). */
+static double oracle_mahalanobis_key(const float* q, const float* r, int32_t d, const double* M) {
+    double acc = 0.0;
+    for (int32_t a = 0; a < d; ++a) {
+        const double da = (double)q[a] - (double)r[a];
+        double inner = 0.0;
+        for (int32_t b = 0; b < d; ++b) {
+#if ORACLE_MUTANT == 5
+            /* mutant 5: off-diagonal terms dropped */
+            const double mab = (a == b) ? M[(size_t)a * d + b] : 0.0;
+#else
+            const double mab = M[(size_t)a * d + b];
+#endif
+            inner = inner + mab * ((double)q[b] - (double)r[b]);
+        }
+        acc = acc + da * inner;
+    }
+    return acc;
+}
+
+/*
+ * oracle_knn_mahalanobis: the brute-force algorithm under the Mahalanobis
+ * distance with matrix M (d x d, row-major double, symmetric positive
+ * definite).  Outputs as oracle_knn: dist = sqrt(key), ascending by (key,
+ * index).  Returns 0, -1 on invalid arguments, -2 on allocation failure.
+ */
+int oracle_knn_mahalanobis(const float* R, int64_t m, const float* Q, int64_t n, int32_t d,
+                           const double* M, int32_t k, double* dist_out, int32_t* idx_out,
+                           int32_t nthreads) {
+    if (m < 1 || n < 0 || d < 1 || k < 1 || k > m) return -1;
+    if (n == 0) return 0;
+    if (!R || !Q || !M || !dist_out || !idx_out) return -1;
+    int failed = 0;
+#ifdef _OPENMP
+    if (nthreads > 0) omp_set_num_threads(nthreads);
+#else
+    (void)nthreads;
+#endif
+#pragma omp parallel
+    {
+        oracle_pair* pairs = (oracle_pair*)malloc((size_t)m * sizeof(oracle_pair));
+        if (!pairs) {
+#pragma omp atomic write
+            failed = 1;
+        }
+#pragma omp for schedule(dynamic, 4)
+        for (int64_t i = 0; i < n; ++i) {
+            if (!pairs) continue;
+            const float* q = Q + i * d;
+            for (int64_t j = 0; j < m; ++j) {
+                pairs[j].key = oracle_mahalanobis_key(q, R + j * d, d, M);
+                pairs[j].j = (int32_t)j;
+            }
+            qsort(pairs, (size_t)m, sizeof(oracle_pair), oracle_pair_cmp);
+            for (int32_t s = 0; s < k; ++s) {
+                dist_out[i * k + s] = sqrt(pairs[s].key);
+                idx_out[i * k + s] = pairs[s].j;
+            }
+        }
+        free(pairs);
+    }
+    return failed ? -2 : 0;
 }
 
 int oracle_max_threads(void) {

@@ -1,6 +1,7 @@
 // knn_capi.cu -- the C ABI declared in include/knn.h: handles, reference sets
 // (shareable between handles), workspace and the orchestration of one search
 // (select -> finalize -> fallback), all enqueued on one CUDA stream.
+#include <cmath>
 #include <cstdio>
 #include <cstdlib>
 #include <algorithm>
@@ -90,6 +91,16 @@ struct knn_ctx {
     cudaStream_t branch[16] = {};
     cudaEvent_t fork_ev = nullptr, join_ev[16] = {}, t_ev[2] = {};
     knn_batch_info last_batch{};
+
+    // Mahalanobis distance: the Cholesky factor L of the inverse covariance
+    // (device, float32, row-major), the whitened reference set built from
+    // `ref` (rebuilt when `ref` or L changes) and a buffer for whitened queries
+    int32_t mahal_d = 0;
+    float* mahal_L = nullptr;
+    std::shared_ptr<RefSet> mref;
+    const RefSet* mref_src = nullptr;
+    float* qw = nullptr;
+    size_t qw_bytes = 0;
 };
 
 namespace {
@@ -157,10 +168,10 @@ struct Carve {
     }
 };
 
-knn_status build_lowp(knn_ctx* h, int prec) {
-    RefSet& rs = *h->ref;
+knn_status build_lowp_on(knn_ctx* h, std::shared_ptr<RefSet>& ref, int prec) {
+    RefSet& rs = *ref;
     if (rs.lp_prec == prec && rs.R_lp) return KNN_OK;
-    if (h->ref.use_count() > 1) {
+    if (ref.use_count() > 1) {
         h->last_error = "the shared reference set holds another low-precision copy";
         return KNN_ERR_BUSY;
     }
@@ -180,6 +191,69 @@ knn_status build_lowp(knn_ctx* h, int prec) {
     rs.kp = kp;
     rs.lp_prec = prec;
     return KNN_OK;
+}
+
+knn_status build_lowp(knn_ctx* h, int prec) { return build_lowp_on(h, h->ref, prec); }
+
+// A reference set owning a float32 copy of R (m x d) and zeroed norm buffers;
+// src_kind is the cudaMemcpy kind of the copy.
+knn_status new_refset(knn_ctx* h, const float* R, int64_t m, int32_t d, cudaMemcpyKind src_kind,
+                      std::shared_ptr<RefSet>* out) {
+    auto rs = std::make_shared<RefSet>();
+    rs->device = h->device;
+    const size_t bytes = static_cast<size_t>(m) * d * sizeof(float);
+    KNN_CUDA(h, cudaMalloc(&rs->R, bytes));
+    // norms padded to whole 128-reference tiles (zero beyond m)
+    const size_t mpad = static_cast<size_t>((m + 127) / 128 * 128);
+    KNN_CUDA(h, cudaMalloc(&rs->r_norms, mpad * sizeof(float)));
+    KNN_CUDA(h, cudaMalloc(&rs->rmax2, sizeof(uint32_t)));
+    KNN_CUDA(h, cudaMemsetAsync(rs->r_norms, 0, mpad * sizeof(float), h->stream));
+    KNN_CUDA(h, cudaMemsetAsync(rs->rmax2, 0, sizeof(uint32_t), h->stream));
+    if (R) KNN_CUDA(h, cudaMemcpyAsync(rs->R, R, bytes, src_kind, h->stream));
+    KNN_CUDA(h, cudaStreamSynchronize(h->stream));
+    rs->m = m;
+    rs->d = d;
+    *out = std::move(rs);
+    return KNN_OK;
+}
+
+// The whitened reference set of the Mahalanobis distance: R L, built from the
+// current reference set when it or L changed since the last build.
+knn_status ensure_mref(knn_ctx* h) {
+    if (h->mref && h->mref_src == h->ref.get()) return KNN_OK;
+    h->mref.reset();
+    h->mref_src = nullptr;
+    std::shared_ptr<RefSet> w;
+    knn_status s = new_refset(h, nullptr, h->ref->m, h->ref->d, cudaMemcpyDeviceToDevice, &w);
+    if (s != KNN_OK) return s;
+    int l = 0;
+    KNN_CUDA(h, launch_whiten(h->ref->R, h->ref->m, h->ref->d, h->mahal_L, w->R, h->stream, &l));
+    KNN_CUDA(h, cudaStreamSynchronize(h->stream));
+    h->launches += l;
+    h->mref = std::move(w);
+    h->mref_src = h->ref.get();
+    return KNN_OK;
+}
+
+// Cholesky factor of a symmetric positive definite d x d matrix (row-major,
+// lower triangle read), in double: L[i][j] for j <= i, zero above.  Returns
+// false when a pivot is not positive or a value is not finite.
+bool cholesky_lower(const double* M, int32_t d, std::vector<double>* L) {
+    L->assign(static_cast<size_t>(d) * d, 0.0);
+    for (int32_t j = 0; j < d; ++j) {
+        double s = M[static_cast<size_t>(j) * d + j];
+        for (int32_t t = 0; t < j; ++t) s -= (*L)[static_cast<size_t>(j) * d + t] * (*L)[static_cast<size_t>(j) * d + t];
+        if (!(s > 0.0) || !std::isfinite(s)) return false;
+        const double ljj = std::sqrt(s);
+        (*L)[static_cast<size_t>(j) * d + j] = ljj;
+        for (int32_t i = j + 1; i < d; ++i) {
+            double v = M[static_cast<size_t>(i) * d + j];
+            for (int32_t t = 0; t < j; ++t) v -= (*L)[static_cast<size_t>(i) * d + t] * (*L)[static_cast<size_t>(j) * d + t];
+            if (!std::isfinite(v)) return false;
+            (*L)[static_cast<size_t>(i) * d + j] = v / ljj;
+        }
+    }
+    return true;
 }
 
 int ceil_div(int64_t a, int64_t b) { return static_cast<int>((a + b - 1) / b); }
@@ -386,10 +460,12 @@ knn_status enqueue_search(knn_ctx* h, const SearchPlan& sp, const RefView& rv, c
 
 knn_status check_search_args(const knn_ctx* h, int64_t n, int32_t d, int32_t k, knn_metric metric) {
     if (!h) return KNN_ERR_INVALID;
-    if (n < 0 || k < 1 || (metric != KNN_L2 && metric != KNN_L1 && metric != KNN_LINF))
+    if (n < 0 || k < 1 ||
+        (metric != KNN_L2 && metric != KNN_L1 && metric != KNN_LINF && metric != KNN_MAHALANOBIS))
         return KNN_ERR_INVALID;
     if (!h->ref) return KNN_ERR_NOREF;
     if (d != h->ref->d || k > h->ref->m) return KNN_ERR_INVALID;
+    if (metric == KNN_MAHALANOBIS && h->mahal_d != d) return KNN_ERR_INVALID;
     if (k > KNN_K_MAX) return KNN_ERR_UNSUPPORTED;
     if (n > 0x7fffffffLL) return KNN_ERR_UNSUPPORTED;
     return KNN_OK;
@@ -651,6 +727,9 @@ knn_status knn_destroy(knn_handle h) {
     if (h->t_ev[1]) cudaEventDestroy(h->t_ev[1]);
     if (h->ws) cudaFree(h->ws);
     if (h->counters) cudaFree(h->counters);
+    h->mref.reset();
+    if (h->mahal_L) cudaFree(h->mahal_L);
+    if (h->qw) cudaFree(h->qw);
     for (int i = 0; i <= kMaxStages; ++i)
         if (h->ev[i]) cudaEventDestroy(h->ev[i]);
     if (h->stream) cudaStreamDestroy(h->stream);
@@ -663,22 +742,12 @@ knn_status knn_set_reference(knn_handle h, const float* R, int64_t m, int32_t d,
     KNN_CUDA(h, cudaSetDevice(h->device));
     KNN_CUDA(h, cudaStreamSynchronize(h->stream));
     h->ref.reset();   // a shared set stays with the other handles
-    auto rs = std::make_shared<RefSet>();
-    rs->device = h->device;
-    const size_t bytes = static_cast<size_t>(m) * d * sizeof(float);
-    KNN_CUDA(h, cudaMalloc(&rs->R, bytes));
-    // norms padded to whole 128-reference tiles (zero beyond m)
-    const size_t mpad = static_cast<size_t>((m + 127) / 128 * 128);
-    KNN_CUDA(h, cudaMalloc(&rs->r_norms, mpad * sizeof(float)));
-    KNN_CUDA(h, cudaMalloc(&rs->rmax2, sizeof(uint32_t)));
-    KNN_CUDA(h, cudaMemsetAsync(rs->r_norms, 0, mpad * sizeof(float), h->stream));
-    KNN_CUDA(h, cudaMemsetAsync(rs->rmax2, 0, sizeof(uint32_t), h->stream));
-    KNN_CUDA(h, cudaMemcpyAsync(rs->R, R, bytes,
-                                r_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
-                                h->stream));
-    KNN_CUDA(h, cudaStreamSynchronize(h->stream));
-    rs->m = m;
-    rs->d = d;
+    h->mref.reset();
+    h->mref_src = nullptr;
+    std::shared_ptr<RefSet> rs;
+    knn_status s0 = new_refset(h, R, m, d,
+                               r_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, &rs);
+    if (s0 != KNN_OK) return s0;
     h->ref = std::move(rs);   // the handle is the set's only owner until it is shared
     if (h->opt.precision != KNN_FP32) {
         knn_status s = build_lowp(h, h->opt.precision == KNN_BF16 ? kBF16 : kTF32);
@@ -687,6 +756,40 @@ knn_status knn_set_reference(knn_handle h, const float* R, int64_t m, int32_t d,
             return s;
         }
     }
+    return KNN_OK;
+}
+
+knn_status knn_set_mahalanobis(knn_handle h, const double* S_inv, int32_t d) {
+    if (!h) return KNN_ERR_INVALID;
+    KNN_CUDA(h, cudaSetDevice(h->device));
+    KNN_CUDA(h, cudaStreamSynchronize(h->stream));
+    h->mref.reset();
+    h->mref_src = nullptr;
+    if (!S_inv) {
+        if (h->mahal_L) KNN_CUDA(h, cudaFree(h->mahal_L));
+        h->mahal_L = nullptr;
+        h->mahal_d = 0;
+        return KNN_OK;
+    }
+    if (d < 1) return KNN_ERR_INVALID;
+    if (whiten_smem_bytes(d) > 227 * 1024) {
+        h->last_error = "Mahalanobis distance: dimension above what the whitening kernel stages";
+        return KNN_ERR_UNSUPPORTED;
+    }
+    std::vector<double> L;
+    if (!cholesky_lower(S_inv, d, &L)) {
+        h->last_error = "Mahalanobis matrix is not symmetric positive definite (Cholesky pivot <= 0)";
+        return KNN_ERR_INVALID;
+    }
+    std::vector<float> Lf(L.size());
+    for (size_t i = 0; i < L.size(); ++i) Lf[i] = static_cast<float>(L[i]);
+    if (h->mahal_L && h->mahal_d != d) {
+        KNN_CUDA(h, cudaFree(h->mahal_L));
+        h->mahal_L = nullptr;
+    }
+    if (!h->mahal_L) KNN_CUDA(h, cudaMalloc(&h->mahal_L, Lf.size() * sizeof(float)));
+    KNN_CUDA(h, cudaMemcpy(h->mahal_L, Lf.data(), Lf.size() * sizeof(float), cudaMemcpyHostToDevice));
+    h->mahal_d = d;
     return KNN_OK;
 }
 
@@ -712,7 +815,8 @@ knn_status knn_workspace_size(knn_handle h, int64_t n, int32_t d, int32_t k, knn
         return KNN_OK;
     }
     SearchPlan sp;
-    s = plan_search(h, n, k, metric, io_on_device, &sp);
+    // a Mahalanobis search is a Euclidean search of whitened points
+    s = plan_search(h, n, k, metric == KNN_MAHALANOBIS ? KNN_L2 : metric, io_on_device, &sp);
     if (s != KNN_OK) return s;
     *bytes = static_cast<int64_t>(sp.bytes);
     return KNN_OK;
@@ -733,15 +837,32 @@ knn_status knn_search(knn_handle h, const float* Q, int64_t n, int32_t d, int32_
     if (n == 0) return KNN_OK;
     KNN_CUDA(h, cudaSetDevice(h->device));
     cudaStream_t st = cuda_stream ? static_cast<cudaStream_t>(cuda_stream) : h->stream;
-    RefSet& rs = *h->ref;
+    // Mahalanobis: a Euclidean search of whitened queries against the
+    // whitened reference set
+    const bool mahal = metric == KNN_MAHALANOBIS;
+    if (mahal) {
+        knn_status sm = ensure_mref(h);
+        if (sm != KNN_OK) return sm;
+        metric = KNN_L2;
+    }
+    std::shared_ptr<RefSet>& refp = mahal ? h->mref : h->ref;
+    RefSet& rs = *refp;
     const int64_t m = rs.m;
 
     SearchPlan sp;
     knn_status s = plan_search(h, n, k, metric, io_on_device, &sp);
     if (s != KNN_OK) return s;
     if (sp.tensor) {
-        s = build_lowp(h, sp.prec);
+        s = build_lowp_on(h, refp, sp.prec);
         if (s != KNN_OK) return s;
+    }
+    if (mahal && h->qw_bytes < static_cast<size_t>(n) * d * sizeof(float)) {
+        KNN_CUDA(h, cudaStreamSynchronize(st));
+        if (h->qw) KNN_CUDA(h, cudaFree(h->qw));
+        h->qw = nullptr;
+        h->qw_bytes = 0;
+        KNN_CUDA(h, cudaMalloc(&h->qw, static_cast<size_t>(n) * d * sizeof(float)));
+        h->qw_bytes = static_cast<size_t>(n) * d * sizeof(float);
     }
     s = ensure_workspace(h, sp.bytes);
     if (s != KNN_OK) return s;
@@ -763,6 +884,11 @@ knn_status knn_search(knn_handle h, const float* Q, int64_t n, int32_t d, int32_
 
     Counters* ctr = h->counters;
     int l = 0;
+    if (mahal) {
+        KNN_CUDA(h, launch_whiten(Qd, n, d, h->mahal_L, h->qw, st, &l));
+        Qd = h->qw;
+        stage(h, st, "whiten_q");
+    }
     RefView rv{rs.R, rs.m, rs.d, rs.R_lp, rs.kp, rs.rmax2};
     s = enqueue_search(h, sp, rv, Qd, n, k, metric, dd, id, ws, &ctr->fallback_count, st, &l, true);
     if (s != KNN_OK) return s;
@@ -903,6 +1029,7 @@ knn_status knn_search_self(knn_handle h, int32_t k, knn_metric metric, float* di
     if (k < 1 || static_cast<int64_t>(k) + 1 > h->ref->m) return KNN_ERR_INVALID;
     knn_status s = check_search_args(h, h->ref->m, h->ref->d, k + 1, metric);
     if (s != KNN_OK) return s;
+    if (metric == KNN_MAHALANOBIS) return KNN_ERR_UNSUPPORTED;
     KNN_CUDA(h, cudaSetDevice(h->device));
     cudaStream_t st = cuda_stream ? static_cast<cudaStream_t>(cuda_stream) : h->stream;
     RefSet& rs = *h->ref;

@@ -126,6 +126,13 @@ int finalize_max_pool();   // largest S*c one finalize pass handles
 
 // Self-join rows: the n x (k+1) result of searching R against itself, minus
 // each row's own index (or its last entry), into n x k outputs.
+// Whitening for the Mahalanobis distance (knn_whiten.cu): Y = X L for rows
+// of X (rows x d), L the d x d lower-triangular Cholesky factor of the inverse
+// covariance (row-major float32); compensated accumulation, one rounding.
+size_t whiten_smem_bytes(int32_t d);
+cudaError_t launch_whiten(const float* X, int64_t rows, int32_t d, const float* L, float* Y,
+                          cudaStream_t st, int* launches);
+
 cudaError_t launch_drop_self(const float* din, const int32_t* iin, int64_t n, int32_t k, float* dout,
                              int32_t* iout, cudaStream_t st, int* launches);
 

@@ -26,8 +26,8 @@ _lib = ctypes.CDLL(LIB_PATH)
 
 KNN_L2, KNN_L1 = 0, 1
 KNN_FP32, KNN_TF32, KNN_BF16 = 0, 1, 2
-KNN_LINF = 2
-METRICS = {"l2": KNN_L2, "l1": KNN_L1, "linf": KNN_LINF}
+KNN_LINF, KNN_MAHALANOBIS = 2, 3
+METRICS = {"l2": KNN_L2, "l1": KNN_L1, "linf": KNN_LINF, "mahalanobis": KNN_MAHALANOBIS}
 PRECISIONS = {"fp32": KNN_FP32, "tf32": KNN_TF32, "bf16": KNN_BF16}
 STATUS = {0: "KNN_OK", 1: "KNN_ERR_INVALID", 2: "KNN_ERR_OOM", 3: "KNN_ERR_CUDA",
           4: "KNN_ERR_TIMEOUT", 5: "KNN_ERR_NOREF", 6: "KNN_ERR_BUSY",
@@ -76,6 +76,7 @@ _SIGS = {
                                   ctypes.c_int, _P]),
     "knn_sync": (ctypes.c_int, [_H]),
     "knn_set_precision": (ctypes.c_int, [_H, _i32]),
+    "knn_set_mahalanobis": (ctypes.c_int, [_H, _P, _i32]),
     "knn_get_stats": (ctypes.c_int, [_H, ctypes.POINTER(knn_stats)]),
     "knn_set_profiling": (ctypes.c_int, [_H, ctypes.c_int]),
     "knn_get_profile": (ctypes.c_int, [_H, ctypes.POINTER(ctypes.c_float),
@@ -105,6 +106,7 @@ knn_set_reference = _lib.knn_set_reference
 knn_search = _lib.knn_search
 knn_sync = _lib.knn_sync
 knn_set_precision = _lib.knn_set_precision
+knn_set_mahalanobis = _lib.knn_set_mahalanobis
 knn_get_stats = _lib.knn_get_stats
 knn_set_profiling = _lib.knn_set_profiling
 knn_get_profile = _lib.knn_get_profile
@@ -211,6 +213,18 @@ class Index:
 
     def set_precision(self, precision: str):
         self._check(knn_set_precision(self.h, PRECISIONS[precision]), "knn_set_precision")
+
+    def set_mahalanobis(self, S_inv):
+        """Inverse covariance (d x d, symmetric positive definite; host array)
+        of metric="mahalanobis"; None forgets it."""
+        if S_inv is None:
+            self._check(knn_set_mahalanobis(self.h, None, 0), "knn_set_mahalanobis")
+            return
+        import numpy as np
+        M = np.ascontiguousarray(S_inv, dtype=np.float64)
+        if M.ndim != 2 or M.shape[0] != M.shape[1]:
+            raise ValueError("S_inv must be a square matrix")
+        self._check(knn_set_mahalanobis(self.h, M.ctypes.data, M.shape[0]), "knn_set_mahalanobis")
 
     def search_into(self, Q, k: int, dist_out, idx_out, metric: str = "l2", stream=None):
         """knn_search with caller-provided outputs (device tensors: asynchronous
