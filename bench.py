@@ -317,8 +317,9 @@ def configs(args):
     """Timings of the forms and shapes beside the bench line, one JSON line:
     config 1 (n = m = 1200, d = 8, k = 20: float32 CUDA-core and bf16 forms,
     and the oracle on the host cores over all 1200 queries), config 2
-    (n = m = 38400, d = 96, k = 20: float32 Euclidean and Manhattan, bf16 and
-    tf32) and config 3 (m = 2^20, n = 16384, d = 128, k = 100, Gaussian
+    (n = m = 38400, d = 96, k = 20: float32 Euclidean, Manhattan and
+    Chebyshev, bf16 and tf32 Euclidean, bf16 Mahalanobis with a seeded inverse
+    covariance) and config 3 (m = 2^20, n = 16384, d = 128, k = 100, Gaussian
     mixture: float32, bf16 and tf32, 400 re-rank candidates).  Device times
     with inputs resident (CUDA events, median of `reps`), L2 flushed before
     each.  Accuracy against the oracle is the tests' job (tests/test_gpu_tc.py,
@@ -331,9 +332,11 @@ def configs(args):
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
     peaks, _ = load_peaks()
 
-    def timed(R, Q, k, precision, metric, reps):
+    def timed(R, Q, k, precision, metric, reps, S_inv=None):
         ix = knn.Index(0, precision, rerank_factor=4)
         ix.set_reference(R)
+        if S_inv is not None:
+            ix.set_mahalanobis(S_inv)
         dist = torch.empty((Q.shape[0], k), device=dev)
         idx = torch.empty((Q.shape[0], k), dtype=torch.int32, device=dev)
         ix.search_into(Q, k, dist, idx, metric, stream)
@@ -374,10 +377,17 @@ def configs(args):
                          "kind": "oracle", "sample": f"all {Q.shape[0]} queries ({dt:.2f} s)"}}
     R, Q, k = inputs.workload(WORKLOAD)
     Rd, Qd = torch.from_numpy(R).to(dev), torch.from_numpy(Q).to(dev)
+    # an inverse covariance with eigenvalues from 1 to 30 (seeded rotation)
+    g = np.random.Generator(np.random.Philox(8))
+    rot, _ = np.linalg.qr(g.standard_normal((R.shape[1], R.shape[1])))
+    S_inv = (rot * np.geomspace(1.0, 30.0, R.shape[1])) @ rot.T
+    S_inv = 0.5 * (S_inv + S_inv.T)
     res[WORKLOAD] = {"fp32_l2": timed(Rd, Qd, k, "fp32", "l2", 5),
                      "fp32_l1": timed(Rd, Qd, k, "fp32", "l1", 5),
+                     "fp32_linf": timed(Rd, Qd, k, "fp32", "linf", 5),
                      "bf16_l2": timed(Rd, Qd, k, "bf16", "l2", 10),
-                     "tf32_l2": timed(Rd, Qd, k, "tf32", "l2", 10)}
+                     "tf32_l2": timed(Rd, Qd, k, "tf32", "l2", 10),
+                     "bf16_mahalanobis": timed(Rd, Qd, k, "bf16", "mahalanobis", 10, S_inv)}
     name = "mixture_m1048576_n16384_d128_k100"
     R, Q, k = inputs.workload(name)
     Rd, Qd = torch.from_numpy(R).to(dev), torch.from_numpy(Q).to(dev)
