@@ -59,7 +59,9 @@ typedef enum { KNN_L2 = 0, KNN_L1 = 1, KNN_LINF = 2, KNN_MAHALANOBIS = 3 } knn_m
  *             (||q||^2 + ||r||^2 - 2 q.r), the best rerank_factor * k
  *             candidates per query are re-ranked with exact float32
  *             differences.  Manhattan and Chebyshev distances ignore this
- *             setting and run in KNN_FP32.
+ *             setting and run in KNN_FP32, and so do Euclidean searches
+ *             whose rows do not fit the tensor-core tile in shared memory
+ *             (d above 444 in bf16, above 220 in tf32).
  * In every mode, candidates whose float32 distances lie within the float32
  * rounding bound of each other around the returned list are re-checked on the
  * GPU (a float-float sum, and the oracle's float64 arithmetic where that

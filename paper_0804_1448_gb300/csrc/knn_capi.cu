@@ -308,7 +308,9 @@ knn_status plan_search_md(const knn_ctx* h, int64_t m, int32_t d, int precision,
     if (p.tensor) {
         p.kp = tc_padded_dim(d, p.prec);
         p.plan = tc_plan(n, m, d, p.kp, p.prec, p.c, sm_share);
-        if (p.plan.stages == 0) return KNN_ERR_UNSUPPORTED;
+        if (p.plan.stages == 0)   // rows too long for the tile: the float32 form
+            return plan_search_md(h, m, d, KNN_FP32, n, k, metric, io_on_device, sm_share, sp,
+                                  fb_cap_bytes);
         p.S = p.plan.S;
         p.chunk = p.plan.chunk;
     } else {

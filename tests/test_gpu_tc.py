@@ -115,3 +115,80 @@ def test_near_tie_ladder(knn, precision):
     o_dist, o_idx = oracle.knn(R, Q, parity.oracle_k(k, R.shape[0]), "l2")
     assert parity.recall(g_idx, o_idx, k) == 1.0
     parity.compare(g_dist, g_idx, o_dist, o_idx, k, R.shape[0])
+
+
+# ------------------------------------------------------------- edge cases
+
+def run_stats(knn, R, Q, k, precision):
+    import torch
+    ix = knn.Index(0, precision)
+    ix.set_reference(torch.from_numpy(R).cuda())
+    dist, idx = ix.search(torch.from_numpy(Q).cuda(), k, "l2")
+    ix.sync()
+    st = ix.stats()
+    ix.close()
+    return dist.cpu().numpy(), idx.cpu().numpy(), st
+
+
+@pytest.mark.parametrize("precision", ["bf16", "tf32"])
+def test_all_identical_points(knn, precision):
+    """Every reference at the same place: every one passes the filter, the
+    lists overflow or the cut cannot choose, and the exact fallback orders
+    them by index."""
+    R = np.full((3000, 16), 0.5, dtype=np.float32)
+    Q = np.array([[0.5] * 16, [0.25] * 16], dtype=np.float32)
+    g_dist, g_idx, st = run_stats(knn, R, Q, 10, precision)
+    assert g_idx.tolist() == [list(range(10))] * 2
+    np.testing.assert_allclose(g_dist[0], 0.0, atol=0)
+    np.testing.assert_allclose(g_dist[1], np.sqrt(16 * 0.25 ** 2), rtol=1e-6)
+
+
+@pytest.mark.parametrize("precision", ["bf16", "tf32"])
+def test_k_equals_m(knn, precision):
+    """k = m: the whole reference set, sorted, for every query."""
+    R = inputs.uniform(200, 12, seed=3301)
+    Q = inputs.uniform(33, 12, seed=3302)
+    g_dist, g_idx, _ = run_stats(knn, R, Q, 200, precision)
+    o_dist, o_idx = oracle.knn(R, Q, 200, "l2")
+    parity.compare(g_dist, g_idx, o_dist, o_idx, 200, 200)
+
+
+@pytest.mark.parametrize("precision", ["bf16", "tf32"])
+@pytest.mark.parametrize("m", [1500, 9000])
+def test_long_rows(knn, precision, m):
+    """d = 300: operand rows of several 128-byte K blocks, one K block per
+    stage and the 16-bit-code staging; m = 1500 runs without a pilot (every
+    reference appended), m = 9000 with one."""
+    R = inputs.uniform(m, 300, seed=3400 + m)
+    Q = inputs.uniform(150, 300, seed=3401 + m)
+    k = 15
+    g_dist, g_idx, st = run_stats(knn, R, Q, k, precision)
+    o_dist, o_idx = oracle.knn(R, Q, parity.oracle_k(k, m), "l2")
+    assert parity.recall(g_idx, o_idx, k) == 1.0
+    check_recalled_rows(R, Q, g_dist, g_idx, o_dist, o_idx, k)
+
+
+@pytest.mark.parametrize("precision", ["bf16", "tf32"])
+def test_one_partial_reference_tile(knn, precision):
+    """m = 37 (one tile, mostly empty columns) and n = 1000 (several query
+    tiles, ragged)."""
+    R = inputs.uniform(37, 20, seed=3501)
+    Q = inputs.uniform(1000, 20, seed=3502)
+    g_dist, g_idx, _ = run_stats(knn, R, Q, 7, precision)
+    o_dist, o_idx = oracle.knn(R, Q, parity.oracle_k(7, 37), "l2")
+    parity.compare(g_dist, g_idx, o_dist, o_idx, 7, 37)
+
+
+@pytest.mark.parametrize("precision", ["bf16", "tf32"])
+def test_duplicated_references(knn, precision):
+    """Every reference three times (indices i, i + m0, i + 2 m0): equal
+    distances ordered by index, and the three copies of the nearest point come
+    first."""
+    base = inputs.uniform(3000, 24, seed=3601)
+    R = np.concatenate([base, base, base])
+    Q = inputs.uniform(64, 24, seed=3602)
+    g_dist, g_idx, _ = run_stats(knn, R, Q, 9, precision)
+    o_dist, o_idx = oracle.knn(R, Q, parity.oracle_k(9, R.shape[0]), "l2")
+    assert parity.recall(g_idx, o_idx, 9) == 1.0
+    parity.compare(g_dist, g_idx, o_dist, o_idx, 9, R.shape[0])
+    assert np.all(g_idx[:, 1] == g_idx[:, 0] + 3000) and np.all(g_idx[:, 2] == g_idx[:, 0] + 6000)
