@@ -174,8 +174,7 @@ cudaError_t launch_rows(const float* Q, int64_t n, const float* R, int64_t m, in
                         const CandidateSet& cand, cudaStream_t st) {
     auto kern = cc_select_kernel<METRIC, ROWS>;
     const size_t smem = cc_smem_bytes<ROWS>(cand.c);
-    cudaError_t err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                           static_cast<int>(smem));
+    cudaError_t err = allow_smem<cc_select_kernel<METRIC, ROWS>>(smem);
     if (err != cudaSuccess) return err;
     dim3 grid(static_cast<unsigned>((n + ROWS - 1) / ROWS), static_cast<unsigned>(cand.S));
     kern<<<grid, kThreads, smem, st>>>(Q, n, R, m, d, cand);

@@ -1231,9 +1231,7 @@ int finalize_max_pool() { return kMaxPool; }
 template <int METRIC, int NV>
 cudaError_t launch_finalize_nv(const FinalizeArgs& a, int P, int wpb, size_t smem, unsigned grid,
                                cudaStream_t st) {
-    cudaError_t err = cudaFuncSetAttribute(finalize_kernel<METRIC, NV>,
-                                           cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                           static_cast<int>(smem));
+    cudaError_t err = allow_smem<finalize_kernel<METRIC, NV>>(smem);
     if (err != cudaSuccess) return err;
     finalize_kernel<METRIC, NV><<<grid, wpb * 32, smem, st>>>(a, P, wpb);
     return cudaGetLastError();
@@ -1281,9 +1279,7 @@ cudaError_t launch_finalize(const FinalizeArgs& a_in, cudaStream_t st, int* laun
 template <int METRIC>
 cudaError_t launch_fallback_m(const FinalizeArgs& a, double* scratch, int32_t grid, size_t smem,
                               cudaStream_t st) {
-    cudaError_t err = cudaFuncSetAttribute(fallback_kernel<METRIC>,
-                                           cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                           static_cast<int>(smem));
+    cudaError_t err = allow_smem<fallback_kernel<METRIC>>(smem);
     if (err != cudaSuccess) return err;
     fallback_kernel<METRIC><<<grid, kFbThreads, smem, st>>>(a, scratch);
     return cudaGetLastError();

@@ -19,10 +19,32 @@
 //                  more near-equal distances than there are spare candidates).
 #pragma once
 
+#include <atomic>
 #include <cstdint>
 #include <cuda_runtime.h>
 
 namespace knn {
+
+// Opt kernel KERN in to `smem` bytes of dynamic shared memory, once per
+// device and size: cudaFuncSetAttribute costs host time on every call (tens
+// of microseconds in front of an idle GPU), and the setting persists.
+template <auto KERN>
+cudaError_t allow_smem(size_t smem) {
+    constexpr int kDevs = 64;
+    static std::atomic<size_t> done[kDevs];
+    int dev = 0;
+    cudaError_t err = cudaGetDevice(&dev);
+    if (err != cudaSuccess) return err;
+    const bool tracked = dev >= 0 && dev < kDevs;
+    if (tracked && smem <= done[dev].load(std::memory_order_relaxed)) return cudaSuccess;
+    err = cudaFuncSetAttribute(KERN, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
+    if (err == cudaSuccess && tracked) {
+        size_t cur = done[dev].load(std::memory_order_relaxed);
+        while (smem > cur && !done[dev].compare_exchange_weak(cur, smem)) {
+        }
+    }
+    return err;
+}
 
 enum Metric : int { kL2 = 0, kL1 = 1, kLinf = 2 };
 

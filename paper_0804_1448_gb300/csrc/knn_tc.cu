@@ -707,8 +707,7 @@ cudaError_t launch_kernel(const TcPlan& p, const CUtensorMap& mq, const CUtensor
                           const TcArgs& a, cudaStream_t st) {
     auto kern = tc_kernel<PREC, PILOT, KBT, EPI>;
     const size_t smem = tc_smem_bytes(p.kb, p.kbs, p.stages, PILOT, EPI != 0);
-    cudaError_t err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                           static_cast<int>(smem));
+    cudaError_t err = allow_smem<tc_kernel<PREC, PILOT, KBT, EPI>>(smem);
     if (err != cudaSuccess) return err;
     dim3 grid(static_cast<unsigned>((a.n + kBlockM - 1) / kBlockM), static_cast<unsigned>(a.S));
     kern<<<grid, kThreads, smem, st>>>(mq, mr, a);

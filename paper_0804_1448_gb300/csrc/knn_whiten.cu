@@ -15,8 +15,8 @@
 // two-sum, the error terms summed aside and added once at the end, so each
 // whitened coordinate is as accurate as if computed in twice the working
 // precision and then rounded to float32.  L (d x d, row-major, float32) is
-// staged in shared memory; a block takes 32 rows, one thread per (row, output
-// coordinate) pair.
+// staged in shared memory; a block takes 32 rows, each thread four rows and
+// every 32nd output coordinate.
 #include "knn_internal.cuh"
 
 namespace knn {
@@ -24,6 +24,7 @@ namespace {
 
 constexpr int kRowsPerBlock = 32;
 constexpr int kThreads = 256;
+constexpr int kRowsPerWarp = kRowsPerBlock / (kThreads / 32);   // 4
 
 // a + b as an unevaluated pair (hi, lo) with hi = fl(a + b) (Knuth's two-sum)
 __device__ __forceinline__ void two_sum(float a, float b, float& hi, float& lo) {
@@ -32,6 +33,20 @@ __device__ __forceinline__ void two_sum(float a, float b, float& hi, float& lo) 
     lo = (a - (hi - bb)) + (b - bb);
 }
 
+// One Dot2 step: (hi, lo) += a * b, the product split exactly by an FMA.
+__device__ __forceinline__ void dot2_step(float a, float b, float& hi, float& lo) {
+    const float p = a * b;
+    const float e = fmaf(a, b, -p);
+    float s, c;
+    two_sum(hi, p, s, c);
+    hi = s;
+    lo += c + e;
+}
+
+// Warp w takes rows 4w..4w+3 of the block's 32; lane l the output coordinates
+// j = l + 32 c (c < NJ = ceil(d / 32)): 4 NJ independent compensated sums per
+// thread, advanced together over i (a term exists when i >= j).
+template <int NJ>
 __global__ void __launch_bounds__(kThreads)
 whiten_kernel(const float* __restrict__ X, int64_t rows, int32_t d, const float* __restrict__ L,
               float* __restrict__ Y) {
@@ -43,21 +58,34 @@ whiten_kernel(const float* __restrict__ X, int64_t rows, int32_t d, const float*
     for (int t = threadIdx.x; t < d * d; t += blockDim.x) sL[t] = L[t];
     for (int t = threadIdx.x; t < nr * d; t += blockDim.x) sX[t] = X[r0 * d + t];
     __syncthreads();
-    for (int t = threadIdx.x; t < nr * d; t += blockDim.x) {
-        const int row = t / d, j = t % d;
-        const float* x = sX + row * d;
-        float hi = 0.f, lo = 0.f;
-        for (int i = j; i < d; ++i) {
-            const float a = x[i], b = sL[i * d + j];
-            const float p = a * b;
-            const float e = fmaf(a, b, -p);                  // a * b = p + e exactly
-            float s, c;
-            two_sum(hi, p, s, c);
-            hi = s;
-            lo += c + e;
+    const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+    const int rb = warp * kRowsPerWarp;
+    float hi[kRowsPerWarp][NJ], lo[kRowsPerWarp][NJ];
+#pragma unroll
+    for (int r = 0; r < kRowsPerWarp; ++r)
+#pragma unroll
+        for (int c = 0; c < NJ; ++c) hi[r][c] = lo[r][c] = 0.f;
+    for (int i = 0; i < d; ++i) {
+        float x[kRowsPerWarp];
+#pragma unroll
+        for (int r = 0; r < kRowsPerWarp; ++r) x[r] = (rb + r < nr) ? sX[(rb + r) * d + i] : 0.f;
+#pragma unroll
+        for (int c = 0; c < NJ; ++c) {
+            const int j = lane + 32 * c;
+            if (j <= i) {                                    // L[i][j] = 0 above the diagonal
+                const float b = sL[i * d + j];
+#pragma unroll
+                for (int r = 0; r < kRowsPerWarp; ++r) dot2_step(x[r], b, hi[r][c], lo[r][c]);
+            }
         }
-        Y[(r0 + row) * d + j] = hi + lo;
     }
+#pragma unroll
+    for (int r = 0; r < kRowsPerWarp; ++r)
+#pragma unroll
+        for (int c = 0; c < NJ; ++c) {
+            const int j = lane + 32 * c;
+            if (rb + r < nr && j < d) Y[(r0 + rb + r) * d + j] = hi[r][c] + lo[r][c];
+        }
 }
 
 }  // namespace
@@ -70,11 +98,21 @@ cudaError_t launch_whiten(const float* X, int64_t rows, int32_t d, const float* 
                           cudaStream_t st, int* launches) {
     if (rows <= 0) return cudaSuccess;
     const size_t smem = whiten_smem_bytes(d);
-    cudaError_t err = cudaFuncSetAttribute(whiten_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                           static_cast<int>(smem));
-    if (err != cudaSuccess) return err;
+    if (d > 224) return cudaErrorInvalidValue;
     const unsigned grid = static_cast<unsigned>((rows + kRowsPerBlock - 1) / kRowsPerBlock);
-    whiten_kernel<<<grid, kThreads, smem, st>>>(X, rows, d, L, Y);
+    cudaError_t err = cudaSuccess;
+    switch ((d + 31) / 32) {
+#define KNN_WHITEN_CASE(NJ)                                                          \
+        case NJ:                                                                     \
+            err = allow_smem<whiten_kernel<NJ>>(smem);                              \
+            if (err == cudaSuccess) whiten_kernel<NJ><<<grid, kThreads, smem, st>>>(X, rows, d, L, Y); \
+            break;
+        KNN_WHITEN_CASE(1) KNN_WHITEN_CASE(2) KNN_WHITEN_CASE(3) KNN_WHITEN_CASE(4)
+        KNN_WHITEN_CASE(5) KNN_WHITEN_CASE(6)
+        default: KNN_WHITEN_CASE(7)
+#undef KNN_WHITEN_CASE
+    }
+    if (err != cudaSuccess) return err;
     if (launches) ++*launches;
     return cudaGetLastError();
 }
