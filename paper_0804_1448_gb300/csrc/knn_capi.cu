@@ -235,6 +235,17 @@ knn_status ensure_mref(knn_ctx* h) {
     return KNN_OK;
 }
 
+// True for page-locked host memory the GPU can address at the same pointer
+// (cudaHostAlloc / cudaHostRegister under unified addressing).
+bool host_mapped(const void* p) {
+    cudaPointerAttributes at{};
+    if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+        (void)cudaGetLastError();
+        return false;
+    }
+    return at.type == cudaMemoryTypeHost && at.devicePointer == p;
+}
+
 // Cholesky factor of a symmetric positive definite d x d matrix (row-major,
 // lower triangle read), in double: L[i][j] for j <= i, zero above.  Returns
 // false when a pivot is not positive or a value is not finite.
@@ -379,10 +390,13 @@ struct RefView {
 
 // Enqueue the kernels of one planned search on st: Q, dd, id on the device,
 // ws the search's workspace, fallback_count a device int of its own.
+// Qd: the queries as the kernels read them.  Q_copy (tensor-core plans only):
+// when given, Qd is host memory read once by the query preparation, which
+// leaves a float32 device copy there for the later stages.
 knn_status enqueue_search(knn_ctx* h, const SearchPlan& sp, const RefView& rv, const float* Qd,
                           int64_t n, int32_t k, knn_metric metric, float* dd, int32_t* id,
                           unsigned char* ws, int32_t* fallback_count, cudaStream_t st, int* l,
-                          bool stages) {
+                          bool stages, float* Q_copy = nullptr) {
     const int64_t m = rv.m;
     const int32_t d = rv.d;
     const int S = sp.S, c = sp.c;
@@ -403,7 +417,8 @@ knn_status enqueue_search(knn_ctx* h, const SearchPlan& sp, const RefView& rv, c
         qs.qscale = reinterpret_cast<float*>(ws + sp.off_qs);
         HitScale qs_prep = qs;   // the threshold pass sets B when there is one
         if (plan.pilot) qs_prep.qscale = nullptr;
-        KNN_CUDA(h, launch_prepare_query(Qd, n, d, rv.kp, prec, Ql, qs_prep, st, l));
+        KNN_CUDA(h, launch_prepare_query(Qd, n, d, rv.kp, prec, Ql, qs_prep, Q_copy, st, l));
+        if (Q_copy) Qd = Q_copy;
         mark("prepare_q");
         if (plan.pilot) {
             uint32_t* gmax = reinterpret_cast<uint32_t*>(ws + sp.off_gmax);
@@ -875,13 +890,27 @@ knn_status knn_search(knn_handle h, const float* Q, int64_t n, int32_t d, int32_
     int32_t* id = idx_out;
     h->nstages = 0;
     if (h->profiling) cudaEventRecord(h->ev[0], st);
+    // Host buffers.  Pinned ones are read and written by the kernels directly
+    // over the CPU-GPU link (the tensor-core query preparation reads Q once and
+    // keeps a device copy; the finalize writes the outputs in place); pageable
+    // ones (and Q of a float32 or Mahalanobis search) go through copies.
+    float* q_copy = nullptr;
+    bool out_direct = false;
     if (!io_on_device) {
-        Qd = reinterpret_cast<float*>(ws + sp.off_q);
-        dd = reinterpret_cast<float*>(ws + sp.off_dist);
-        id = reinterpret_cast<int32_t*>(ws + sp.off_idx);
-        KNN_CUDA(h, cudaMemcpyAsync(const_cast<float*>(Qd), Q, static_cast<size_t>(n) * d * 4,
-                                    cudaMemcpyHostToDevice, st));
-        stage(h, st, "h2d");
+        const bool q_direct = !mahal && sp.tensor && host_mapped(Q);
+        out_direct = host_mapped(dist_out) && host_mapped(idx_out);
+        if (q_direct) {
+            q_copy = reinterpret_cast<float*>(ws + sp.off_q);
+        } else {
+            Qd = reinterpret_cast<float*>(ws + sp.off_q);
+            KNN_CUDA(h, cudaMemcpyAsync(const_cast<float*>(Qd), Q, static_cast<size_t>(n) * d * 4,
+                                        cudaMemcpyHostToDevice, st));
+            stage(h, st, "h2d");
+        }
+        if (!out_direct) {
+            dd = reinterpret_cast<float*>(ws + sp.off_dist);
+            id = reinterpret_cast<int32_t*>(ws + sp.off_idx);
+        }
     }
 
     Counters* ctr = h->counters;
@@ -892,17 +921,20 @@ knn_status knn_search(knn_handle h, const float* Q, int64_t n, int32_t d, int32_
         stage(h, st, "whiten_q");
     }
     RefView rv{rs.R, rs.m, rs.d, rs.R_lp, rs.kp, rs.rmax2};
-    s = enqueue_search(h, sp, rv, Qd, n, k, metric, dd, id, ws, &ctr->fallback_count, st, &l, true);
+    s = enqueue_search(h, sp, rv, Qd, n, k, metric, dd, id, ws, &ctr->fallback_count, st, &l, true,
+                       q_copy);
     if (s != KNN_OK) return s;
     h->launches += l;
     h->searches += 1;
 
     if (!io_on_device) {
-        KNN_CUDA(h, cudaMemcpyAsync(dist_out, dd, static_cast<size_t>(n) * k * 4,
-                                    cudaMemcpyDeviceToHost, st));
-        KNN_CUDA(h, cudaMemcpyAsync(idx_out, id, static_cast<size_t>(n) * k * 4,
-                                    cudaMemcpyDeviceToHost, st));
-        stage(h, st, "d2h");
+        if (!out_direct) {
+            KNN_CUDA(h, cudaMemcpyAsync(dist_out, dd, static_cast<size_t>(n) * k * 4,
+                                        cudaMemcpyDeviceToHost, st));
+            KNN_CUDA(h, cudaMemcpyAsync(idx_out, id, static_cast<size_t>(n) * k * 4,
+                                        cudaMemcpyDeviceToHost, st));
+            stage(h, st, "d2h");
+        }
         KNN_CUDA(h, cudaStreamSynchronize(st));
         int32_t flag = 0;
         KNN_CUDA(h, cudaMemcpy(&flag, &ctr->error_flag, sizeof(flag), cudaMemcpyDeviceToHost));

@@ -206,9 +206,12 @@ struct HitScale {
 cudaError_t launch_prepare_ref(const float* R, int64_t m, int32_t d, int32_t kp, int prec,
                                void* R_lp, float* norms, uint32_t* rmax2, cudaStream_t st,
                                int* launches);
-// Query copy [q, 1, 1, 0, 0, 0..] (threshold words filled by the threshold pass).
+// Query copy [q, 1, 1, 0, 0, 0..] (threshold words filled by the threshold pass);
+// when Q_copy is given, the float32 rows are also written there (Q may then be
+// host memory the GPU reads directly).
 cudaError_t launch_prepare_query(const float* Q, int64_t n, int32_t d, int32_t kp, int prec,
-                                 void* Q_lp, const HitScale& qs, cudaStream_t st, int* launches);
+                                 void* Q_lp, const HitScale& qs, float* Q_copy, cudaStream_t st,
+                                 int* launches);
 cudaError_t launch_tc_pilot(const TcPlan& p, const void* Q_lp, int64_t n, const void* R_lp,
                             int64_t m, int32_t kp, int prec, uint32_t* gmax, int32_t* error_flag,
                             cudaStream_t st, int* launches);

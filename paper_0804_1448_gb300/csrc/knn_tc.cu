@@ -574,7 +574,8 @@ __device__ __forceinline__ float hit_scale(float nq2, float rmax2, float t) {
 template <int PREC, bool REF>
 __global__ void prepare_kernel(const float* __restrict__ X, int64_t rows, int32_t d, int32_t kp,
                                void* __restrict__ out, float* __restrict__ norms,
-                               uint32_t* __restrict__ rmax2, float* __restrict__ qscale) {
+                               uint32_t* __restrict__ rmax2, float* __restrict__ qscale,
+                               float* __restrict__ xcopy) {
     const int64_t r = (static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x) / 32;
     const int lane = threadIdx.x % 32;
     if (r >= rows) return;
@@ -596,7 +597,10 @@ __global__ void prepare_kernel(const float* __restrict__ X, int64_t rows, int32_
     const float lo = lowp_round<PREC>(h - hi);
     for (int t = lane; t < kp; t += 32) {
         float v = 0.f;
-        if (t < d) v = x[t];
+        if (t < d) {
+            v = x[t];
+            if (!REF && xcopy) xcopy[r * d + t] = v;
+        }
         else if (t == d) v = REF ? hi : 1.f;
         else if (t == d + 1) v = REF ? lo : 1.f;
         else if (t == d + 2 || t == d + 3) v = REF ? 1.f : 0.f;
@@ -904,22 +908,27 @@ cudaError_t launch_prepare_ref(const float* R, int64_t m, int32_t d, int32_t kp,
     if (err != cudaSuccess) return err;
     const unsigned grid = static_cast<unsigned>((m * 32 + 255) / 256);
     if (prec == kBF16)
-        prepare_kernel<kBF16, true><<<grid, 256, 0, st>>>(R, m, d, kp, R_lp, norms, rmax2, nullptr);
+        prepare_kernel<kBF16, true><<<grid, 256, 0, st>>>(R, m, d, kp, R_lp, norms, rmax2, nullptr,
+                                                           nullptr);
     else
-        prepare_kernel<kTF32, true><<<grid, 256, 0, st>>>(R, m, d, kp, R_lp, norms, rmax2, nullptr);
+        prepare_kernel<kTF32, true><<<grid, 256, 0, st>>>(R, m, d, kp, R_lp, norms, rmax2, nullptr,
+                                                           nullptr);
     if (launches) ++*launches;
     return cudaGetLastError();
 }
 
 cudaError_t launch_prepare_query(const float* Q, int64_t n, int32_t d, int32_t kp, int prec,
-                                 void* Q_lp, const HitScale& qs, cudaStream_t st, int* launches) {
+                                 void* Q_lp, const HitScale& qs, float* Q_copy, cudaStream_t st,
+                                 int* launches) {
     const unsigned grid = static_cast<unsigned>((n * 32 + 255) / 256);
     if (prec == kBF16)
         prepare_kernel<kBF16, false><<<grid, 256, 0, st>>>(Q, n, d, kp, Q_lp, nullptr,
-                                                            const_cast<uint32_t*>(qs.rmax2), qs.qscale);
+                                                            const_cast<uint32_t*>(qs.rmax2), qs.qscale,
+                                                            Q_copy);
     else
         prepare_kernel<kTF32, false><<<grid, 256, 0, st>>>(Q, n, d, kp, Q_lp, nullptr,
-                                                            const_cast<uint32_t*>(qs.rmax2), qs.qscale);
+                                                            const_cast<uint32_t*>(qs.rmax2), qs.qscale,
+                                                            Q_copy);
     if (launches) ++*launches;
     return cudaGetLastError();
 }

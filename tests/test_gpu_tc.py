@@ -192,3 +192,28 @@ def test_duplicated_references(knn, precision):
     assert parity.recall(g_idx, o_idx, 9) == 1.0
     parity.compare(g_dist, g_idx, o_dist, o_idx, 9, R.shape[0])
     assert np.all(g_idx[:, 1] == g_idx[:, 0] + 3000) and np.all(g_idx[:, 2] == g_idx[:, 0] + 6000)
+
+
+@pytest.mark.parametrize("precision", ["bf16", "tf32", "fp32"])
+def test_pinned_host_buffers_equal_device_buffers(knn, precision):
+    """Pinned host buffers are read and written by the kernels in place
+    (tensor-core forms: the query preparation reads Q over the CPU-GPU link,
+    the finalize writes the outputs there); pageable ones are copied.  All
+    give the device-buffer result bit for bit."""
+    import torch
+    R = inputs.uniform(20000, 64, seed=3701)
+    Q = inputs.uniform(3000, 64, seed=3702)
+    k = 16
+    ix = knn.Index(0, precision)
+    ix.set_reference(torch.from_numpy(R).cuda())
+    d_dev, i_dev = ix.search(torch.from_numpy(Q).cuda(), k, "l2")
+    ix.sync()
+    Qh = torch.from_numpy(Q).pin_memory()
+    dh = torch.empty((3000, k), dtype=torch.float32).pin_memory()
+    ih = torch.empty((3000, k), dtype=torch.int32).pin_memory()
+    ix.search_into(Qh, k, dh, ih, "l2")            # synchronous for host buffers
+    assert torch.equal(dh, d_dev.cpu()) and torch.equal(ih, i_dev.cpu())
+    d_pg, i_pg = ix.search(Q, k, "l2")             # pageable numpy arrays: copies
+    np.testing.assert_array_equal(d_pg, d_dev.cpu().numpy())
+    np.testing.assert_array_equal(i_pg, i_dev.cpu().numpy())
+    ix.close()
