@@ -634,23 +634,34 @@ __global__ void threshold_kernel(const uint32_t* __restrict__ gmax, int64_t n, i
     }
     for (int o = 16; o > 0; o >>= 1) nq2 += __shfl_xor_sync(0xffffffffu, nq2, o);
     uint32_t v[VPL];
-    uint32_t least = 0xffffffffu;
+    uint32_t least = 0xffffffffu, most = 0u;
+    int nvalid = 0;
 #pragma unroll
     for (int i = 0; i < VPL; ++i) {
         const int g = i * 32 + lane;
         v[i] = (g < G) ? src[g] : 0u;
-        if (v[i] != 0u) least = min(least, v[i]);
+        if (v[i] != 0u) {
+            least = min(least, v[i]);
+            most = max(most, v[i]);
+            ++nvalid;
+        }
     }
     least = __reduce_min_sync(0xffffffffu, least);
-    uint32_t prefix = 0;
-    for (int b = 31; b >= 8; --b) {
+    most = __reduce_max_sync(0xffffffffu, most);
+    nvalid = __reduce_add_sync(0xffffffffu, nvalid);
+    // every group maximum, hence the answer, shares the bits above the highest
+    // bit in which the largest and the smallest differ: start from them
+    const uint32_t diff = most ^ least;
+    const int top = 31 - __clz(diff);                 // -1 when all are equal
+    uint32_t prefix = top < 0 ? most : (top >= 31 ? 0u : (most & ~((2u << top) - 1u)));
+    for (int b = top; b >= 8; --b) {
         const uint32_t cand = prefix | (1u << b);
         int c = 0;
 #pragma unroll
         for (int i = 0; i < VPL; ++i) c += (v[i] >= cand) ? 1 : 0;
         if (__reduce_add_sync(0xffffffffu, c) >= cprime) prefix = cand;
     }
-    const uint32_t best = prefix ? prefix : least;   // fewer than cprime groups: the weakest
+    const uint32_t best = nvalid >= cprime ? prefix : least;   // fewer than cprime groups: the weakest
     const float t_acc = unord_f32(best);
     const float tcol = -t_acc + 1e-3f * (1.f + fabsf(t_acc));
     const float hi = lowp_round<PREC>(tcol);
