@@ -288,7 +288,7 @@ struct SearchPlan {
     TcPlan plan{};
     int64_t fb_grid = 1;
     size_t off_cand = 0, off_ql = 0, off_gmax = 0, off_lists = 0, off_counts = 0, off_qs = 0;
-    size_t off_list = 0, off_scr = 0, off_q = 0, off_dist = 0, off_idx = 0;
+    size_t off_list = 0, off_scr = 0, off_fbdone = 0, off_q = 0, off_dist = 0, off_idx = 0;
     size_t bytes = 0;
 };
 
@@ -361,6 +361,7 @@ knn_status plan_search_md(const knn_ctx* h, int64_t m, int32_t d, int precision,
     }
     p.off_list = cv.take(static_cast<size_t>(n) * sizeof(int32_t));
     p.off_scr = cv.take(static_cast<size_t>(p.fb_grid) * m * sizeof(double));
+    p.off_fbdone = cv.take(static_cast<size_t>(p.fb_grid) * sizeof(int32_t));
     if (!io_on_device) {
         p.off_q = cv.take(static_cast<size_t>(n) * d * sizeof(float));
         p.off_dist = cv.take(static_cast<size_t>(n) * k * sizeof(float));
@@ -467,10 +468,12 @@ knn_status enqueue_search(knn_ctx* h, const SearchPlan& sp, const RefView& rv, c
     fa.recheck_counter = &ctr->recheck_total;
     fa.fallback_total = &ctr->fallback_total;
     fa.fallback_reason = ctr->fallback_reason;
+    fa.fb_done = reinterpret_cast<int32_t*>(ws + sp.off_fbdone);
+    fa.fb_slots = static_cast<int32_t>(sp.fb_grid);
     KNN_CUDA(h, launch_finalize(fa, st, l));
     mark("finalize");
     KNN_CUDA(h, launch_fallback(fa, reinterpret_cast<double*>(ws + sp.off_scr),
-                                static_cast<int32_t>(sp.fb_grid), st, l));
+                                static_cast<int32_t>(sp.fb_grid), fa.fb_done, st, l));
     mark("fallback");
     return KNN_OK;
 }

@@ -681,6 +681,8 @@ finalize_kernel(FinalizeArgs a, int P, int warps_per_block) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
     const int64_t q = static_cast<int64_t>(blockIdx.x) * warps_per_block + warp;
+    if (a.fb_done && blockIdx.x == 0 && static_cast<int>(threadIdx.x) < a.fb_slots)
+        a.fb_done[threadIdx.x] = 0;   // the fallback's chunk counters, for this search
     if (q >= a.n) return;   // warp-uniform: no block-level sync below
 
     const int S = a.use_hits ? 1 : a.cand.S;
@@ -955,6 +957,7 @@ constexpr int kFbThreads = 1024;
 constexpr int kFbWarps = kFbThreads / 32;
 constexpr int kFbMaxK = 1024;
 constexpr int kFbCand = 4096;
+constexpr int64_t kFbChunk = 16384;   // references per CTA in the spread key pass
 constexpr uint64_t kInfBits = 0x7ff0000000000000ull;
 
 struct FbShared {
@@ -1073,128 +1076,193 @@ __device__ void sort_pairs(uint64_t* ck, uint32_t* ci, int cnt) {
     }
 }
 
+// Float32 keys (distance bit patterns) of references [j_begin, j_end) of one
+// query (row in shared memory) into keys32; four references per thread at a
+// time, their loads issued together.
 template <int METRIC>
-__global__ void __launch_bounds__(kFbThreads)
-fallback_kernel(FinalizeArgs a, double* __restrict__ scratch) {
-    __shared__ FbShared sh;
-    extern __shared__ __align__(16) unsigned char fb_dyn[];
-    uint64_t* ck = reinterpret_cast<uint64_t*>(fb_dyn);                  // [kFbCand]
-    uint32_t* ci = reinterpret_cast<uint32_t*>(ck + kFbCand);            // [kFbCand]
-    float* qrow = reinterpret_cast<float*>(ci + kFbCand);                // [d + 4]
+__device__ void fb_keys(const FinalizeArgs& a, const float* qrow, uint32_t* keys32, int64_t j_begin,
+                        int64_t j_end) {
+    const int tid = threadIdx.x, d = a.d;
+    const bool vec = ((d & 3) == 0) && ((reinterpret_cast<uintptr_t>(a.R) & 15) == 0);
+    for (int64_t j0 = j_begin + static_cast<int64_t>(tid) * 4; j0 < j_end; j0 += 4LL * kFbThreads) {
+        float acc[4] = {0.f, 0.f, 0.f, 0.f};
+        if (vec && j0 + 4 <= j_end) {
+            const float4* q4 = reinterpret_cast<const float4*>(qrow);
+            const float4* r4 = reinterpret_cast<const float4*>(a.R + j0 * d);
+            const int d4 = d >> 2;
+#pragma unroll 2
+            for (int t = 0; t < d4; ++t) {
+                const float4 y = q4[t];
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    const float4 x = __ldg(r4 + u * d4 + t);
+                    acc[u] = acc_f32<METRIC>(acc[u], y.x - x.x);
+                    acc[u] = acc_f32<METRIC>(acc[u], y.y - x.y);
+                    acc[u] = acc_f32<METRIC>(acc[u], y.z - x.z);
+                    acc[u] = acc_f32<METRIC>(acc[u], y.w - x.w);
+                }
+            }
+        } else {
+            for (int u = 0; u < 4 && j0 + u < j_end; ++u)
+                acc[u] = dist_f32<METRIC>(qrow, a.R + (j0 + u) * d, d);
+        }
+        for (int u = 0; u < 4 && j0 + u < j_end; ++u) keys32[j0 + u] = __float_as_uint(acc[u]);
+    }
+}
+
+// Given the float32 keys of all m references of query q (keys32, aliasing the
+// float64 scratch `keys`): the k-th by radix selection, float64 distances of
+// every reference that could still be in the answer, the exact order and the
+// k outputs.  One CTA.
+template <int METRIC>
+__device__ void fb_select(const FinalizeArgs& a, int64_t q, const float* qrow, double* keys,
+                          uint32_t* keys32, FbShared& sh, uint64_t* ck, uint32_t* ci) {
     const int tid = threadIdx.x;
-    const int count = *a.fallback_count;
     const int64_t m = a.m;
     const int d = a.d, k = a.k;
     const double rel = f32_rel_bound(d);
-    double* keys = scratch + static_cast<int64_t>(blockIdx.x) * m;
-    uint32_t* keys32 = reinterpret_cast<uint32_t*>(keys);
-
-    for (int f = blockIdx.x; f < count; f += gridDim.x) {
-        const int64_t q = a.fallback_list[f];
-        __syncthreads();
-        for (int t = tid; t < d; t += kFbThreads) qrow[t] = a.Q[q * d + t];
-        if (tid == 0) sh.cnt = 0;
-        __syncthreads();
-        // float32 pass (four references per thread at a time, their loads issued
-        // together) and its k-th smallest
-        const bool vec = ((d & 3) == 0) && ((reinterpret_cast<uintptr_t>(a.R) & 15) == 0);
-        for (int64_t j0 = static_cast<int64_t>(tid) * 4; j0 < m; j0 += 4LL * kFbThreads) {
-            float acc[4] = {0.f, 0.f, 0.f, 0.f};
-            if (vec && j0 + 4 <= m) {
-                const float4* q4 = reinterpret_cast<const float4*>(qrow);
-                const float4* r4 = reinterpret_cast<const float4*>(a.R + j0 * d);
-                const int d4 = d >> 2;
-#pragma unroll 2
-                for (int t = 0; t < d4; ++t) {
-                    const float4 y = q4[t];
-#pragma unroll
-                    for (int u = 0; u < 4; ++u) {
-                        const float4 x = __ldg(r4 + u * d4 + t);
-                        acc[u] = acc_f32<METRIC>(acc[u], y.x - x.x);
-                        acc[u] = acc_f32<METRIC>(acc[u], y.y - x.y);
-                        acc[u] = acc_f32<METRIC>(acc[u], y.z - x.z);
-                        acc[u] = acc_f32<METRIC>(acc[u], y.w - x.w);
-                    }
-                }
-            } else {
-                for (int u = 0; u < 4 && j0 + u < m; ++u)
-                    acc[u] = dist_f32<METRIC>(qrow, a.R + (j0 + u) * d, d);
-            }
-            for (int u = 0; u < 4 && j0 + u < m; ++u) keys32[j0 + u] = __float_as_uint(acc[u]);
+    if (tid == 0) sh.cnt = 0;
+    __syncthreads();
+    const float kth32 = __uint_as_float(radix_select32(keys32, m, k, sh));
+    const double bound = static_cast<double>(kth32) * (1.0 + rel) / (1.0 - rel) * (1.0 + 1e-12) + 1e-37;
+    // the references that could still be in the answer, with float64 distances
+    for (int64_t j = tid; j < m; j += kFbThreads) {
+        if (static_cast<double>(__uint_as_float(keys32[j])) <= bound) {
+            const int pos = atomicAdd(&sh.cnt, 1);
+            if (pos < kFbCand) ci[pos] = static_cast<uint32_t>(j);
         }
+    }
+    __syncthreads();
+    const int cnt = sh.cnt;
+    if (cnt <= kFbCand) {
+        for (int i = tid; i < cnt; i += kFbThreads)
+            ck[i] = dbits(dist_f64<METRIC>(qrow, a.R + static_cast<int64_t>(ci[i]) * d, d));
         __syncthreads();
-        const float kth32 = __uint_as_float(radix_select32(keys32, m, k, sh));
-        const double bound = static_cast<double>(kth32) * (1.0 + rel) / (1.0 - rel) * (1.0 + 1e-12) + 1e-37;
-        // the references that could still be in the answer, with float64 distances
+        sort_pairs(ck, ci, cnt);
+    } else {
+        // more candidates than shared memory holds: float64 keys of all m in
+        // the scratch (they overwrite the float32 keys, so those are recomputed)
         for (int64_t j = tid; j < m; j += kFbThreads) {
-            if (static_cast<double>(__uint_as_float(keys32[j])) <= bound) {
-                const int pos = atomicAdd(&sh.cnt, 1);
-                if (pos < kFbCand) ci[pos] = static_cast<uint32_t>(j);
+            const float v32 = dist_f32<METRIC>(qrow, a.R + j * d, d);
+            keys[j] = (static_cast<double>(v32) <= bound)
+                          ? dist_f64<METRIC>(qrow, a.R + j * d, d)
+                          : bitsd(kInfBits);
+        }
+        __syncthreads();
+        int ties;
+        const uint64_t T = radix_select64(keys, m, k, sh, &ties);
+        const int n_less = k - ties;   // strictly below T; then `ties` entries equal to T
+        if (tid == 0) { sh.less = 0; sh.taken = 0; }
+        __syncthreads();
+        for (int64_t j = tid; j < m; j += kFbThreads) {
+            const uint64_t u = dbits(keys[j]);
+            if (u < T) {
+                const int slot = atomicAdd(&sh.less, 1);
+                ck[slot] = u;
+                ci[slot] = static_cast<uint32_t>(j);
             }
         }
         __syncthreads();
-        const int cnt = sh.cnt;
-        if (cnt <= kFbCand) {
-            for (int i = tid; i < cnt; i += kFbThreads)
-                ck[i] = dbits(dist_f64<METRIC>(qrow, a.R + static_cast<int64_t>(ci[i]) * d, d));
+        // the `ties` entries equal to T with the smallest indices, in index order
+        const int lane = tid % 32, wid = tid / 32;
+        for (int64_t b0 = 0; b0 < m; b0 += kFbThreads) {
+            const int64_t j = b0 + tid;
+            const bool eq = (j < m) && dbits(keys[j]) == T;
+            const unsigned bal = __ballot_sync(0xffffffffu, eq);
+            if (lane == 0) sh.wsum[wid] = __popc(bal);
             __syncthreads();
-            sort_pairs(ck, ci, cnt);
-        } else {
-            // more candidates than shared memory holds: float64 keys of all m in
-            // the scratch (they overwrite the float32 keys, so those are recomputed)
-            for (int64_t j = tid; j < m; j += kFbThreads) {
-                const float v32 = dist_f32<METRIC>(qrow, a.R + j * d, d);
-                keys[j] = (static_cast<double>(v32) <= bound)
-                              ? dist_f64<METRIC>(qrow, a.R + j * d, d)
-                              : bitsd(kInfBits);
+            int before = sh.taken;
+            for (int x = 0; x < wid; ++x) before += sh.wsum[x];
+            before += __popc(bal & ((1u << lane) - 1u));
+            if (eq && before < ties) {
+                ck[n_less + before] = T;
+                ci[n_less + before] = static_cast<uint32_t>(j);
             }
             __syncthreads();
-            int ties;
-            const uint64_t T = radix_select64(keys, m, k, sh, &ties);
-            const int n_less = k - ties;   // strictly below T; then `ties` entries equal to T
-            if (tid == 0) { sh.less = 0; sh.taken = 0; }
-            __syncthreads();
-            for (int64_t j = tid; j < m; j += kFbThreads) {
-                const uint64_t u = dbits(keys[j]);
-                if (u < T) {
-                    const int slot = atomicAdd(&sh.less, 1);
-                    ck[slot] = u;
-                    ci[slot] = static_cast<uint32_t>(j);
-                }
+            if (tid == 0) {
+                int tot = 0;
+                for (int x = 0; x < kFbWarps; ++x) tot += sh.wsum[x];
+                sh.taken += tot;
             }
             __syncthreads();
-            // the `ties` entries equal to T with the smallest indices, in index order
-            const int lane = tid % 32, wid = tid / 32;
-            for (int64_t b0 = 0; b0 < m; b0 += kFbThreads) {
-                const int64_t j = b0 + tid;
-                const bool eq = (j < m) && dbits(keys[j]) == T;
-                const unsigned bal = __ballot_sync(0xffffffffu, eq);
-                if (lane == 0) sh.wsum[wid] = __popc(bal);
-                __syncthreads();
-                int before = sh.taken;
-                for (int x = 0; x < wid; ++x) before += sh.wsum[x];
-                before += __popc(bal & ((1u << lane) - 1u));
-                if (eq && before < ties) {
-                    ck[n_less + before] = T;
-                    ci[n_less + before] = static_cast<uint32_t>(j);
-                }
-                __syncthreads();
-                if (tid == 0) {
-                    int tot = 0;
-                    for (int x = 0; x < kFbWarps; ++x) tot += sh.wsum[x];
-                    sh.taken += tot;
-                }
-                __syncthreads();
-                if (sh.taken >= ties) break;
-            }
-            sort_pairs(ck, ci, k);
+            if (sh.taken >= ties) break;
         }
-        for (int s = tid; s < k; s += kFbThreads) {
-            const double v = bitsd(ck[s]);
-            a.dist_out[q * k + s] =
-                (METRIC == kL2) ? static_cast<float>(__dsqrt_rn(v)) : static_cast<float>(v);
-            a.idx_out[q * k + s] = static_cast<int32_t>(ci[s]);
+        sort_pairs(ck, ci, k);
+    }
+    for (int s = tid; s < k; s += kFbThreads) {
+        const double v = bitsd(ck[s]);
+        a.dist_out[q * k + s] =
+            (METRIC == kL2) ? static_cast<float>(__dsqrt_rn(v)) : static_cast<float>(v);
+        a.idx_out[q * k + s] = static_cast<int32_t>(ci[s]);
+    }
+}
+
+// Shared-memory carve of the fallback kernels: candidate keys and indices,
+// then the query row.
+struct FbDyn {
+    uint64_t* ck;
+    uint32_t* ci;
+    float* qrow;
+};
+__device__ __forceinline__ FbDyn fb_dyn_carve(unsigned char* base) {
+    FbDyn f;
+    f.ck = reinterpret_cast<uint64_t*>(base);                  // [kFbCand]
+    f.ci = reinterpret_cast<uint32_t*>(f.ck + kFbCand);        // [kFbCand]
+    f.qrow = reinterpret_cast<float*>(f.ci + kFbCand);         // [d + 4]
+    return f;
+}
+
+// One launch for every queued query.  Rows y < spread of the grid: the first
+// `spread` queued queries, spread over the GPU -- CTA (p, y) computes the
+// float32 keys of chunk p (kFbChunk references) of queued query y into that
+// query's scratch slot, and the CTA that completes a query's last chunk (a
+// counter per slot, with fences around it) runs the selection; nothing waits
+// on another CTA.  Rows y >= spread (column 0 only): the queued queries beyond
+// the first `spread`, one CTA each, keys and selection, in scratch slot y.
+template <int METRIC>
+__global__ void __launch_bounds__(kFbThreads)
+fallback_kernel(FinalizeArgs a, double* __restrict__ scratch, int32_t* __restrict__ done,
+                int32_t spread) {
+    __shared__ FbShared sh;
+    __shared__ int last;
+    extern __shared__ __align__(16) unsigned char fb_dyn[];
+    const FbDyn f = fb_dyn_carve(fb_dyn);
+    const int tid = threadIdx.x;
+    const int count = *a.fallback_count;
+    const int y = blockIdx.y;
+    const int64_t m = a.m;
+    const int d = a.d;
+    double* keys = scratch + static_cast<int64_t>(y) * m;
+    uint32_t* keys32 = reinterpret_cast<uint32_t*>(keys);
+    if (y < spread) {
+        if (y >= count) return;   // CTA-uniform
+        const int64_t q = a.fallback_list[y];
+        for (int t = tid; t < d; t += kFbThreads) f.qrow[t] = a.Q[q * d + t];
+        __syncthreads();
+        const int64_t j0 = static_cast<int64_t>(blockIdx.x) * kFbChunk;
+        fb_keys<METRIC>(a, f.qrow, keys32, j0, min(m, j0 + kFbChunk));
+        __syncthreads();
+        if (tid == 0) {
+            __threadfence();
+            last = (atomicAdd(&done[y], 1) == static_cast<int>(gridDim.x) - 1) ? 1 : 0;
         }
+        __syncthreads();
+        if (!last) return;
+        __threadfence();
+        fb_select<METRIC>(a, q, f.qrow, keys, keys32, sh, f.ck, f.ci);
+        if (tid == 0) done[y] = 0;
+        return;
+    }
+    if (blockIdx.x != 0) return;
+    const int tail = static_cast<int>(gridDim.y) - spread;
+    for (int i = spread + (y - spread); i < count; i += tail) {
+        const int64_t q = a.fallback_list[i];
+        __syncthreads();
+        for (int t = tid; t < d; t += kFbThreads) f.qrow[t] = a.Q[q * d + t];
+        __syncthreads();
+        fb_keys<METRIC>(a, f.qrow, keys32, 0, m);
+        __syncthreads();
+        fb_select<METRIC>(a, q, f.qrow, keys, keys32, sh, f.ck, f.ci);
     }
 }
 
@@ -1277,25 +1345,29 @@ cudaError_t launch_finalize(const FinalizeArgs& a_in, cudaStream_t st, int* laun
 }
 
 template <int METRIC>
-cudaError_t launch_fallback_m(const FinalizeArgs& a, double* scratch, int32_t grid, size_t smem,
-                              cudaStream_t st) {
+cudaError_t launch_fallback_m(const FinalizeArgs& a, double* scratch, int32_t slots, int32_t* done,
+                              size_t smem, cudaStream_t st) {
     cudaError_t err = allow_smem<fallback_kernel<METRIC>>(smem);
     if (err != cudaSuccess) return err;
-    fallback_kernel<METRIC><<<grid, kFbThreads, smem, st>>>(a, scratch);
+    // half of the scratch slots for spread queries, half for the rest (a lone
+    // slot serves every queued query with one CTA)
+    const int32_t spread = slots >= 2 ? slots / 2 : 0;
+    const unsigned chunks = spread > 0 ? static_cast<unsigned>((a.m + kFbChunk - 1) / kFbChunk) : 1u;
+    fallback_kernel<METRIC><<<dim3(chunks, static_cast<unsigned>(slots)), kFbThreads, smem, st>>>(
+        a, scratch, done, spread);
     return cudaGetLastError();
 }
 
-
-cudaError_t launch_fallback(const FinalizeArgs& a, double* scratch, int32_t grid,
+cudaError_t launch_fallback(const FinalizeArgs& a, double* scratch, int32_t slots, int32_t* done,
                             cudaStream_t st, int* launches) {
     if (a.k > kFbMaxK) return cudaErrorInvalidValue;
     const size_t smem = static_cast<size_t>(kFbCand) * (sizeof(uint64_t) + sizeof(uint32_t)) +
                         (static_cast<size_t>(a.d) + 4) * sizeof(float);
-    if (smem + sizeof(FbShared) > 227 * 1024) return cudaErrorInvalidValue;
+    if (smem + sizeof(FbShared) + 16 > 227 * 1024) return cudaErrorInvalidValue;
     if (launches) ++*launches;
-    if (a.metric == kL2) return launch_fallback_m<kL2>(a, scratch, grid, smem, st);
-    if (a.metric == kL1) return launch_fallback_m<kL1>(a, scratch, grid, smem, st);
-    return launch_fallback_m<kLinf>(a, scratch, grid, smem, st);
+    if (a.metric == kL2) return launch_fallback_m<kL2>(a, scratch, slots, done, smem, st);
+    if (a.metric == kL1) return launch_fallback_m<kL1>(a, scratch, slots, done, smem, st);
+    return launch_fallback_m<kLinf>(a, scratch, slots, done, smem, st);
 }
 
 }  // namespace knn

@@ -125,6 +125,8 @@ struct FinalizeArgs {
     unsigned long long* recheck_counter;
     unsigned long long* fallback_total;
     unsigned long long* fallback_reason;   // [4]: short list, overflow, wide cut, uncertified
+    int32_t* fb_done;                      // fallback chunk counters to zero, or null
+    int32_t fb_slots;
     // rounding bounds for this d, set by launch_finalize: float32 distance
     // (relative), its near-tie window as a float, and the float-float window
     double rel;
@@ -158,8 +160,11 @@ cudaError_t launch_whiten(const float* X, int64_t rows, int32_t d, const float* 
 cudaError_t launch_drop_self(const float* din, const int32_t* iin, int64_t n, int32_t k, float* dout,
                              int32_t* iout, cudaStream_t st, int* launches);
 
-// Exact float64 pass for the queued queries.  scratch holds grid*m doubles.
-cudaError_t launch_fallback(const FinalizeArgs& a, double* scratch, int32_t grid,
+// Exact float64 pass for the queued queries.  scratch holds slots*m doubles;
+// done holds `slots` counters, zeroed by the finalize that runs before (its
+// FinalizeArgs::fb_done / fb_slots).  The first slots/2 queued queries have
+// their float32 key pass spread over the GPU; the rest take one CTA each.
+cudaError_t launch_fallback(const FinalizeArgs& a, double* scratch, int32_t slots, int32_t* done,
                             cudaStream_t st, int* launches);
 
 // ---- tensor-core path (knn_tc.cu) -----------------------------------------

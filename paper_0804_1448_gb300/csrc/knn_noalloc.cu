@@ -42,6 +42,7 @@ struct StaticCounters {
     unsigned long long recheck_total;
     unsigned long long fallback_total;
     unsigned long long fallback_reason[4];
+    int32_t fb_done[64];   // the fallback's chunk counters (zeroed with the rest)
 };
 
 size_t align256(size_t x) { return (x + 255) & ~static_cast<size_t>(255); }
@@ -158,7 +159,7 @@ extern "C" knn_status knn_search_static(const float* R, int64_t m, const float* 
     if (err == cudaSuccess) err = launch_finalize(fa, stream, &launches);
     if (err == cudaSuccess)
         err = launch_fallback(fa, reinterpret_cast<double*>(base + off_fb),
-                              static_cast<int32_t>(fb_grid), stream, &launches);
+                              static_cast<int32_t>(fb_grid), ctr->fb_done, stream, &launches);
     if (err != cudaSuccess) {
         (void)cudaGetLastError();
         return KNN_ERR_CUDA;

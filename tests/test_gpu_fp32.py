@@ -232,3 +232,25 @@ def test_workspace_limit_reports_oom(knn):
         ix.search(torch.rand((1000, 16), device="cuda"), 10)
     assert e.value.status == 2
     ix.close()
+
+
+@pytest.mark.parametrize("precision", ["fp32", "bf16"])
+def test_many_queries_in_the_fallback_at_once(knn, precision):
+    """40000 references at one point and 100 queries: every query goes to
+    the exact fallback.  The first half of the scratch slots take their
+    queries spread over several CTAs (three key chunks each, the last CTA to
+    finish selects); the queries beyond take one CTA each."""
+    import torch
+    R = np.full((40000, 8), 0.5, dtype=np.float32)
+    g = np.random.Generator(np.random.Philox(77))
+    Q = g.uniform(0.0, 1.0, size=(100, 8)).astype(np.float32)
+    ix = knn.Index(0, precision)
+    ix.set_reference(torch.from_numpy(R).cuda())
+    dist, idx = ix.search(torch.from_numpy(Q).cuda(), 12, "l2")
+    ix.sync()
+    st = ix.stats()
+    ix.close()
+    assert st["fallback_queries"] == 100
+    assert idx.cpu().numpy().tolist() == [list(range(12))] * 100
+    want = np.sqrt(((Q.astype(np.float64) - 0.5) ** 2).sum(1))
+    np.testing.assert_allclose(dist.cpu().numpy(), np.repeat(want[:, None], 12, 1), rtol=1e-6)
