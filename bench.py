@@ -319,8 +319,11 @@ def configs(args):
     and the oracle on the host cores over all 1200 queries), config 2
     (n = m = 38400, d = 96, k = 20: float32 Euclidean, Manhattan and
     Chebyshev, bf16 and tf32 Euclidean, bf16 Mahalanobis with a seeded inverse
-    covariance) and config 3 (m = 2^20, n = 16384, d = 128, k = 100, Gaussian
-    mixture: float32, bf16 and tf32, 400 re-rank candidates).  Device times
+    covariance), config 3 (m = 2^20, n = 16384, d = 128, k = 100, Gaussian
+    mixture: float32, bf16 and tf32, 400 re-rank candidates, and the oracle on
+    32 of its queries) and the serving shape (m = 4,194,304, d = 96) at batch
+    sizes 1, 64, 512 and 4096 with k = 20, with the filter's achieved HBM rate
+    on the bf16 reference copy.  Device times
     with inputs resident (CUDA events, median of `reps`), L2 flushed before
     each.  Accuracy against the oracle is the tests' job (tests/test_gpu_tc.py,
     tests/test_gpu_mixture.py)."""
@@ -391,11 +394,36 @@ def configs(args):
     name = "mixture_m1048576_n16384_d128_k100"
     R, Q, k = inputs.workload(name)
     Rd, Qd = torch.from_numpy(R).to(dev), torch.from_numpy(Q).to(dev)
+    sel = np.arange(0, Q.shape[0], Q.shape[0] // 32)[:32]
+    t0 = time.perf_counter()
+    oracle.knn_subset(R, Q, sel, k, "l2")
+    dt = time.perf_counter() - t0
     del R, Q
     res[name] = {"fp32_l2": timed(Rd, Qd, k, "fp32", "l2", 3),
                  "bf16_l2": timed(Rd, Qd, k, "bf16", "l2", 5),
-                 "tf32_l2": timed(Rd, Qd, k, "tf32", "l2", 5)}
+                 "tf32_l2": timed(Rd, Qd, k, "tf32", "l2", 5),
+                 "cpu_baseline": {"value": len(sel) / dt, "unit": "queries/s",
+                                  "cores": oracle.max_threads(), "kind": "oracle",
+                                  "sample": f"{len(sel)} of 16384 queries ({dt:.1f} s)"}}
+    del Rd, Qd
+    torch.cuda.empty_cache()
+    # the serving shape at fixed batch sizes: small batches stream the bf16
+    # reference copy once per search (HBM-bound), large ones are tensor-bound
+    w = inputs.WORKLOADS[SERVE_WORKLOAD]
+    Rs = torch.from_numpy(inputs.workload_refs(SERVE_WORKLOAD)).to(dev)
+    pool = torch.from_numpy(inputs.uniform(8192, w["d"], seed=w["seed_q"])).to(dev)
+    kp = (w["d"] + 4 + 63) // 64 * 64
+    r_bytes = float(w["m"]) * kp * 2
+    serve_rows = {}
+    for b in (1, 64, 512, 4096):
+        t = timed(Rs, pool[:b].contiguous(), 20, "bf16", "l2", 5)
+        if "filter_ms" in t:
+            t["filter_hbm_gbs"] = r_bytes / (t["filter_ms"] / 1e3) / 1e9
+            t["filter_hbm_frac"] = t["filter_hbm_gbs"] / peaks["hbm_gbs"]
+        serve_rows[f"n{b}_k20"] = t
+    res[SERVE_WORKLOAD] = serve_rows
     print(json.dumps({"configs": res, "peaks": {"bf16_tflops": peaks["bf16_tflops"],
+                                                "hbm_gbs": peaks["hbm_gbs"],
                                                 "tf32": "half the bf16 peak (nominal ratio)"}}),
           flush=True)
 

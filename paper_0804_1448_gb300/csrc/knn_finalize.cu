@@ -215,9 +215,9 @@ __host__ __device__ constexpr size_t align16(size_t x) { return (x + 15) & ~stat
 __host__ __device__ inline size_t prefix_bytes(int L) {
     return align16(static_cast<size_t>(L) * 8) * 2 + align16(static_cast<size_t>(L) * 4) * 4;
 }
-__host__ __device__ inline size_t warp_scratch_bytes(int P, int L, int S, int d, bool staged) {
+__host__ __device__ inline size_t warp_scratch_bytes(int P, int L, int S, int d, int stage_entries) {
     const size_t u = prefix_bytes(L);
-    const size_t st = staged ? static_cast<size_t>(kStage) * 8 : 0;
+    const size_t st = static_cast<size_t>(stage_entries) * 8;
     return align16(static_cast<size_t>(P) * 8) + (u > st ? u : st) +
            align16(static_cast<size_t>(S) * 8) + align16((kBins + 4) * 4) +
            align16((static_cast<size_t>(d) + 4) * 4);
@@ -225,7 +225,7 @@ __host__ __device__ inline size_t warp_scratch_bytes(int P, int L, int S, int d,
 
 __host__ __device__ inline int prefix_cap(int P, int k) { return P < k + 64 ? P : k + 64; }
 
-__device__ __forceinline__ WarpScratch carve(unsigned char* base, int P, int L, int S, bool staged) {
+__device__ __forceinline__ WarpScratch carve(unsigned char* base, int P, int L, int S, int stage_entries) {
     WarpScratch w;
     size_t o = 0;
     w.keys = reinterpret_cast<uint64_t*>(base + o);   o += align16(static_cast<size_t>(P) * 8);
@@ -237,7 +237,7 @@ __device__ __forceinline__ WarpScratch carve(unsigned char* base, int P, int L, 
     w.runs = reinterpret_cast<int32_t*>(base + o);    o += align16(static_cast<size_t>(L) * 4);
     w.rend = reinterpret_cast<int32_t*>(base + o);    o += align16(static_cast<size_t>(L) * 4);
     w.rlist = reinterpret_cast<int32_t*>(base + o);   o += align16(static_cast<size_t>(L) * 4);
-    const size_t st = staged ? static_cast<size_t>(kStage) * 8 : 0;
+    const size_t st = static_cast<size_t>(stage_entries) * 8;
     if (o < u0 + st) o = u0 + st;
     w.smax = reinterpret_cast<uint64_t*>(base + o);   o += align16(static_cast<size_t>(S) * 8);
     w.hist = reinterpret_cast<int32_t*>(base + o);    o += align16((kBins + 4) * 4);
@@ -508,6 +508,24 @@ __device__ int gather_hits_impl(const FinalizeArgs& a, int64_t q, int P, WarpScr
     const int S = hl.S, cap = hl.cap, c = hl.c;
     const uint64_t* base = hl.keys + q * static_cast<int64_t>(S) * cap;
     const int32_t* cnts = hl.counts + q * static_cast<int64_t>(S);
+    // every listed key straight from global memory (MODE 0): many short lists
+    // (many reference splits) are walked one list per lane, all lanes at once;
+    // a few long lists one list at a time, its entries over the lanes
+    auto visit_global = [&](auto&& g) {
+        if (S >= 16) {
+            for (int s = lane; s < S; s += 32) {
+                const int cs = min(cnts[s], cap);
+                const uint64_t* sp = base + static_cast<int64_t>(s) * cap;
+                for (int e = 0; e < cs; ++e) g(sp[e]);
+            }
+        } else {
+            for (int s = 0; s < S; ++s) {
+                const int cs = min(cnts[s], cap);
+                const uint64_t* sp = base + static_cast<int64_t>(s) * cap;
+                for (int e = lane; e < cs; e += 32) g(sp[e]);
+            }
+        }
+    };
     uint32_t hv[MODE == 1 ? kRegHits : 1];   // high words of the staged keys (order of the score)
     uint64_t* const dst = MODE == 2 ? w.keys : w.stage;
     if constexpr (STAGED) {
@@ -548,11 +566,7 @@ __device__ int gather_hits_impl(const FinalizeArgs& a, int64_t q, int P, WarpScr
         } else if constexpr (MODE == 2) {
             for (int e = lane; e < total; e += 32) f(hit_val(static_cast<uint32_t>(w.keys[e] >> 32)));
         } else {
-            for (int s = 0; s < S; ++s) {
-                const int cs = min(cnts[s], cap);
-                const uint64_t* sp = base + static_cast<int64_t>(s) * cap;
-                for (int e = lane; e < cs; e += 32) f(hit_val(static_cast<uint32_t>(sp[e] >> 32)));
-            }
+            visit_global([&](uint64_t key) { f(hit_val(static_cast<uint32_t>(key >> 32))); });
         }
     };
     for_each([&](float v) {
@@ -622,17 +636,12 @@ __device__ int gather_hits_impl(const FinalizeArgs& a, int64_t q, int P, WarpScr
     } else {
         if (lane == 0) w.hist[kBins] = 0;
         __syncwarp();
-        for (int s = 0; s < S; ++s) {
-            const int cs = min(cnts[s], cap);
-            const uint64_t* sp = base + static_cast<int64_t>(s) * cap;
-            for (int e = lane; e < cs; e += 32) {
-                const uint64_t key = sp[e];
-                if (keep(hit_val(static_cast<uint32_t>(key >> 32)))) {
-                    const int pos = atomicAdd(&w.hist[kBins], 1);
-                    if (pos < P) w.keys[pos] = key_idx(key);
-                }
+        visit_global([&](uint64_t key) {
+            if (keep(hit_val(static_cast<uint32_t>(key >> 32)))) {
+                const int pos = atomicAdd(&w.hist[kBins], 1);
+                if (pos < P) w.keys[pos] = key_idx(key);
             }
-        }
+        });
         __syncwarp();
         kept = w.hist[kBins];
     }
@@ -677,7 +686,7 @@ __device__ __forceinline__ void queue_fallback(const FinalizeArgs& a, int64_t q,
 
 template <int METRIC, int NV>
 __global__ void __launch_bounds__(kThreads, 4)
-finalize_kernel(FinalizeArgs a, int P, int warps_per_block) {
+finalize_kernel(FinalizeArgs a, int P, int warps_per_block, int stage_entries) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
     const int64_t q = static_cast<int64_t>(blockIdx.x) * warps_per_block + warp;
@@ -688,12 +697,11 @@ finalize_kernel(FinalizeArgs a, int P, int warps_per_block) {
     const int S = a.use_hits ? 1 : a.cand.S;
     const int d = a.d, k = a.k;
     const int Lcap = prefix_cap(P, k);
-    const bool staged = a.use_hits != 0;
-    WarpScratch w = carve(smem_raw + warp_scratch_bytes(P, Lcap, S, d, staged) * warp, P, Lcap, S,
-                          staged);
+    const int se = a.use_hits ? stage_entries : 0;   // staging entries (hit lists only)
+    WarpScratch w = carve(smem_raw + warp_scratch_bytes(P, Lcap, S, d, se) * warp, P, Lcap, S, se);
     // entries that fit keys[P] and the staging area behind it (contiguous)
-    const size_t union_bytes = prefix_bytes(Lcap) > (staged ? static_cast<size_t>(kStage) * 8 : 0)
-                                   ? prefix_bytes(Lcap) : static_cast<size_t>(kStage) * 8;
+    const size_t union_bytes = prefix_bytes(Lcap) > static_cast<size_t>(se) * 8
+                                   ? prefix_bytes(Lcap) : static_cast<size_t>(se) * 8;
     const int stage_all = static_cast<int>((align16(static_cast<size_t>(P) * 8) + union_bytes) / 8);
     // the query row: its loads are issued before the hit-list sizes are read
     const float* qg = a.Q + q * d;
@@ -1297,23 +1305,23 @@ cudaError_t launch_drop_self(const float* din, const int32_t* iin, int64_t n, in
 int finalize_max_pool() { return kMaxPool; }
 
 template <int METRIC, int NV>
-cudaError_t launch_finalize_nv(const FinalizeArgs& a, int P, int wpb, size_t smem, unsigned grid,
-                               cudaStream_t st) {
+cudaError_t launch_finalize_nv(const FinalizeArgs& a, int P, int wpb, int se, size_t smem,
+                               unsigned grid, cudaStream_t st) {
     cudaError_t err = allow_smem<finalize_kernel<METRIC, NV>>(smem);
     if (err != cudaSuccess) return err;
-    finalize_kernel<METRIC, NV><<<grid, wpb * 32, smem, st>>>(a, P, wpb);
+    finalize_kernel<METRIC, NV><<<grid, wpb * 32, smem, st>>>(a, P, wpb, se);
     return cudaGetLastError();
 }
 
 template <int METRIC>
-cudaError_t launch_finalize_m(const FinalizeArgs& a, int nv, int P, int wpb, size_t smem,
+cudaError_t launch_finalize_m(const FinalizeArgs& a, int nv, int P, int wpb, int se, size_t smem,
                               unsigned grid, cudaStream_t st) {
     switch (nv) {
-        case 1: return launch_finalize_nv<METRIC, 1>(a, P, wpb, smem, grid, st);
-        case 2: return launch_finalize_nv<METRIC, 2>(a, P, wpb, smem, grid, st);
-        case 3: return launch_finalize_nv<METRIC, 3>(a, P, wpb, smem, grid, st);
-        case 4: return launch_finalize_nv<METRIC, 4>(a, P, wpb, smem, grid, st);
-        default: return launch_finalize_nv<METRIC, 0>(a, P, wpb, smem, grid, st);
+        case 1: return launch_finalize_nv<METRIC, 1>(a, P, wpb, se, smem, grid, st);
+        case 2: return launch_finalize_nv<METRIC, 2>(a, P, wpb, se, smem, grid, st);
+        case 3: return launch_finalize_nv<METRIC, 3>(a, P, wpb, se, smem, grid, st);
+        case 4: return launch_finalize_nv<METRIC, 4>(a, P, wpb, se, smem, grid, st);
+        default: return launch_finalize_nv<METRIC, 0>(a, P, wpb, se, smem, grid, st);
     }
 }
 
@@ -1325,8 +1333,16 @@ cudaError_t launch_finalize(const FinalizeArgs& a_in, cudaStream_t st, int* laun
     int P = a.use_hits ? 2 * a.hits.c + 32 : a.cand.S * a.cand.c;
     P = (P + 3) & ~3;
     if (P > kMaxPool) return cudaErrorInvalidValue;
+    // hit-list staging: kStage entries; when the queries do not fill the GPU
+    // anyway, room for every list entry a query can have (up to 12288), so
+    // long lists are still read from shared memory
+    int se = a.use_hits ? kStage : 0;
+    if (a.use_hits && a.n <= 256) {
+        const int64_t all = static_cast<int64_t>(a.hits.S) * a.hits.cap;
+        se = static_cast<int>(all < kStage ? kStage : (all > 12288 ? 12288 : all));
+    }
     const size_t per_warp = warp_scratch_bytes(P, prefix_cap(P, a.k), a.use_hits ? 1 : a.cand.S,
-                                               a.d, a.use_hits != 0);
+                                               a.d, se);
     // up to eight warps per block and four blocks per SM when the scratch allows
     int wpb = static_cast<int>((52 * 1024) / per_warp);
     if (wpb < 8) wpb = static_cast<int>((96 * 1024) / per_warp);
@@ -1339,9 +1355,9 @@ cudaError_t launch_finalize(const FinalizeArgs& a_in, cudaStream_t st, int* laun
         ((reinterpret_cast<uintptr_t>(a.R) | reinterpret_cast<uintptr_t>(a.Q)) & 15) == 0;
     const int nv = (aligned && (a.d & 3) == 0 && a.d <= 128) ? (a.d + 31) / 32 : 0;
     if (launches) ++*launches;
-    if (a.metric == kL2) return launch_finalize_m<kL2>(a, nv, P, wpb, smem, grid, st);
-    if (a.metric == kL1) return launch_finalize_m<kL1>(a, nv, P, wpb, smem, grid, st);
-    return launch_finalize_m<kLinf>(a, nv, P, wpb, smem, grid, st);
+    if (a.metric == kL2) return launch_finalize_m<kL2>(a, nv, P, wpb, se, smem, grid, st);
+    if (a.metric == kL1) return launch_finalize_m<kL1>(a, nv, P, wpb, se, smem, grid, st);
+    return launch_finalize_m<kLinf>(a, nv, P, wpb, se, smem, grid, st);
 }
 
 template <int METRIC>
