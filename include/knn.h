@@ -144,6 +144,16 @@ knn_status knn_search(knn_handle h, const float* Q, int64_t n, int32_t d, int32_
 knn_status knn_sync(knn_handle h);
 
 /*
+ * Self-test of that failure detection: enqueues on the handle's stream one
+ * device-side wait, bounded by limit_ms (1..1000), on a barrier nothing
+ * completes -- the wait gives up, raises the handle's error flag the way a
+ * search kernel does and returns -- then does knn_sync.  Returns
+ * KNN_ERR_TIMEOUT when the detection works; the handle stays usable.  No
+ * fault, trap or hang is involved.  Errors: KNN_ERR_INVALID, KNN_ERR_CUDA.
+ */
+knn_status knn_selftest_bounded_wait(knn_handle h, int32_t limit_ms);
+
+/*
  * Change the handle's precision (knn_precision).  Builds the bf16/tf32
  * copy of the current reference set if one is needed.  Synchronous.
  * Errors: KNN_ERR_INVALID, KNN_ERR_OOM, KNN_ERR_CUDA.

@@ -1114,6 +1114,14 @@ knn_status knn_sync(knn_handle h) {
     return KNN_OK;
 }
 
+knn_status knn_selftest_bounded_wait(knn_handle h, int32_t limit_ms) {
+    if (!h || limit_ms < 1 || limit_ms > 1000) return KNN_ERR_INVALID;
+    KNN_CUDA(h, cudaSetDevice(h->device));
+    KNN_CUDA(h, launch_wait_probe(&h->counters->error_flag,
+                                  static_cast<uint64_t>(limit_ms) * 1000000ull, h->stream));
+    return knn_sync(h);
+}
+
 knn_status knn_get_stats(knn_handle h, knn_stats* out) {
     if (!h || !out) return KNN_ERR_INVALID;
     KNN_CUDA(h, cudaSetDevice(h->device));

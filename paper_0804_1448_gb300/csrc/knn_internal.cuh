@@ -157,6 +157,10 @@ size_t whiten_smem_bytes(int32_t d);
 cudaError_t launch_whiten(const float* X, int64_t rows, int32_t d, const float* L, float* Y,
                           cudaStream_t st, int* launches);
 
+// One bounded mbarrier wait that nothing completes: raises *error_flag after
+// limit_ns (the failure path of every device-side wait, exercised on purpose).
+cudaError_t launch_wait_probe(int32_t* error_flag, uint64_t limit_ns, cudaStream_t st);
+
 cudaError_t launch_drop_self(const float* din, const int32_t* iin, int64_t n, int32_t k, float* dout,
                              int32_t* iout, cudaStream_t st, int* launches);
 

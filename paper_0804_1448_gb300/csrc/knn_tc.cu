@@ -790,6 +790,22 @@ TcArgs base_args(const TcPlan& p, int64_t n, int64_t m, int32_t* error_flag) {
 
 }  // namespace
 
+// Self-test of the bounded waits: one thread waits, with the given limit, on
+// an mbarrier nothing arrives at; when the wait gives up it raises the error
+// flag, as the search kernels do, and the kernel returns.
+__global__ void wait_probe_kernel(int32_t* error_flag, uint64_t limit_ns) {
+    __shared__ __align__(8) uint64_t bar;
+    if (threadIdx.x != 0) return;
+    mbar_init(&bar, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    if (!mbar_wait(&bar, 0, nullptr, limit_ns)) atomicExch(error_flag, 1);
+}
+
+cudaError_t launch_wait_probe(int32_t* error_flag, uint64_t limit_ns, cudaStream_t st) {
+    wait_probe_kernel<<<1, 32, 0, st>>>(error_flag, limit_ns);
+    return cudaGetLastError();
+}
+
 int tc_padded_dim(int32_t d, int prec) {
     const int step = (prec == kBF16) ? 64 : 32;   // whole 128-byte K blocks per row
     return (d + kAugCols + step - 1) / step * step;

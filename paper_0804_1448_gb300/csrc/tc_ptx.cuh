@@ -44,14 +44,15 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
 }
 // Bounded wait for the phase of `bar` with the given parity.  Returns false
 // when the CTA's abort flag is raised or the time limit passes.
-static __device__ bool mbar_wait(uint64_t* bar, uint32_t parity, volatile int* abort_flag) {
+static __device__ bool mbar_wait(uint64_t* bar, uint32_t parity, volatile int* abort_flag,
+                                 uint64_t limit_ns = kTimeoutNs) {
     if (mbar_try_wait(bar, parity)) return true;
     const uint64_t t0 = globaltimer();
     for (uint32_t it = 1;; ++it) {
         if (mbar_try_wait(bar, parity)) return true;
         if ((it & 31) == 0) {
             if (abort_flag && *abort_flag) return false;
-            if (globaltimer() - t0 > kTimeoutNs) return false;
+            if (globaltimer() - t0 > limit_ns) return false;
         }
     }
 }

@@ -75,6 +75,7 @@ _SIGS = {
     "knn_search": (ctypes.c_int, [_H, _P, _i64, _i32, _i32, ctypes.c_int, _P, _P,
                                   ctypes.c_int, _P]),
     "knn_sync": (ctypes.c_int, [_H]),
+    "knn_selftest_bounded_wait": (ctypes.c_int, [_H, _i32]),
     "knn_set_precision": (ctypes.c_int, [_H, _i32]),
     "knn_set_mahalanobis": (ctypes.c_int, [_H, _P, _i32]),
     "knn_get_stats": (ctypes.c_int, [_H, ctypes.POINTER(knn_stats)]),
@@ -105,6 +106,7 @@ knn_create = _lib.knn_create
 knn_set_reference = _lib.knn_set_reference
 knn_search = _lib.knn_search
 knn_sync = _lib.knn_sync
+knn_selftest_bounded_wait = _lib.knn_selftest_bounded_wait
 knn_set_precision = _lib.knn_set_precision
 knn_set_mahalanobis = _lib.knn_set_mahalanobis
 knn_get_stats = _lib.knn_get_stats
