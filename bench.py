@@ -65,6 +65,9 @@ def parse_args():
     p.add_argument("--configs", action="store_true",
                    help="timings of the other forms and shapes (configs 1-3) instead of the bench line")
     p.add_argument("--serve-requests", type=int, default=48)
+    p.add_argument("--serve-batch", type=int, default=0,
+                   help="time searches of this many queries on the serving reference set "
+                        "(m = 4,194,304, d = 96, k = 20) instead of the bench line")
     return p.parse_args()
 
 
@@ -428,6 +431,51 @@ def configs(args):
           flush=True)
 
 
+def serve_batch(args):
+    """Searches of args.serve_batch queries against the resident serving set
+    (m = 4,194,304, d = 96, bf16, k = 20): args.warmup untimed, then args.steps
+    timed with CUDA events (L2 flushed before each); one JSON line with the
+    per-search time, the filter's time and its rate on the bf16 reference copy
+    (small batches stream that copy once per search: the HBM-bound case)."""
+    import numpy as np
+    import torch
+    from paper_0804_1448_gb300 import inputs, knn
+    dev = torch.device("cuda", 0)
+    stream = torch.cuda.current_stream(dev)
+    peaks, src = load_peaks()
+    w = inputs.WORKLOADS[SERVE_WORKLOAD]
+    R = torch.from_numpy(inputs.workload_refs(SERVE_WORKLOAD)).to(dev)
+    b = args.serve_batch
+    Q = torch.from_numpy(inputs.uniform(b, w["d"], seed=w["seed_q"])).to(dev)
+    ix = knn.Index(0, "bf16")
+    ix.set_reference(R)
+    dist = torch.empty((b, 20), device=dev)
+    idx = torch.empty((b, 20), dtype=torch.int32, device=dev)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    for _ in range(max(1, args.warmup)):
+        ix.search_into(Q, 20, dist, idx, "l2", stream)
+    ix.set_profiling(True)
+    times, filt = [], []
+    for _ in range(args.steps):
+        flush.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        ix.search_into(Q, 20, dist, idx, "l2", stream)
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        times.append(e0.elapsed_time(e1))
+        filt.append(ix.profile().get("tc_filter", float("nan")))
+    ix.close()
+    kp = (w["d"] + 4 + 63) // 64 * 64
+    r_bytes = float(w["m"]) * kp * 2
+    fms = float(np.median(filt))
+    print(json.dumps({"serve_batch": b, "m": w["m"], "d": w["d"], "k": 20, "precision": "bf16",
+                      "ms": float(np.median(times)), "filter_ms": fms,
+                      "filter_hbm_gbs": r_bytes / (fms / 1e3) / 1e9,
+                      "filter_hbm_frac": r_bytes / (fms / 1e3) / 1e9 / peaks["hbm_gbs"],
+                      "peak_source": f"{src} hbm_gbs"}), flush=True)
+
+
 def sweep(args):
     """The Table 1 grid: N = n = m in TABLE1_N, D in {8, 16, 32, 64, 80, 96},
     k = 20, uniform [0,1) points, Euclidean.  Per point: the bf16 and float32
@@ -490,6 +538,9 @@ def main():
         return
     if args.configs:
         configs(args)
+        return
+    if args.serve_batch > 0:
+        serve_batch(args)
         return
     if args.sweep:
         sweep(args)

@@ -849,7 +849,7 @@ TcPlan tc_plan(int64_t n, int64_t m, int32_t d, int32_t kp, int prec, int32_t c,
     // reference splits: the fewest whose CTAs fill at least 85% of the last wave
     int64_t max_s = m / (4 * kTileN);
     if (max_s < 1) max_s = 1;
-    if (max_s > 64) max_s = 64;
+    if (max_s > 256) max_s = 256;
     int S = 1;
     double best = 0.0;
     for (int s = 1; s <= max_s; ++s) {
