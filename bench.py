@@ -71,6 +71,18 @@ def parse_args():
     return p.parse_args()
 
 
+def max_over_ranks(value: float, pg, device) -> float:
+    """The largest of every rank's `value` (all-reduce MAX through the process
+    group pg; pg None: a single process).  Timings are taken as the slowest
+    rank's, and whole-job throughput is the work of all ranks over that time."""
+    if pg is None:
+        return value
+    import torch
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    pg.all_reduce(t, op=pg.ReduceOp.MAX)
+    return float(t.item())
+
+
 def dist_env():
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -603,11 +615,7 @@ def main():
     total_ms, filt_ms, launches = timed_steps(ix, args.steps, "tc_filter")
     clock_info = clocks.stop()
     prof = ix.profile()
-    ms_step = total_ms / args.steps
-    if pg is not None:
-        t = torch.tensor([ms_step], device=dev)
-        pg.all_reduce(t, op=pg.ReduceOp.MAX)
-        ms_step = float(t.item())
+    ms_step = max_over_ranks(total_ms / args.steps, pg, dev)
     value = world * n / (ms_step / 1e3)
 
     # ---- roofline of the dominant kernel (the tensor-core filter pass)
@@ -632,7 +640,7 @@ def main():
     ix32.sync()
     k32 = max(3, args.steps // 6)
     fp32_ms, _, _ = timed_steps(ix32, k32)
-    fp32_value = world * n / (fp32_ms / k32 / 1e3)
+    fp32_value = world * n / (max_over_ranks(fp32_ms / k32, pg, dev) / 1e3)
     ix32.close()
 
     # ---- end to end through the C ABI with pinned host buffers
@@ -649,7 +657,7 @@ def main():
         ix.search_into(Qh, k, dh, ih, "l2")     # synchronous: Q in, search, results out
         e2e_t.append(time.perf_counter() - t0)
     barrier()
-    e2e_s = statistics.median(e2e_t)
+    e2e_s = max_over_ranks(statistics.median(e2e_t), pg, dev)
     e2e = {"value": world * n / e2e_s, "unit": "queries/s",
            "h2d_bytes_per_step": int(n * d * 4), "d2h_bytes_per_step": int(n * k * 8),
            "statistic": f"median of {e2e_steps} wall-clock steps (mean {statistics.mean(e2e_t) * 1e3:.3f} ms)"}
