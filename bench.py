@@ -40,11 +40,11 @@ WORKLOAD = "uniform_n38400_d96_k20"
 SERVE_WORKLOAD = "serve_m4194304_d96"
 PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
 # DRAM traffic of one tensor-core filter launch on this workload, from one ncu
-# capture (dram__bytes_read.sum + dram__bytes_write.sum: 36.48 + 62.62 MB; see
+# capture (dram__bytes_read.sum + dram__bytes_write.sum: 36.43 + 62.70 MB; see
 # profiles/tc_filter_uniform_n38400_d96_k20.md), valid only for the kernel
 # source it was measured on (sha256 prefix below); otherwise reported as null.
-FILTER_TRAFFIC_BYTES = 99.10e6
-FILTER_TRAFFIC_SRC = "6667399c76f15295"
+FILTER_TRAFFIC_BYTES = 99.13e6
+FILTER_TRAFFIC_SRC = "f09a4600e257e1b7"
 
 FALLBACK_PEAKS = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}
 
