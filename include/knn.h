@@ -238,7 +238,7 @@ knn_status knn_search_self(knn_handle h, int32_t k, knn_metric metric, float* di
  *
  * No handle and no allocation: R (m x d), Q (n x d), dist_out and idx_out
  * (n x k) are device pointers on the current device, valid on cuda_stream
- * (NULL = the legacy default stream); metric is KNN_L2 or KNN_L1; the results
+ * (NULL = the legacy default stream); metric is KNN_L2, KNN_L1 or KNN_LINF; the results
  * follow knn_search's conventions.  The call only enqueues work
  * (asynchronous).  Intermediates live in one 32 MiB __device__ array that
  * belongs to the library's device image, so every GPU that loads the library
