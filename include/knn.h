@@ -154,6 +154,40 @@ knn_status knn_sync(knn_handle h);
 knn_status knn_selftest_bounded_wait(knn_handle h, int32_t limit_ms);
 
 /*
+ * The plan a search would run with, without running it (host only; no GPU,
+ * no handle): how knn_search of n queries against m references of dimension
+ * d would be split and staged on a GPU with num_sms SMs, in the given
+ * precision (knn_precision) with rerank_factor * k re-rank candidates for the
+ * tensor-core forms.  For understanding performance: whether the pilot runs,
+ * how many references a query tile's CTAs share, the hit-list sizes, the
+ * workspace the search needs (device I/O).  KNN_MAHALANOBIS plans as the
+ * Euclidean search it becomes.  Errors: KNN_ERR_INVALID (out NULL, n < 1,
+ * m < 1, d < 1, k < 1, k > m, bad metric, precision or rerank_factor,
+ * num_sms < 1), KNN_ERR_UNSUPPORTED (the search would be refused).
+ */
+typedef struct {
+    int32_t tensor_cores;       /* 1: tensor-core filter (bf16/tf32); 0: float32 CUDA-core select */
+    int32_t candidates;         /* candidates per query kept for the exact re-rank */
+    int32_t splits;             /* reference splits (CTAs sharing one query tile) */
+    int64_t chunk;              /* references per split */
+    int32_t k_blocks;           /* tensor cores: 128-byte K blocks per operand row */
+    int32_t stages;             /* tensor cores: depth of the reference stage ring */
+    int32_t whole_tile_stages;  /* tensor cores: 1 when a stage holds a whole reference tile */
+    int32_t raw_staging;        /* tensor cores: 1 float32 hit staging, 0 16-bit codes */
+    int32_t pilot;              /* tensor cores: 1 pilot + threshold, 0 every reference kept */
+    int32_t pilot_stride;       /* the pilot samples every stride-th reference tile */
+    int32_t pilot_groups;       /* group maxima per query */
+    int32_t threshold_rank;     /* which largest group maximum becomes the threshold */
+    int32_t list_capacity;      /* hit-list entries per query, split and column group */
+    int32_t fallback_slots;     /* scratch rows of the exact fallback */
+    int64_t workspace_bytes;    /* device workspace of the search (device I/O) */
+} knn_plan;
+
+knn_status knn_explain_plan(int64_t n, int64_t m, int32_t d, int32_t k, knn_metric metric,
+                            int32_t precision, int32_t rerank_factor, int32_t num_sms,
+                            knn_plan* out);
+
+/*
  * Change the handle's precision (knn_precision).  Builds the bf16/tf32
  * copy of the current reference set if one is needed.  Synchronous.
  * Errors: KNN_ERR_INVALID, KNN_ERR_OOM, KNN_ERR_CUDA.

@@ -1114,6 +1114,44 @@ knn_status knn_sync(knn_handle h) {
     return KNN_OK;
 }
 
+knn_status knn_explain_plan(int64_t n, int64_t m, int32_t d, int32_t k, knn_metric metric,
+                            int32_t precision, int32_t rerank_factor, int32_t num_sms,
+                            knn_plan* out) {
+    if (!out || n < 1 || m < 1 || d < 1 || k < 1 || k > m || num_sms < 1) return KNN_ERR_INVALID;
+    if (metric != KNN_L2 && metric != KNN_L1 && metric != KNN_LINF && metric != KNN_MAHALANOBIS)
+        return KNN_ERR_INVALID;
+    if (precision < KNN_FP32 || precision > KNN_BF16 || rerank_factor < 1 || rerank_factor > 64)
+        return KNN_ERR_INVALID;
+    if (k > KNN_K_MAX || m > 0x7fffffffLL || n > 0x7fffffffLL) return KNN_ERR_UNSUPPORTED;
+    knn_ctx h;   // only its options are read by the planner
+    h.opt.rerank_factor = rerank_factor;
+    h.opt.precision = precision;
+    SearchPlan sp;
+    const knn_metric planned = metric == KNN_MAHALANOBIS ? KNN_L2 : metric;
+    knn_status s = plan_search_md(&h, m, d, precision, n, k, planned, 1, num_sms, &sp);
+    if (s != KNN_OK) return s;
+    knn_plan o{};
+    o.tensor_cores = sp.tensor ? 1 : 0;
+    o.candidates = sp.c;
+    o.splits = sp.S;
+    o.chunk = sp.chunk;
+    if (sp.tensor) {
+        o.k_blocks = sp.plan.kb;
+        o.stages = sp.plan.stages;
+        o.whole_tile_stages = sp.plan.kbs == sp.plan.kb ? 1 : 0;
+        o.raw_staging = sp.plan.raw;
+        o.pilot = sp.plan.pilot;
+        o.pilot_stride = sp.plan.stride;
+        o.pilot_groups = sp.plan.G;
+        o.threshold_rank = sp.plan.cprime;
+        o.list_capacity = sp.plan.cap;
+    }
+    o.fallback_slots = static_cast<int32_t>(sp.fb_grid);
+    o.workspace_bytes = static_cast<int64_t>(sp.bytes);
+    *out = o;
+    return KNN_OK;
+}
+
 knn_status knn_selftest_bounded_wait(knn_handle h, int32_t limit_ms) {
     if (!h || limit_ms < 1 || limit_ms > 1000) return KNN_ERR_INVALID;
     KNN_CUDA(h, cudaSetDevice(h->device));

@@ -68,6 +68,17 @@ class knn_stats(ctypes.Structure):
 _H = ctypes.c_void_p
 _P = ctypes.c_void_p
 _i32, _i64 = ctypes.c_int32, ctypes.c_int64
+class knn_plan(ctypes.Structure):
+    _fields_ = [("tensor_cores", ctypes.c_int32), ("candidates", ctypes.c_int32),
+                ("splits", ctypes.c_int32), ("chunk", ctypes.c_int64),
+                ("k_blocks", ctypes.c_int32), ("stages", ctypes.c_int32),
+                ("whole_tile_stages", ctypes.c_int32), ("raw_staging", ctypes.c_int32),
+                ("pilot", ctypes.c_int32), ("pilot_stride", ctypes.c_int32),
+                ("pilot_groups", ctypes.c_int32), ("threshold_rank", ctypes.c_int32),
+                ("list_capacity", ctypes.c_int32), ("fallback_slots", ctypes.c_int32),
+                ("workspace_bytes", ctypes.c_int64)]
+
+
 _SIGS = {
     "knn_options_default": (None, [ctypes.POINTER(knn_options)]),
     "knn_create": (ctypes.c_int, [ctypes.POINTER(_H), ctypes.c_int, ctypes.POINTER(knn_options)]),
@@ -76,6 +87,8 @@ _SIGS = {
                                   ctypes.c_int, _P]),
     "knn_sync": (ctypes.c_int, [_H]),
     "knn_selftest_bounded_wait": (ctypes.c_int, [_H, _i32]),
+    "knn_explain_plan": (ctypes.c_int, [_i64, _i64, _i32, _i32, ctypes.c_int, _i32, _i32, _i32,
+                                        ctypes.POINTER(knn_plan)]),
     "knn_set_precision": (ctypes.c_int, [_H, _i32]),
     "knn_set_mahalanobis": (ctypes.c_int, [_H, _P, _i32]),
     "knn_get_stats": (ctypes.c_int, [_H, ctypes.POINTER(knn_stats)]),
@@ -107,6 +120,18 @@ knn_set_reference = _lib.knn_set_reference
 knn_search = _lib.knn_search
 knn_sync = _lib.knn_sync
 knn_selftest_bounded_wait = _lib.knn_selftest_bounded_wait
+knn_explain_plan = _lib.knn_explain_plan
+
+
+def explain_plan(n: int, m: int, d: int, k: int, metric: str = "l2", precision: str = "bf16",
+                 rerank_factor: int = 4, num_sms: int = 152) -> dict:
+    """knn_explain_plan: the plan of a search, as a dict (host only)."""
+    p = knn_plan()
+    st = knn_explain_plan(n, m, d, k, METRICS[metric], PRECISIONS[precision], rerank_factor,
+                          num_sms, ctypes.byref(p))
+    if st != 0:
+        raise KnnError(st, "knn_explain_plan")
+    return {f: getattr(p, f) for f, _ in knn_plan._fields_}
 knn_set_precision = _lib.knn_set_precision
 knn_set_mahalanobis = _lib.knn_set_mahalanobis
 knn_get_stats = _lib.knn_get_stats

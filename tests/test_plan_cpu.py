@@ -1,0 +1,85 @@
+"""Search planning on the host (knn_explain_plan; no GPU): the plan of the
+bench shape, the pilot's invariants over the Table 1 grid and the serving
+shape, which searches run on tensor cores, and argument checks."""
+import math
+
+import pytest
+
+from paper_0804_1448_gb300 import knn
+
+SMS = 152   # GB300
+
+
+def plan(n, m, d, k, **kw):
+    kw.setdefault("num_sms", SMS)
+    return knn.explain_plan(n, m, d, k, **kw)
+
+
+def test_bench_shape():
+    p = plan(38400, 38400, 96, 20)
+    assert p["tensor_cores"] == 1 and p["candidates"] == 80
+    assert p["splits"] == 1 and p["chunk"] == 38400          # 300 query tiles fill two waves
+    assert p["k_blocks"] == 2 and p["whole_tile_stages"] == 1 and p["stages"] == 2
+    assert p["raw_staging"] == 1
+    assert p["pilot"] == 1 and p["pilot_stride"] == 16
+    assert p["pilot_groups"] == 80                             # 10 sampled tiles x 8 groups
+    assert p["threshold_rank"] == 19                           # lambda = 80 * 10/150
+    assert p["list_capacity"] == 256
+
+
+@pytest.mark.parametrize("N", [1200, 2400, 4800, 9600, 19200, 38400])
+@pytest.mark.parametrize("D", [8, 16, 32, 64, 80, 96])
+def test_table1_grid_invariants(N, D):
+    p = plan(N, N, D, 20)
+    assert p["tensor_cores"] == 1
+    assert p["chunk"] % 256 == 0 and p["splits"] * p["chunk"] >= N
+    assert (p["splits"] - 1) * p["chunk"] < N                 # no empty split
+    assert 1 <= p["splits"] <= 256
+    assert p["list_capacity"] % 32 == 0
+    if N >= 4800:
+        assert p["pilot"] == 1
+        assert p["pilot_groups"] <= 2048
+        # the c'-th largest of the group maxima needs groups to spare
+        assert p["pilot_groups"] >= p["threshold_rank"] + 8
+    else:
+        assert p["pilot"] == 0                                 # too few groups even at stride 1
+        assert p["list_capacity"] * 4 * p["splits"] >= N       # every reference fits a list
+
+
+@pytest.mark.parametrize("n", [1, 64, 256])
+def test_small_batches_spread_over_every_sm(n):
+    p = plan(n, 4194304, 96, 20)
+    ctas = math.ceil(n / 128) * p["splits"]                    # query tiles x reference splits
+    assert ctas >= math.ceil(0.85 * SMS)                       # most SMs busy
+    assert p["pilot"] == 1 and p["pilot_groups"] <= 2048
+
+
+def test_which_searches_use_tensor_cores():
+    assert plan(1000, 5000, 32, 10, precision="fp32")["tensor_cores"] == 0
+    assert plan(1000, 5000, 32, 10, metric="l1")["tensor_cores"] == 0
+    assert plan(1000, 5000, 32, 10, metric="linf")["tensor_cores"] == 0
+    assert plan(1000, 5000, 32, 10, metric="mahalanobis")["tensor_cores"] == 1
+    # rows longer than the tensor-core tile holds run in float32
+    assert plan(100, 5000, 444, 10)["tensor_cores"] == 1
+    assert plan(100, 5000, 445, 10)["tensor_cores"] == 0
+    assert plan(100, 5000, 220, 10, precision="tf32")["tensor_cores"] == 1
+    assert plan(100, 5000, 221, 10, precision="tf32")["tensor_cores"] == 0
+
+
+def test_rerank_factor_sets_the_candidates():
+    assert plan(5000, 50000, 64, 10, rerank_factor=4)["candidates"] == 40
+    assert plan(5000, 50000, 64, 10, rerank_factor=8)["candidates"] == 80
+
+
+def test_bad_arguments_are_refused():
+    with pytest.raises(knn.KnnError) as e:
+        plan(10, 100, 8, 101)                                  # k > m
+    assert e.value.status == 1
+    for bad in (dict(n=0), dict(d=0), dict(num_sms=0), dict(rerank_factor=0)):
+        args = dict(n=10, m=100, d=8, k=5)
+        args.update(bad)
+        with pytest.raises(knn.KnnError):
+            knn.explain_plan(args.pop("n"), args.pop("m"), args.pop("d"), args.pop("k"), **args)
+    with pytest.raises(knn.KnnError) as e:
+        plan(10, 5000, 8, 2000)                                # k above KNN_K_MAX
+    assert e.value.status == 7
