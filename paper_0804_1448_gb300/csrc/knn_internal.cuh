@@ -148,8 +148,6 @@ int cc_max_candidates();
 cudaError_t launch_finalize(const FinalizeArgs& a, cudaStream_t st, int* launches);
 int finalize_max_pool();   // largest S*c one finalize pass handles
 
-// Self-join rows: the n x (k+1) result of searching R against itself, minus
-// each row's own index (or its last entry), into n x k outputs.
 // Whitening for the Mahalanobis distance (knn_whiten.cu): Y = X L for rows
 // of X (rows x d), L the d x d lower-triangular Cholesky factor of the inverse
 // covariance (row-major float32); compensated accumulation, one rounding.
@@ -161,6 +159,8 @@ cudaError_t launch_whiten(const float* X, int64_t rows, int32_t d, const float* 
 // limit_ns (the failure path of every device-side wait, exercised on purpose).
 cudaError_t launch_wait_probe(int32_t* error_flag, uint64_t limit_ns, cudaStream_t st);
 
+// Self-join rows: the n x (k+1) result of searching R against itself, minus
+// each row's own index (or its last entry), into n x k outputs.
 cudaError_t launch_drop_self(const float* din, const int32_t* iin, int64_t n, int32_t k, float* dout,
                              int32_t* iout, cudaStream_t st, int* launches);
 

@@ -122,16 +122,6 @@ knn_sync = _lib.knn_sync
 knn_selftest_bounded_wait = _lib.knn_selftest_bounded_wait
 knn_explain_plan = _lib.knn_explain_plan
 
-
-def explain_plan(n: int, m: int, d: int, k: int, metric: str = "l2", precision: str = "bf16",
-                 rerank_factor: int = 4, num_sms: int = 152) -> dict:
-    """knn_explain_plan: the plan of a search, as a dict (host only)."""
-    p = knn_plan()
-    st = knn_explain_plan(n, m, d, k, METRICS[metric], PRECISIONS[precision], rerank_factor,
-                          num_sms, ctypes.byref(p))
-    if st != 0:
-        raise KnnError(st, "knn_explain_plan")
-    return {f: getattr(p, f) for f, _ in knn_plan._fields_}
 knn_set_precision = _lib.knn_set_precision
 knn_set_mahalanobis = _lib.knn_set_mahalanobis
 knn_get_stats = _lib.knn_get_stats
@@ -147,6 +137,17 @@ knn_batch_info_get = _lib.knn_batch_info_get
 knn_destroy = _lib.knn_destroy
 knn_status_string = _lib.knn_status_string
 knn_last_error = _lib.knn_last_error
+
+
+def explain_plan(n: int, m: int, d: int, k: int, metric: str = "l2", precision: str = "bf16",
+                 rerank_factor: int = 4, num_sms: int = 152) -> dict:
+    """knn_explain_plan: the plan of a search, as a dict (host only)."""
+    p = knn_plan()
+    st = knn_explain_plan(n, m, d, k, METRICS[metric], PRECISIONS[precision], rerank_factor,
+                          num_sms, ctypes.byref(p))
+    if st != 0:
+        raise KnnError(st, "knn_explain_plan")
+    return {f: getattr(p, f) for f, _ in knn_plan._fields_}
 
 
 class KnnError(RuntimeError):
