@@ -64,6 +64,18 @@ typedef struct {
 } oracle_pair;
 
 /* Ascending by key, ties by the smaller reference index (reading c1). */
+/* Threads of one call: nthreads when positive, else the OpenMP default.  Passed
+ * to the parallel region alone, so one call's count does not carry over to the
+ * next (omp_set_num_threads would). */
+static int oracle_team(int32_t nthreads) {
+#ifdef _OPENMP
+    return nthreads > 0 ? nthreads : omp_get_max_threads();
+#else
+    (void)nthreads;
+    return 1;
+#endif
+}
+
 static int oracle_pair_cmp(const void* a, const void* b) {
     const oracle_pair* x = (const oracle_pair*)a;
     const oracle_pair* y = (const oracle_pair*)b;
@@ -117,12 +129,9 @@ int oracle_knn(const float* R, int64_t m, const float* Q, int64_t n, int32_t d,
     if (n == 0) return 0;
     if (!R || !Q || !dist_out || !idx_out) return -1;
     int failed = 0;
-#ifdef _OPENMP
-    if (nthreads > 0) omp_set_num_threads(nthreads);
-#else
-    (void)nthreads;
-#endif
-#pragma omp parallel
+    const int team = oracle_team(nthreads);
+    (void)team;
+#pragma omp parallel num_threads(team)
     {
         oracle_pair* pairs = (oracle_pair*)malloc((size_t)m * sizeof(oracle_pair));
         if (!pairs) {
@@ -224,12 +233,9 @@ int oracle_knn_mahalanobis(const float* R, int64_t m, const float* Q, int64_t n,
     if (n == 0) return 0;
     if (!R || !Q || !M || !dist_out || !idx_out) return -1;
     int failed = 0;
-#ifdef _OPENMP
-    if (nthreads > 0) omp_set_num_threads(nthreads);
-#else
-    (void)nthreads;
-#endif
-#pragma omp parallel
+    const int team = oracle_team(nthreads);
+    (void)team;
+#pragma omp parallel num_threads(team)
     {
         oracle_pair* pairs = (oracle_pair*)malloc((size_t)m * sizeof(oracle_pair));
         if (!pairs) {

@@ -260,6 +260,23 @@ def test_subset_and_pairs_agree_with_full():
     np.testing.assert_array_equal(np.sqrt(keys), ds.reshape(-1))
 
 
+def test_thread_count_is_per_call():
+    # the result does not depend on the thread count, and a call's count does
+    # not stay behind for the next one (the single-core timing runs between
+    # all-core ones)
+    R = inputs.uniform(500, 5, seed=93)
+    Q = inputs.uniform(64, 5, seed=94)
+    before = oracle.max_threads()
+    d1, i1 = oracle.knn(R, Q, 10, "l1", nthreads=1)
+    assert oracle.max_threads() == before
+    d3, i3 = oracle.knn(R, Q, 10, "l1", nthreads=3)
+    np.testing.assert_array_equal(d1, d3)
+    np.testing.assert_array_equal(i1, i3)
+    M = np.eye(5)
+    oracle.knn_mahalanobis(R, Q, M, 4, nthreads=1)
+    assert oracle.max_threads() == before
+
+
 # --------------------------------------------------------------------------
 # 5. the pins catch planted mistakes
 # --------------------------------------------------------------------------
