@@ -325,17 +325,8 @@ knn_status plan_search_md(const knn_ctx* h, int64_t m, int32_t d, int precision,
         p.S = p.plan.S;
         p.chunk = p.plan.chunk;
     } else {
-        int S = 1;
-        const int64_t tiles = (n + 63) / 64;
-        const int64_t want = 2LL * sm_share;
-        if (tiles < want) S = ceil_div(want, tiles);
-        const int64_t max_by_size = m / (8LL * p.c);
-        if (S > max_by_size) S = static_cast<int>(max_by_size);
-        if (S < 1) S = 1;
-        while (S > 1 && static_cast<int64_t>(S) * p.c > finalize_max_pool()) --S;
-        int64_t chunk = (m + S - 1) / S;
-        chunk = (chunk + 127) / 128 * 128;
-        S = ceil_div(m, chunk);
+        int64_t chunk = 0;
+        const int S = cc_plan_splits(n, m, p.c, sm_share, finalize_max_pool(), &chunk);
         if (static_cast<int64_t>(S) * p.c > finalize_max_pool()) return KNN_ERR_UNSUPPORTED;
         p.S = S;
         p.chunk = chunk;

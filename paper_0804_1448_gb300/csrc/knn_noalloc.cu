@@ -99,17 +99,8 @@ extern "C" knn_status knn_search_static(const float* R, int64_t m, const float* 
     if (c > cc_max_candidates()) c = cc_max_candidates();
     if (c > m) c = static_cast<int>(m);
     if (c < k) return KNN_ERR_UNSUPPORTED;
-    int S = 1;
-    const int64_t tiles = (n + 63) / 64;
-    const int64_t want = 2LL * ds.num_sms;
-    if (tiles < want) S = static_cast<int>((want + tiles - 1) / tiles);
-    const int64_t max_by_size = m / (8LL * c);
-    if (S > max_by_size) S = static_cast<int>(max_by_size);
-    if (S < 1) S = 1;
-    while (S > 1 && static_cast<int64_t>(S) * c > finalize_max_pool()) --S;
-    int64_t chunk = (m + S - 1) / S;
-    chunk = (chunk + 127) / 128 * 128;
-    S = static_cast<int>((m + chunk - 1) / chunk);
+    int64_t chunk = 0;
+    const int S = cc_plan_splits(n, m, c, ds.num_sms, finalize_max_pool(), &chunk);
     if (static_cast<int64_t>(S) * c > finalize_max_pool()) return KNN_ERR_UNSUPPORTED;
 
     // layout of the static scratch: counters, candidates, fallback queue, and
