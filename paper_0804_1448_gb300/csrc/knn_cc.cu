@@ -317,9 +317,15 @@ int cc_plan_splits(int64_t n, int64_t m, int32_t c, int num_sms, int max_pool,
         const int64_t rounds = (ctas / slots) * per_sm + (ctas % slots + sms - 1) / sms;
         return static_cast<double>(rounds) * static_cast<double>(chunk + 2 * kTM);
     };
-    double best = cost(1);
-    for (int64_t S = 2; S <= s_cap; ++S) best = best < cost(S) ? best : cost(S);
-    int64_t S = 1;
+    // The estimate takes a lone CTA on an SM to run as fast as the SM's full
+    // share, which holds for long chunks only; when the query tiles give
+    // fewer than two CTAs per SM, at least enough splits for two are taken.
+    int64_t s_min = 1;
+    if (tiles < 2 * sms) s_min = (2 * sms + tiles - 1) / tiles;
+    if (s_min > s_cap) s_min = s_cap;
+    double best = cost(s_min);
+    for (int64_t S = s_min + 1; S <= s_cap; ++S) best = best < cost(S) ? best : cost(S);
+    int64_t S = s_min;
     while (S < s_cap && cost(S) > 1.02 * best) ++S;
     const int64_t chunk = chunk_of(S);
     *chunk_out = chunk;

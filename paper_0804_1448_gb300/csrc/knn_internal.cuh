@@ -146,9 +146,10 @@ int cc_max_candidates();
 
 // Reference splits S of the float32 search and their length *chunk (a
 // multiple of 128): among the S with every split at least 8c long and S*c
-// within max_pool, the one with the least estimated time, the CTAs resident
-// on an SM sharing its throughput (so a partly filled last wave of CTAs costs
-// what its busiest SM holds).
+// within max_pool, and at least two CTAs per SM where that is possible, the
+// one with the least estimated time, the CTAs resident on an SM sharing its
+// throughput (so a partly filled last wave of CTAs costs what its busiest SM
+// holds).
 int cc_plan_splits(int64_t n, int64_t m, int32_t c, int num_sms, int max_pool, int64_t* chunk);
 
 cudaError_t launch_finalize(const FinalizeArgs& a, cudaStream_t st, int* launches);
