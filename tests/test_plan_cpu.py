@@ -1,6 +1,7 @@
 """Search planning on the host (knn_explain_plan; no GPU): the plan of the
 bench shape, the pilot's invariants over the Table 1 grid and the serving
-shape, which searches run on tensor cores, and argument checks."""
+shape, which searches run on tensor cores, the reference splits of the
+float32 form, and argument checks."""
 import math
 
 import pytest
@@ -83,3 +84,49 @@ def test_bad_arguments_are_refused():
     with pytest.raises(knn.KnnError) as e:
         plan(10, 5000, 8, 2000)                                # k above KNN_K_MAX
     assert e.value.status == 7
+
+
+# ---------------------------------------------------------------------------
+# float32 CUDA-core form: reference splits
+# ---------------------------------------------------------------------------
+def fp32(n, m, d, k, **kw):
+    return plan(n, m, d, k, precision="fp32", **kw)
+
+
+def test_fp32_bench_shape_keeps_one_split():
+    # 600 tiles of 64 queries: one full wave of three CTAs per SM and a
+    # second of one, which costs less than splitting the references
+    p = fp32(38400, 38400, 96, 20)
+    assert p["tensor_cores"] == 0 and p["candidates"] == 28    # k + max(8, k/4)
+    assert p["splits"] == 1 and p["chunk"] == 38400
+
+
+def test_fp32_long_reference_set_is_split():
+    # 256 query tiles, k = 100: two CTAs per SM; one split per query tile
+    # would leave a last wave of 208 CTAs holding two on most SMs
+    p = fp32(16384, 1 << 20, 128, 100)
+    assert p["candidates"] == 125 and p["splits"] == 7
+
+
+@pytest.mark.parametrize("N,S", [(1200, 5), (2400, 7), (4800, 6), (9600, 3), (19200, 2), (38400, 1)])
+def test_fp32_table1_splits(N, S):
+    # at least two CTAs per SM where the query tiles alone give fewer
+    p = fp32(N, N, 96, 20)
+    assert p["splits"] == S
+    tiles = math.ceil(N / 64)
+    if tiles < 2 * SMS:
+        # splits no longer than those of the smallest count giving two CTAs
+        # per SM (or of the most splits 8c-long references allow)
+        s_min = min(math.ceil(2 * SMS / tiles), N // (8 * 28))
+        assert p["chunk"] <= math.ceil(math.ceil(N / s_min) / 128) * 128
+
+
+@pytest.mark.parametrize("n,m,k", [(1, 1000, 5), (64, 4194304, 20), (700, 5000, 16), (4096, 4194304, 20),
+                                   (38400, 38400, 1000), (100000, 1000, 5), (333, 123457, 64)])
+def test_fp32_split_invariants(n, m, k):
+    p = fp32(n, m, 24, k)
+    S, chunk, c = p["splits"], p["chunk"], p["candidates"]
+    assert chunk % 128 == 0 and S * chunk >= m and (S - 1) * chunk < m   # no empty split
+    assert S * c <= 4096                                                 # one finalize pool
+    if S > 1:
+        assert chunk >= 8 * c - 127                                     # splits much longer than c
