@@ -48,6 +48,51 @@ def test_host_only_entry_points(lib):
     assert lib.knn_set_reference(None, None, 1, 1, 0) == 1
 
 
+def test_every_entry_point_refuses_a_null_handle(lib):
+    """Argument checks come before any CUDA call (KNN_ERR_INVALID = 1)."""
+    from paper_0804_1448_gb300 import knn
+    out = ctypes.c_int64(0)
+    stats, info = knn.knn_stats(), knn.knn_batch_info()
+    count = ctypes.c_int32(0)
+    assert knn.knn_sync(None) == 1
+    assert knn.knn_selftest_bounded_wait(None, 10) == 1
+    assert knn.knn_set_precision(None, 2) == 1
+    assert knn.knn_set_mahalanobis(None, None, 4) == 1
+    assert knn.knn_get_stats(None, ctypes.byref(stats)) == 1
+    assert knn.knn_set_profiling(None, 1) == 1
+    assert knn.knn_get_profile(None, None, None, 0, ctypes.byref(count)) == 1
+    assert knn.knn_search_self(None, 4, 0, None, None, None) == 1
+    assert knn.knn_create_shared(None, None, None) == 1
+    h = knn._H()
+    assert knn.knn_create_shared(ctypes.byref(h), None, None) == 1 and not h.value
+    assert knn.knn_workspace_size(None, 10, 4, 2, 0, 1, ctypes.byref(out)) == 1
+    assert knn.knn_workspace_size(None, 10, 4, 2, 0, 1, None) == 1
+    assert knn.knn_reserve(None, 1 << 20) == 1
+    assert knn.knn_search_batch(None, None, 0, 0, None) == 1
+    assert knn.knn_batch_info_get(None, ctypes.byref(info)) == 1
+    assert knn.knn_last_error(None) == b""
+
+
+def test_static_entry_checks_arguments_first(lib):
+    """knn_search_static: invalid shapes, metric or pointers are refused, and
+    n = 0 is a no-op, all before the device is touched."""
+    from paper_0804_1448_gb300 import knn
+    buf = (ctypes.c_float * 64)()
+    ib = (ctypes.c_int32 * 64)()
+    p = ctypes.cast(buf, ctypes.c_void_p)
+    q = ctypes.cast(ib, ctypes.c_void_p)
+    call = knn.knn_search_static
+    assert call(p, 0, p, 1, 4, 1, 0, p, q, None) == 1          # m < 1
+    assert call(p, 8, p, -1, 4, 1, 0, p, q, None) == 1         # n < 0
+    assert call(p, 8, p, 1, 0, 1, 0, p, q, None) == 1          # d < 1
+    assert call(p, 8, p, 1, 4, 9, 0, p, q, None) == 1          # k > m
+    assert call(p, 8, p, 1, 4, 1, 3, p, q, None) == 1          # Mahalanobis is not offered
+    assert call(None, 8, p, 1, 4, 1, 0, p, q, None) == 1       # no reference set
+    assert call(p, 8, None, 1, 4, 1, 0, p, q, None) == 1       # no queries
+    assert call(p, 2000, p, 1, 4, 1025, 0, p, q, None) == 7    # k > KNN_K_MAX
+    assert call(p, 8, None, 0, 4, 1, 0, None, None, None) == 0  # n = 0: nothing to do
+
+
 def test_binding_mirrors_the_header():
     from paper_0804_1448_gb300 import knn
     for name in declared_functions():
