@@ -46,6 +46,8 @@ PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
 FILTER_TRAFFIC_BYTES = 99.13e6
 FILTER_TRAFFIC_SRC = "f09a4600e257e1b7"
 
+CLOCK_HOLD_S = 0.3
+
 FALLBACK_PEAKS = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}
 
 
@@ -106,6 +108,20 @@ class Clocks:
                  "-lms", "50"], stdout=self.f, stderr=subprocess.DEVNULL)
         except (OSError, FileNotFoundError):
             self.proc = None
+
+    def wait_first(self, limit_s: float = 3.0) -> None:
+        """Return once the sampler has written its first reading (nvidia-smi
+        takes a moment to start), or after limit_s."""
+        if self.proc is None:
+            return
+        t_end = time.monotonic() + limit_s
+        while time.monotonic() < t_end and self.proc.poll() is None:
+            try:
+                if os.path.getsize(self.path) > 0:
+                    return
+            except OSError:
+                return
+            time.sleep(0.01)
 
     def stop(self) -> dict:
         if self.proc is None:
@@ -620,9 +636,19 @@ def main():
         ix.search_into(Qd, k, dist_out, idx_out, "l2", stream)
     ix.sync()
     clocks = Clocks(local)
+    clocks.wait_first()
     total_ms, filt_ms, launches = timed_steps(ix, args.steps, "tc_filter")
-    clock_info = clocks.stop()
     prof = ix.profile()
+    # the timed steps are shorter than the sampling period: the same searches
+    # go on, untimed, for CLOCK_HOLD_S more so that the readings see that load
+    t_hold = time.perf_counter() + CLOCK_HOLD_S
+    while time.perf_counter() < t_hold:
+        flush.fill_(1)
+        ix.search_into(Qd, k, dist_out, idx_out, "l2", stream)
+        torch.cuda.synchronize(dev)
+    clock_info = clocks.stop()
+    clock_info["window"] = (f"sampled every 50 ms from before the timed steps to {CLOCK_HOLD_S} s "
+                            "of the same searches after them")
     ms_step = max_over_ranks(total_ms / args.steps, pg, dev)
     value = world * n / (ms_step / 1e3)
 
