@@ -76,3 +76,15 @@ def test_distance_tolerance_is_relative():
 def test_oracle_k_leaves_room_for_boundary_runs():
     assert parity.oracle_k(20, 38400) == 52
     assert parity.oracle_k(20, 30) == 30
+
+
+def test_recall_and_max_relative_error():
+    o_dist, o_idx, k, m = case(seed=31)
+    assert parity.recall(o_idx[:, :k], o_idx, k) == 1.0
+    g = o_idx[:, :k].copy()
+    g[0, k - 1] = m - 1 if m - 1 not in o_idx[0, :k] else m - 2   # one wrong neighbour in one row
+    assert parity.recall(g, o_idx, k) == pytest.approx(1.0 - 1.0 / (k * g.shape[0]))
+    assert parity.max_rel_err(o_dist[:, :k], o_dist, k) == 0.0
+    d = o_dist[:, :k].copy()
+    d[2, 3] *= 1 + 4e-6
+    assert parity.max_rel_err(d, o_dist, k) == pytest.approx(4e-6, rel=1e-6)
