@@ -263,12 +263,11 @@ knn_status knn_search_self(knn_handle h, int32_t k, knn_metric metric, float* di
 /*
  * The float32 search of knn_search (distance from coordinate differences,
  * float64 re-check of near ties, exact fallback) for callers that cannot
- * allocate device memory when they search: code running while a CUDA graph is
- * being captured (cudaMalloc is not a stream operation and breaks a
- * global-mode capture), frameworks that route every device allocation through
- * their own pool, and latency-critical paths that cannot take the device-wide
- * synchronisation of cudaMalloc/cudaFree.  The paper has no counterpart: it
- * describes the search, not its memory management.
+ * allocate device memory when they search: frameworks that hand out every
+ * device allocation from their own pool (and account for it), and
+ * latency-critical paths that cannot take the device-wide synchronisation of
+ * cudaMalloc/cudaFree.  The paper has no counterpart: it describes the
+ * search, not its memory management.
  *
  * No handle and no allocation: R (m x d), Q (n x d), dist_out and idx_out
  * (n x k) are device pointers on the current device, valid on cuda_stream
@@ -285,9 +284,12 @@ knn_status knn_search_self(knn_handle h, int32_t k, knn_metric metric, float* di
  * by the caller.
  *
  * Errors: KNN_ERR_INVALID (bad argument, k > m), KNN_ERR_UNSUPPORTED when the
- * problem needs more scratch than the array holds (about n * 8 * (k + max(8,
- * k/4)) bytes of candidates plus m * 8 bytes for the exact fallback; e.g.
- * n = m = 38400, d = 96, k = 20 fits) or k > KNN_K_MAX, KNN_ERR_CUDA.
+ * problem needs more scratch than the array holds, or k > KNN_K_MAX,
+ * KNN_ERR_CUDA.  The scratch is n * S * 8 * (k + max(8, k/4)) bytes of
+ * candidates, S being the number of reference splits the float32 search
+ * plans for this n, m, k and the GPU's SM count (1 when the query tiles alone
+ * fill the GPU, more for few queries), plus n * 4 bytes of fallback queue and
+ * m * 8 bytes for the exact fallback.
  */
 knn_status knn_search_static(const float* R, int64_t m, const float* Q, int64_t n, int32_t d,
                              int32_t k, knn_metric metric, float* dist_out, int32_t* idx_out,

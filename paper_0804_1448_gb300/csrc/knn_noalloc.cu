@@ -1,11 +1,10 @@
 // knn_noalloc.cu -- the float32 search with a statically reserved scratch area
 // and no allocation at all (knn_search_static in include/knn.h).
 //
-// Some callers cannot allocate device memory at the moment they search: code
-// that runs while a CUDA graph is being captured (cudaMalloc is not a stream
-// operation and breaks a global-mode capture), frameworks that own every
-// device allocation through their own pool, and latency-bound paths that
-// cannot afford the implicit device synchronisation of cudaMalloc/cudaFree.
+// Some callers cannot allocate device memory at the moment they search:
+// frameworks that hand out every device allocation from their own pool (and
+// account for it), and latency-bound paths that cannot afford the implicit
+// device synchronisation of cudaMalloc/cudaFree.
 // For them this file runs the same three stages as the float32 form of
 // knn_search (fused distance + top-c select, finalize, exact fallback), with
 // every intermediate placed in one file-scope __device__ array.

@@ -56,21 +56,32 @@ def check_row(g_dist, g_idx, o_dist, o_idx, k, m):
 
 
 def compare(g_dist, g_idx, o_dist, o_idx, k, m, max_report=5):
-    """Assert-style check of all rows; returns (n_rows, n_exact_index_rows)."""
+    """Assert-style check of all rows; returns (n_rows, n_exact_index_rows).
+
+    Rows whose k indices equal the oracle's first k, in order, and whose
+    distances are all within REL_DIST pass check_row by construction (every
+    run then holds exactly the oracle's members, the oracle's indices are
+    distinct and in range); they are accepted in one vectorised pass and only
+    the other rows go through check_row."""
     g_dist = np.asarray(g_dist)
     g_idx = np.asarray(g_idx)
+    o_dist = np.asarray(o_dist)
+    o_idx = np.asarray(o_idx)
+    n = g_idx.shape[0]
+    if n == 0:
+        return 0, 0
+    same = np.all(g_idx[:, :k] == o_idx[:, :k], axis=1)
+    err = np.abs(np.asarray(g_dist[:, :k], np.float64) - o_dist[:, :k])
+    close = np.all(err <= REL_DIST * np.abs(o_dist[:, :k]), axis=1)
     errors = []
-    exact = 0
-    for i in range(g_idx.shape[0]):
+    for i in np.nonzero(~(same & close))[0]:
         msg = check_row(g_dist[i], g_idx[i], o_dist[i], o_idx[i], k, m)
         if msg:
-            errors.append(f"row {i}: {msg}")
+            errors.append(f"row {int(i)}: {msg}")
             if len(errors) >= max_report:
                 break
-        if np.array_equal(g_idx[i, :k], o_idx[i, :k]):
-            exact += 1
     assert not errors, "\n".join(errors)
-    return g_idx.shape[0], exact
+    return n, int(np.count_nonzero(same))
 
 
 def oracle_k(k: int, m: int) -> int:
@@ -88,7 +99,33 @@ def max_rel_err(g_dist, o_dist, k):
 
 def recall(g_idx, o_idx, k):
     """Mean fraction of the oracle's k indices present in the returned k."""
-    tot = 0.0
-    for a, b in zip(np.asarray(g_idx)[:, :k], np.asarray(o_idx)[:, :k]):
-        tot += len(set(a.tolist()) & set(b.tolist())) / k
-    return tot / len(g_idx)
+    g = np.sort(np.asarray(g_idx)[:, :k].astype(np.int64), axis=1)
+    o = np.sort(np.asarray(o_idx)[:, :k].astype(np.int64), axis=1)
+    if g.shape[0] == 0:
+        return 1.0
+    # a repeated returned index counts once: repeats become negative values
+    # no oracle index can equal
+    rep = np.zeros_like(g, dtype=bool)
+    rep[:, 1:] = g[:, 1:] == g[:, :-1]
+    g = np.where(rep, -1 - np.arange(k, dtype=np.int64)[None, :], g)
+    # count the common members of each pair of rows by merging them (rows
+    # offset so that values of different rows never meet)
+    off = (np.arange(g.shape[0], dtype=np.int64) * (2 ** 33))[:, None]
+    both = np.concatenate([g + off, o + off], axis=1).ravel()
+    both.sort()
+    common = np.count_nonzero(both[1:] == both[:-1])
+    return common / (k * g.shape[0])
+
+
+# (workload, form) -> (rows checked, recall@k, max relative distance error),
+# filled by the GPU tests and printed at the end of the run by conftest.py
+SUMMARY: dict[str, tuple[int, float, float]] = {}
+
+
+def record(name, g_dist, g_idx, o_dist, o_idx, k):
+    """Store the recall and the largest relative distance error of a checked
+    result under `name`, for the end-of-run summary, and return them."""
+    rec = recall(g_idx, o_idx, k)
+    err = max_rel_err(np.asarray(g_dist), np.asarray(o_dist), k)
+    SUMMARY[name] = (int(np.asarray(g_idx).shape[0]), rec, err)
+    return rec, err

@@ -4,8 +4,9 @@ Every case calls the C ABI through the ctypes binding and compares with the
 oracle element by element under the rule of tests/parity.py.  Shapes span
 several tiles with ragged tails (queries per CTA 64, references per tile 128,
 coordinates per stage 16), k = 1 and k = m, duplicates, lattices full of
-exact ties (which exercise the float64 re-check and the exact fallback), and
-the full n = m = 38400, d = 96 workload checked on sampled queries.
+exact ties (which exercise the float64 re-check and the exact fallback).  The
+full n = m = 38400, d = 96 workload, every row, is in
+tests/test_gpu_fullsize.py.
 """
 import numpy as np
 import pytest
@@ -187,21 +188,6 @@ def test_prefix_property(knn):
         d_k, i_k, _ = run_case(knn, R, Q, k, "l2")
         np.testing.assert_array_equal(i_k, i_big[:, :k])
         np.testing.assert_array_equal(d_k, d_big[:, :k])
-
-
-@pytest.mark.parametrize("metric", ["l2", "l1", "linf"])
-def test_uniform_n38400_d96_k20_sampled(knn, metric):
-    """Full-size Table-1 shape (N = 38400, D = 96, k = 20): all queries run on
-    the GPU in one call; 96 sampled rows are checked against the oracle."""
-    R, Q, k = inputs.workload("uniform_n38400_d96_k20")
-    g_dist, g_idx, st = run_case(knn, R, Q, k, metric)
-    sel = np.random.default_rng(123).choice(Q.shape[0], 96, replace=False)
-    sel[0], sel[1] = 0, Q.shape[0] - 1
-    o_dist, o_idx = oracle.knn_subset(R, Q, sel, parity.oracle_k(k, R.shape[0]), metric)
-    parity.compare(g_dist[sel], g_idx[sel], o_dist, o_idx, k, R.shape[0])
-    # properties that hold for every row
-    assert np.all(np.diff(g_dist, axis=1) >= 0)
-    assert np.all((g_idx >= 0) & (g_idx < R.shape[0]))
 
 
 def test_invalid_arguments(knn):

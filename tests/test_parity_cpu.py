@@ -88,3 +88,30 @@ def test_recall_and_max_relative_error():
     d = o_dist[:, :k].copy()
     d[2, 3] *= 1 + 4e-6
     assert parity.max_rel_err(d, o_dist, k) == pytest.approx(4e-6, rel=1e-6)
+
+
+def test_recall_matches_the_set_definition():
+    """The vectorised recall counts, per row, the returned indices that are
+    among the oracle's k (a repeated index once), as a set intersection does."""
+    rng = np.random.default_rng(5)
+    k, rows = 7, 300
+    o = np.stack([rng.choice(60, k, replace=False) for _ in range(rows)])
+    g = rng.integers(0, 60, size=(rows, k))            # repeats and misses included
+    want = np.mean([len(set(a.tolist()) & set(b.tolist())) / k for a, b in zip(g, o)])
+    assert parity.recall(g, o, k) == pytest.approx(want, abs=1e-12)
+
+
+def test_compare_finds_one_bad_row_among_many():
+    """Rows equal to the oracle take the vectorised path; a planted mistake in
+    one row out of many is still reported, with its row number."""
+    o_dist, o_idx, k, m = case(k=8, m=300, seed=41)
+    reps = 500
+    od = np.tile(o_dist, (reps, 1))
+    oi = np.tile(o_idx, (reps, 1))
+    g_dist = od[:, :k].astype(np.float32).copy()
+    g_idx = oi[:, :k].copy()
+    assert parity.compare(g_dist, g_idx, od, oi, k, m) == (od.shape[0], od.shape[0])
+    bad = 1234
+    g_idx[bad, 0] = next(j for j in range(m) if j not in set(oi[bad, :k + 2].tolist()))
+    with pytest.raises(AssertionError, match=f"row {bad}:"):
+        parity.compare(g_dist, g_idx, od, oi, k, m)

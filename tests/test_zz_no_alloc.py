@@ -1,19 +1,21 @@
 """knn_search_static: the allocation-free entry point (needs a GB300).
 
-Callers that cannot allocate device memory when they search (inside a CUDA
-graph capture, under a framework that owns all allocations, on a
-latency-critical path) use knn_search_static, which keeps its intermediates in
-a fixed 32 MiB __device__ array of the library instead of a handle's
-workspace.  This file checks, through the C ABI, that two calls in a row give
-the same results as the handle-based knn_search, within the parity tolerance
-the other tests use, and that a problem too large for the array is refused.
-It is named to be collected last.
+Callers that cannot allocate device memory when they search (a framework that
+hands out all device memory from its own pool, a latency-critical path that
+cannot take the device-wide synchronisation of cudaMalloc/cudaFree) use
+knn_search_static, which keeps its intermediates in a fixed 32 MiB __device__
+array of the library instead of a handle's workspace.  This file checks,
+through the C ABI, that two calls in a row give the oracle's result under the
+parity rule the other tests use and the same result as the handle-based
+knn_search, and that a problem too large for the array is refused.  It is
+named to be collected last.
 """
 import ctypes
 
 import numpy as np
 import pytest
 
+import oracle
 from paper_0804_1448_gb300 import inputs
 from tests import parity
 
@@ -53,10 +55,12 @@ def test_two_calls_match_knn_search(env, metric):
         Qd = torch.from_numpy(Q).cuda()
         k = 16
         s_dist, s_idx = static_search(torch, knn, Rd, Qd, k, metric)
+        o_dist, o_idx = oracle.knn(R, Q, parity.oracle_k(k, R.shape[0]), metric)
+        parity.compare(s_dist, s_idx, o_dist, o_idx, k, R.shape[0])
         h_dist, h_idx = ix.search(Qd, k, metric)
         torch.cuda.synchronize()
         h_dist, h_idx = h_dist.cpu().numpy(), h_idx.cpu().numpy()
-        # the handle-based result plays the oracle's role here: same rule and tolerance
+        # and the result of the existing entry point, under the same rule
         parity.compare(s_dist, s_idx, h_dist.astype(np.float64), h_idx, k, R.shape[0])
     ix.close()
 
