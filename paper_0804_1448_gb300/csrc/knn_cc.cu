@@ -4,9 +4,14 @@
 // and the r_j) fused with steps 2-3 (sort, keep the smallest): a CTA owns
 // ROWS queries and streams the references of its split through shared memory
 // in tiles of TM; each thread accumulates an RR x CN register micro-tile of
-// distances over the d coordinates; the finished tile goes to shared memory and
-// one thread per query pushes it through that query's bounded max-heap of c
-// candidates.  Only the c survivors per (query, split) are written out.
+// distances over the d coordinates; the finished tile goes to shared memory.
+// Selection is warp-level: every thread of the CTA tests its share of one
+// query row's tile against that row's current threshold (the largest key of
+// the row's bounded max-heap of c candidates), the pass bits of a row are
+// gathered by warp shuffles into the row's leader lane, and the leader inserts
+// only the passing distances.  After the first tiles almost nothing passes,
+// so the serial part of the selection shrinks to the rare insertions.  Only
+// the c survivors per (query, split) are written out.
 //
 // Distances are formed from coordinate differences in float32, coordinate 0
 // first: Euclidean sum_t fma(q_t - r_t, q_t - r_t, acc) (the squared
@@ -21,16 +26,35 @@ constexpr int kThreads = 256;
 constexpr int kDK = 16;    // coordinates per shared-memory stage
 constexpr int kTM = 128;   // references per tile
 
+// CTA shapes: TY x TX threads, each an RR (queries) x CN (references)
+// micro-tile whose references come in groups of G consecutive columns;
+// MINB CTAs per SM (the register bound).  The 128-row shape loads 16 floats
+// from shared memory per 64 distance terms (the 64-row one 12 per 32), which
+// is what bounds the arithmetic at large n; the 16-row shape leaves room for
+// the heaps of large c.
 template <int ROWS>
 struct CCShape;
 template <>
+struct CCShape<128> {      // 16 x 16 threads, 8 queries x 8 references each
+    static constexpr int TY = 16, TX = 16, RR = 8, CN = 8, G = 4, MINB = 2;
+};
+template <>
 struct CCShape<64> {       // 16 x 16 threads, 4 queries x 8 references each
-    static constexpr int TY = 16, TX = 16, RR = 4, CN = 8, G = 4;
+    static constexpr int TY = 16, TX = 16, RR = 4, CN = 8, G = 4, MINB = 3;
 };
 template <>
 struct CCShape<16> {       // 4 x 64 threads, 4 queries x 2 references each
-    static constexpr int TY = 4, TX = 64, RR = 4, CN = 2, G = 2;
+    static constexpr int TY = 4, TX = 64, RR = 4, CN = 2, G = 2, MINB = 3;
 };
+
+// Row pitch of the finished distance tile (floats).  The selection reads it
+// 16 bytes per thread with TPR = kThreads / ROWS threads per row at 16-byte
+// strides; a quarter warp then spans 8 / TPR rows, and a pitch of 4 TPR
+// (mod 32) banks puts them on distinct banks.
+template <int ROWS>
+constexpr int cc_dst() {
+    return (kThreads / ROWS) <= 4 ? kTM + 4 * (kThreads / ROWS) : kTM + 4;
+}
 
 // Shared memory: the two coordinate-stage buffers (queries and references)
 // and the finished distance tile use the same space, one after the other;
@@ -41,9 +65,9 @@ constexpr size_t cc_stage_bytes() {
 }
 template <int ROWS>
 constexpr size_t cc_union_bytes() {
-    return cc_stage_bytes<ROWS>() > sizeof(float) * ROWS * (kTM + 1)
+    return cc_stage_bytes<ROWS>() > sizeof(float) * ROWS * cc_dst<ROWS>()
                ? cc_stage_bytes<ROWS>()
-               : sizeof(float) * ROWS * (kTM + 1);
+               : sizeof(float) * ROWS * cc_dst<ROWS>();
 }
 template <int ROWS>
 constexpr size_t cc_smem_bytes(int c) {
@@ -51,10 +75,9 @@ constexpr size_t cc_smem_bytes(int c) {
 }
 
 // Max-heap (largest key at slot 0) of c keys, slot-major with stride ROWS.
-// Replace the top by `key` (key < top) and sift down.
+// Place `key` at slot i, whose subtrees are heaps, and sift it down.
 template <int ROWS>
-__device__ __forceinline__ void heap_replace_top(uint64_t* h, int c, uint64_t key) {
-    int i = 0;
+__device__ __forceinline__ void heap_sift_down(uint64_t* h, int c, int i, uint64_t key) {
     while (true) {
         int l = 2 * i + 1;
         if (l >= c) break;
@@ -69,6 +92,16 @@ __device__ __forceinline__ void heap_replace_top(uint64_t* h, int c, uint64_t ke
         i = bi;
     }
     h[i * ROWS] = key;
+}
+// Replace the top by `key` (key < top).
+template <int ROWS>
+__device__ __forceinline__ void heap_replace_top(uint64_t* h, int c, uint64_t key) {
+    heap_sift_down<ROWS>(h, c, 0, key);
+}
+// Make slots 0..c-1 (any order) a heap (Floyd's bottom-up construction).
+template <int ROWS>
+__device__ __forceinline__ void heapify(uint64_t* h, int c) {
+    for (int i = c / 2 - 1; i >= 0; --i) heap_sift_down<ROWS>(h, c, i, h[i * ROWS]);
 }
 
 // Two float32 lanes: (a, a) - (b0, b1), the difference of one query
@@ -96,20 +129,23 @@ __device__ __forceinline__ float pair_hi(uint64_t v) { return __uint_as_float(st
 // are in flight during the arithmetic; two shared-memory buffers alternate,
 // and one barrier per step separates the writes of a buffer from the reads of
 // the step before.  A finished tile's distances take the buffers' place until
-// the selector threads have consumed them (two more barriers per tile).
+// the selection has consumed them (two more barriers per tile).
 // Euclidean sums run as two-lane float32 instructions (sub, fma): per lane
 // the same operations, in the same order, as the scalar form.
 template <int METRIC, int ROWS>
-__global__ void __launch_bounds__(kThreads, 3)
+__global__ void __launch_bounds__(kThreads, CCShape<ROWS>::MINB)
 cc_select_kernel(const float* __restrict__ Q, int64_t n, const float* __restrict__ R,
                  int64_t m, int32_t d, CandidateSet cand) {
     using S = CCShape<ROWS>;
     static_assert(S::TY * S::TX == kThreads, "thread shape");
     static_assert(S::TY * S::RR == ROWS && S::TX * S::CN == kTM, "tile shape");
-    static_assert(S::CN % 2 == 0 && S::G % 2 == 0, "column pairs");
+    static_assert(S::CN % 2 == 0 && S::G % 2 == 0 && S::RR % 4 == 0, "column pairs, row quads");
     constexpr int QST = ROWS + 4;      // padded strides (bank spread)
     constexpr int RST = kTM + 4;
-    constexpr int DST = kTM + 1;
+    constexpr int DST = cc_dst<ROWS>();
+    constexpr int TPR = kThreads / ROWS;         // selection threads per query row
+    constexpr int VPT = kTM / (4 * TPR);         // float4s of the tile per selection thread
+    static_assert(TPR <= 32 && 32 % TPR == 0 && VPT * 4 <= 64, "selection shape");
     constexpr int QPT = ROWS * kDK / kThreads;   // query values per thread and step
     constexpr int RPT = kTM * kDK / kThreads;    // reference values per thread and step
     constexpr int CP = S::CN / 2;
@@ -132,8 +168,20 @@ cc_select_kernel(const float* __restrict__ Q, int64_t n, const float* __restrict
     const int steps = tiles * stages;
 
     for (int e = tid; e < c * ROWS; e += kThreads) heap[e] = kEmptyKey;
-    uint64_t top = kEmptyKey;  // cached heap[0] of this thread's row (selector threads)
-    float top_d = __int_as_float(0x7f800000);   // its distance (+inf while the heap has room)
+    // selection roles: thread tid tests row srow of a finished tile; the lane
+    // with ssub == 0 (the row's leader) owns the row's heap and keeps its
+    // largest key and that key's distance (+inf while the heap has room).
+    // Until the heap holds c keys they are appended unordered (slots 0..fill-1)
+    // and the c-th makes it a heap at once: the first tile's keys, which all
+    // pass, cost one store each instead of a sift each.  The finalize reads a
+    // split's keys as a set, so a heap left short (a split of fewer than c
+    // references) needs no order.
+    const int srow = tid / TPR, ssub = tid % TPR;
+    const bool leader = ssub == 0;
+    const bool srow_live = qbase + srow < n;
+    uint64_t top = kEmptyKey;
+    float top_d = __int_as_float(0x7f800000);
+    int fill = 0;
 
     float pq[QPT], pr[RPT];
     auto fetch = [&](int h) {
@@ -184,8 +232,11 @@ cc_select_kernel(const float* __restrict__ Q, int64_t n, const float* __restrict
 #pragma unroll 4
         for (int t = 0; t < kDK; ++t) {
             float qv[S::RR], rv[S::CN];
-            const float4 q4 = *reinterpret_cast<const float4*>(&qs[t * QST + ty * S::RR]);
-            qv[0] = q4.x; qv[1] = q4.y; qv[2] = q4.z; qv[3] = q4.w;
+#pragma unroll
+            for (int i = 0; i < S::RR; i += 4) {
+                const float4 q4 = *reinterpret_cast<const float4*>(&qs[t * QST + ty * S::RR + i]);
+                qv[i] = q4.x; qv[i + 1] = q4.y; qv[i + 2] = q4.z; qv[i + 3] = q4.w;
+            }
 #pragma unroll
             for (int g = 0; g < S::CN / S::G; ++g) {
                 const float* src = &rs[t * RST + g * S::TX * S::G + tx * S::G];
@@ -222,40 +273,82 @@ cc_select_kernel(const float* __restrict__ Q, int64_t n, const float* __restrict
         const int64_t tbase = r_begin + static_cast<int64_t>(h / stages) * kTM;
         __syncthreads();
 #pragma unroll
-        for (int i = 0; i < S::RR; ++i)
+        for (int i = 0; i < S::RR; ++i) {
+            float* drow = Dt + (ty * S::RR + i) * DST;
 #pragma unroll
-            for (int j = 0; j < S::CN; ++j) {
-                const int col = (j / S::G) * (S::TX * S::G) + tx * S::G + (j % S::G);
-                float v;
-                if constexpr (METRIC == kL2) v = (j & 1) ? pair_hi(acc2[i][j / 2]) : pair_lo(acc2[i][j / 2]);
-                else v = acc[i][j];
-                Dt[(ty * S::RR + i) * DST + col] = v;
-                acc[i][j] = 0.f;
+            for (int g = 0; g < S::CN / S::G; ++g) {
+                const int col = g * (S::TX * S::G) + tx * S::G;
+                if constexpr (METRIC == kL2) {
+                    const uint64_t p0 = acc2[i][g * S::G / 2];
+                    const uint64_t p1 = acc2[i][(g * S::G / 2 + 1) % CP];
+                    if constexpr (S::G == 4)
+                        *reinterpret_cast<float4*>(drow + col) =
+                            make_float4(pair_lo(p0), pair_hi(p0), pair_lo(p1), pair_hi(p1));
+                    else
+                        *reinterpret_cast<float2*>(drow + col) = make_float2(pair_lo(p0), pair_hi(p0));
+                } else {
+                    if constexpr (S::G == 4)
+                        *reinterpret_cast<float4*>(drow + col) =
+                            make_float4(acc[i][g * 4], acc[i][g * 4 + 1], acc[i][g * 4 + 2], acc[i][g * 4 + 3]);
+                    else
+                        *reinterpret_cast<float2*>(drow + col) = make_float2(acc[i][g * 2], acc[i][g * 2 + 1]);
+                }
             }
 #pragma unroll
-        for (int i = 0; i < S::RR; ++i)
+            for (int j = 0; j < S::CN; ++j) acc[i][j] = 0.f;
 #pragma unroll
             for (int j = 0; j < CP; ++j) acc2[i][j] = 0ull;
+        }
         __syncthreads();
-        // one thread per query row streams the tile through the row's heap;
-        // a distance above the heap's largest cannot enter it (four columns
-        // read ahead, so their loads overlap)
-        if (tid < ROWS && qbase + tid < n) {
-            uint64_t* hp = heap + tid;
+        // selection.  Thread (srow, ssub) tests the float4s ssub, ssub + TPR,
+        // ... of row srow against the row's current largest distance (from
+        // the leader: a stale, larger value only lets more through) and sets
+        // bit 4v + e of its mask for element e of its v-th float4 when it may
+        // enter the heap.  The leader gathers the TPR masks and inserts.
+        {
             const int cols = static_cast<int>(min(static_cast<int64_t>(kTM), r_end - tbase));
-            const float* drow = Dt + tid * DST;
-            for (int c0 = 0; c0 < cols; c0 += 4) {
-                float v[4];
+            const int lead_lane = (tid & 31) & ~(TPR - 1);
+            const float thr = __shfl_sync(0xffffffffu, top_d, lead_lane);
+            const float* drow = Dt + srow * DST;
+            uint64_t mask = 0ull;
 #pragma unroll
-                for (int u = 0; u < 4; ++u) v[u] = (c0 + u < cols) ? drow[c0 + u] : top_d;
+            for (int v = 0; v < VPT; ++v) {
+                const int c0 = 4 * (v * TPR + ssub);
+                const float4 x = *reinterpret_cast<const float4*>(drow + c0);
+                const uint32_t b = ((x.x <= thr && c0 + 0 < cols) ? 1u : 0u) |
+                                   ((x.y <= thr && c0 + 1 < cols) ? 2u : 0u) |
+                                   ((x.z <= thr && c0 + 2 < cols) ? 4u : 0u) |
+                                   ((x.w <= thr && c0 + 3 < cols) ? 8u : 0u);
+                mask |= static_cast<uint64_t>(b) << (4 * v);
+            }
+            if (!srow_live) mask = 0ull;
+            uint64_t sub_mask[TPR];
 #pragma unroll
-                for (int u = 0; u < 4; ++u) {
-                    if (c0 + u < cols && v[u] <= top_d) {
-                        const uint64_t key = make_key(v[u], static_cast<uint32_t>(tbase + c0 + u));
-                        if (key < top) {
-                            heap_replace_top<ROWS>(hp, c, key);
-                            top = hp[0];
-                            top_d = top == kEmptyKey ? __int_as_float(0x7f800000) : key_dist(top);
+            for (int u = 0; u < TPR; ++u) sub_mask[u] = __shfl_sync(0xffffffffu, mask, lead_lane + u);
+            if (leader) {
+                uint64_t* hp = heap + srow;
+#pragma unroll
+                for (int u = 0; u < TPR; ++u) {
+                    uint64_t bits = sub_mask[u];
+                    while (bits) {
+                        const int b = __ffsll(static_cast<long long>(bits)) - 1;
+                        bits &= bits - 1;
+                        const int col = 4 * ((b >> 2) * TPR + u) + (b & 3);
+                        const float v = drow[col];
+                        if (fill < c) {
+                            hp[fill * ROWS] = make_key(v, static_cast<uint32_t>(tbase + col));
+                            if (++fill == c) {
+                                heapify<ROWS>(hp, c);
+                                top = hp[0];
+                                top_d = key_dist(top);
+                            }
+                        } else if (v <= top_d) {
+                            const uint64_t key = make_key(v, static_cast<uint32_t>(tbase + col));
+                            if (key < top) {
+                                heap_replace_top<ROWS>(hp, c, key);
+                                top = hp[0];
+                                top_d = key_dist(top);
+                            }
                         }
                     }
                 }
@@ -287,18 +380,37 @@ cudaError_t launch_rows(const float* Q, int64_t n, const float* R, int64_t m, in
 constexpr size_t kSmemCap = 220 * 1024;
 constexpr size_t kSmemPerSm = 233472;   // shared memory of one SM
 constexpr size_t kSmemPerCta = 1024;    // reserved by the hardware per resident CTA
-constexpr int kMaxResident = 3;         // CTAs per SM the register bound allows
+constexpr int64_t kWideRowsMinN = 8192; // 128-row CTAs only for query sets this large
+
+// The CTA shape (queries per CTA) for n queries and c candidates, and the
+// CTAs of it one SM holds: 128 rows when n is large and their heaps leave
+// room for two CTAs per SM, else 64 when the shape fits, else 16.
+int cc_rows(int64_t n, int32_t c, int64_t* per_sm) {
+    int rows = 16;
+    size_t smem = cc_smem_bytes<16>(c);
+    int minb = CCShape<16>::MINB;
+    if (n >= kWideRowsMinN && 2 * (cc_smem_bytes<128>(c) + kSmemPerCta) <= kSmemPerSm) {
+        rows = 128;
+        smem = cc_smem_bytes<128>(c);
+        minb = CCShape<128>::MINB;
+    } else if (cc_smem_bytes<64>(c) <= kSmemCap) {
+        rows = 64;
+        smem = cc_smem_bytes<64>(c);
+        minb = CCShape<64>::MINB;
+    }
+    int64_t k = static_cast<int64_t>(kSmemPerSm / (smem + kSmemPerCta));
+    if (k > minb) k = minb;
+    if (k < 1) k = 1;
+    *per_sm = k;
+    return rows;
+}
 
 }  // namespace
 
 int cc_plan_splits(int64_t n, int64_t m, int32_t c, int num_sms, int max_pool,
                    int64_t* chunk_out) {
-    const bool wide = cc_smem_bytes<64>(c) <= kSmemCap;
-    const int64_t rows = wide ? 64 : 16;
-    const size_t smem = wide ? cc_smem_bytes<64>(c) : cc_smem_bytes<16>(c);
-    int64_t per_sm = static_cast<int64_t>(kSmemPerSm / (smem + kSmemPerCta));
-    if (per_sm > kMaxResident) per_sm = kMaxResident;
-    if (per_sm < 1) per_sm = 1;
+    int64_t per_sm = 1;
+    const int64_t rows = cc_rows(n, c, &per_sm);
     const int64_t sms = num_sms > 0 ? num_sms : 1;
     const int64_t slots = per_sm * sms;
     const int64_t tiles = n > 0 ? (n + rows - 1) / rows : 1;
@@ -319,9 +431,11 @@ int cc_plan_splits(int64_t n, int64_t m, int32_t c, int num_sms, int max_pool,
     };
     // The estimate takes a lone CTA on an SM to run as fast as the SM's full
     // share, which holds for long chunks only; when the query tiles give
-    // fewer than two CTAs per SM, at least enough splits for two are taken.
+    // fewer than two CTAs per SM (one per SM for the one-CTA shapes), with 5%
+    // slack, at least enough splits for two are taken.
     int64_t s_min = 1;
-    if (tiles < 2 * sms) s_min = (2 * sms + tiles - 1) / tiles;
+    const int64_t want = (per_sm < 2 ? per_sm : 2) * sms;
+    if (tiles * 100 < want * 95) s_min = (want + tiles - 1) / tiles;
     if (s_min > s_cap) s_min = s_cap;
     double best = cost(s_min);
     for (int64_t S = s_min + 1; S <= s_cap; ++S) best = best < cost(S) ? best : cost(S);
@@ -341,17 +455,21 @@ int cc_max_candidates() {
 cudaError_t launch_cc_select(const float* Q, int64_t n, const float* R, int64_t m, int32_t d,
                              int32_t metric, const CandidateSet& cand, cudaStream_t st,
                              int* launches) {
-    const bool wide = cc_smem_bytes<64>(cand.c) <= kSmemCap;
-    if (!wide && cc_smem_bytes<16>(cand.c) > kSmemCap) return cudaErrorInvalidValue;
+    int64_t per_sm = 1;
+    const int rows = cc_rows(n, cand.c, &per_sm);
+    if (rows == 16 && cc_smem_bytes<16>(cand.c) > kSmemCap) return cudaErrorInvalidValue;
     if (launches) ++*launches;
     if (metric == kL2)
-        return wide ? launch_rows<kL2, 64>(Q, n, R, m, d, cand, st)
-                    : launch_rows<kL2, 16>(Q, n, R, m, d, cand, st);
+        return rows == 128 ? launch_rows<kL2, 128>(Q, n, R, m, d, cand, st)
+               : rows == 64 ? launch_rows<kL2, 64>(Q, n, R, m, d, cand, st)
+                            : launch_rows<kL2, 16>(Q, n, R, m, d, cand, st);
     if (metric == kL1)
-        return wide ? launch_rows<kL1, 64>(Q, n, R, m, d, cand, st)
-                    : launch_rows<kL1, 16>(Q, n, R, m, d, cand, st);
-    return wide ? launch_rows<kLinf, 64>(Q, n, R, m, d, cand, st)
-                : launch_rows<kLinf, 16>(Q, n, R, m, d, cand, st);
+        return rows == 128 ? launch_rows<kL1, 128>(Q, n, R, m, d, cand, st)
+               : rows == 64 ? launch_rows<kL1, 64>(Q, n, R, m, d, cand, st)
+                            : launch_rows<kL1, 16>(Q, n, R, m, d, cand, st);
+    return rows == 128 ? launch_rows<kLinf, 128>(Q, n, R, m, d, cand, st)
+           : rows == 64 ? launch_rows<kLinf, 64>(Q, n, R, m, d, cand, st)
+                        : launch_rows<kLinf, 16>(Q, n, R, m, d, cand, st);
 }
 
 }  // namespace knn
