@@ -61,7 +61,10 @@ typedef enum { KNN_L2 = 0, KNN_L1 = 1, KNN_LINF = 2, KNN_MAHALANOBIS = 3 } knn_m
  *             differences.  Manhattan and Chebyshev distances ignore this
  *             setting and run in KNN_FP32, and so do Euclidean searches
  *             whose rows do not fit the tensor-core tile in shared memory
- *             (d above 444 in bf16, above 220 in tf32).
+ *             (d above 444 in bf16, above 220 in tf32) and searches of
+ *             reference sets too small for the tensor-core pilot (m below
+ *             about 2800 at k = 20, at most 4096), where the exact float32
+ *             form is the faster one.
  * In every mode, candidates whose float32 distances lie within the float32
  * rounding bound of each other around the returned list are re-checked on the
  * GPU (a float-float sum, and the oracle's float64 arithmetic where that
@@ -181,6 +184,10 @@ typedef struct {
     int32_t list_capacity;      /* hit-list entries per query, split and column group */
     int32_t fallback_slots;     /* scratch rows of the exact fallback */
     int64_t workspace_bytes;    /* device workspace of the search (device I/O) */
+    int32_t small_select;       /* float32: 1 when each query's m distances are held in
+                                   shared memory and the c nearest selected exactly (small
+                                   reference sets; the tensor-core forms take this path
+                                   too when their pilot would not run) */
 } knn_plan;
 
 knn_status knn_explain_plan(int64_t n, int64_t m, int32_t d, int32_t k, knn_metric metric,

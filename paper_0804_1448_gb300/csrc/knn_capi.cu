@@ -280,6 +280,8 @@ void stage(knn_ctx* h, cudaStream_t st, const char* name) {
 // candidate count, the reference splits and the workspace layout.
 struct SearchPlan {
     bool tensor = false;
+    bool small = false;      // float32: all m distances per query in shared memory (knn_small.cu)
+    int c_need = 0;          // small: the nearest keys a query must keep (c slots, c >= c_need)
     int prec = 0;
     int kp = 0;
     int c = 0;
@@ -319,11 +321,20 @@ knn_status plan_search_md(const knn_ctx* h, int64_t m, int32_t d, int precision,
     if (p.tensor) {
         p.kp = tc_padded_dim(d, p.prec);
         p.plan = tc_plan(n, m, d, p.kp, p.prec, p.c, sm_share);
-        if (p.plan.stages == 0)   // rows too long for the tile: the float32 form
+        // rows too long for the tile, or a reference set too small for the
+        // pilot (every reference would be appended to the lists): the float32
+        // form, whose small-set select handles the latter faster and exactly
+        if (p.plan.stages == 0 || (!p.plan.pilot && small_select_fits(m, d)))
             return plan_search_md(h, m, d, KNN_FP32, n, k, metric, io_on_device, sm_share, sp,
                                   fb_cap_bytes);
         p.S = p.plan.S;
         p.chunk = p.plan.chunk;
+    } else if (small_select_fits(m, d)) {
+        p.small = true;
+        p.c_need = p.c;
+        p.c = static_cast<int>(std::min<int64_t>(m, p.c + kSmallSelectSpare));
+        p.S = 1;
+        p.chunk = m;
     } else {
         int64_t chunk = 0;
         const int S = cc_plan_splits(n, m, p.c, sm_share, finalize_max_pool(), &chunk);
@@ -440,8 +451,13 @@ knn_status enqueue_search(knn_ctx* h, const SearchPlan& sp, const RefView& rv, c
         cs.c = c;
         cs.chunk = sp.chunk;
         cs.exact = 1;
-        KNN_CUDA(h, launch_cc_select(Qd, n, rv.R, m, d, metric, cs, st, l));
-        mark("cc_select");
+        if (sp.small) {
+            KNN_CUDA(h, launch_small_select(Qd, n, rv.R, m, d, metric, sp.c_need, cs, st, l));
+            mark("small_select");
+        } else {
+            KNN_CUDA(h, launch_cc_select(Qd, n, rv.R, m, d, metric, cs, st, l));
+            mark("cc_select");
+        }
         fa.use_hits = 0;
         fa.cand = cs;
     }
@@ -1139,6 +1155,7 @@ knn_status knn_explain_plan(int64_t n, int64_t m, int32_t d, int32_t k, knn_metr
     }
     o.fallback_slots = static_cast<int32_t>(sp.fb_grid);
     o.workspace_bytes = static_cast<int64_t>(sp.bytes);
+    o.small_select = sp.small ? 1 : 0;
     *out = o;
     return KNN_OK;
 }

@@ -144,6 +144,21 @@ cudaError_t launch_cc_select(const float* Q, int64_t n, const float* R, int64_t 
 // The largest c launch_cc_select supports.
 int cc_max_candidates();
 
+// Float32 select for small reference sets (knn_small.cu): one warp per query
+// holds all m distances in shared memory and selects exactly a set of keys
+// that holds its c_need nearest and that no key left out precedes, of at most
+// cand.c (>= c_need) keys, the unused slots empty.  Writes cand with S = 1
+// split of the whole set (exact = 1).  Available when small_select_fits(m, d):
+// m up to kSmallSelectMaxM and the shared memory (small_select_smem) within
+// one CTA's.  kSmallSelectSpare: the spare slots a search plans beyond c_need.
+constexpr int64_t kSmallSelectMaxM = 4096;
+constexpr int kSmallSelectSpare = 16;
+size_t small_select_smem(int64_t m, int32_t d);
+bool small_select_fits(int64_t m, int32_t d);
+cudaError_t launch_small_select(const float* Q, int64_t n, const float* R, int64_t m, int32_t d,
+                                int32_t metric, int32_t c_need, const CandidateSet& cand,
+                                cudaStream_t st, int* launches);
+
 // Reference splits S of the float32 search and their length *chunk (a
 // multiple of 128): among the S with every split at least 8c long and S*c
 // within max_pool, and at least two CTAs per SM where that is possible, the

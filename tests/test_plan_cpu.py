@@ -32,19 +32,21 @@ def test_bench_shape():
 @pytest.mark.parametrize("D", [8, 16, 32, 64, 80, 96])
 def test_table1_grid_invariants(N, D):
     p = plan(N, N, D, 20)
-    assert p["tensor_cores"] == 1
+    if N < 4800:
+        # too few groups for the pilot even at stride 1: the exact float32
+        # small-set select (all N distances of a query in shared memory)
+        assert p["tensor_cores"] == 0 and p["small_select"] == 1
+        assert p["splits"] == 1 and p["chunk"] == N and p["candidates"] == 28 + 16
+        return
+    assert p["tensor_cores"] == 1 and p["small_select"] == 0
     assert p["chunk"] % 256 == 0 and p["splits"] * p["chunk"] >= N
     assert (p["splits"] - 1) * p["chunk"] < N                 # no empty split
     assert 1 <= p["splits"] <= 256
     assert p["list_capacity"] % 32 == 0
-    if N >= 4800:
-        assert p["pilot"] == 1
-        assert p["pilot_groups"] <= 2048
-        # the c'-th largest of the group maxima needs groups to spare
-        assert p["pilot_groups"] >= p["threshold_rank"] + 8
-    else:
-        assert p["pilot"] == 0                                 # too few groups even at stride 1
-        assert p["list_capacity"] * 4 * p["splits"] >= N       # every reference fits a list
+    assert p["pilot"] == 1
+    assert p["pilot_groups"] <= 2048
+    # the c'-th largest of the group maxima needs groups to spare
+    assert p["pilot_groups"] >= p["threshold_rank"] + 8
 
 
 @pytest.mark.parametrize("n", [1, 64, 256])
@@ -108,7 +110,7 @@ def test_fp32_long_reference_set_is_split():
     assert p["candidates"] == 125 and p["splits"] == 7
 
 
-@pytest.mark.parametrize("N,S", [(1200, 5), (2400, 7), (4800, 6), (9600, 6), (19200, 3), (38400, 1)])
+@pytest.mark.parametrize("N,S", [(4800, 6), (9600, 6), (19200, 3), (38400, 1)])
 def test_fp32_table1_splits(N, S):
     # at least two CTAs per SM where the query tiles alone give fewer (with
     # 5% slack); query tiles of 64 rows below 8192 queries, of 128 above
@@ -127,7 +129,23 @@ def test_fp32_table1_splits(N, S):
 def test_fp32_split_invariants(n, m, k):
     p = fp32(n, m, 24, k)
     S, chunk, c = p["splits"], p["chunk"], p["candidates"]
+    if p["small_select"]:                                               # one split of the whole set
+        assert S == 1 and chunk == m and c <= m
+        return
     assert chunk % 128 == 0 and S * chunk >= m and (S - 1) * chunk < m   # no empty split
     assert S * c <= 4096                                                 # one finalize pool
     if S > 1:
         assert chunk >= 8 * c - 127                                     # splits much longer than c
+
+
+@pytest.mark.parametrize("m,d,small", [(1200, 8, 1), (4096, 96, 1), (4097, 96, 0), (4096, 256, 1),
+                                       (4096, 444, 0), (2000, 200, 1)])
+def test_small_reference_sets_use_the_small_select(m, d, small):
+    """Reference sets of at most 4096 points whose distances, eight query rows
+    of them, fit one CTA's shared memory take the small-set select (one split
+    of k + max(8, k/4) keys per query and 16 spare slots); larger ones the
+    tiled select."""
+    p = fp32(300, m, d, 20)
+    assert p["small_select"] == small and p["tensor_cores"] == 0
+    if small:
+        assert p["splits"] == 1 and p["chunk"] == m and p["candidates"] == 28 + 16
