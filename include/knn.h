@@ -359,20 +359,37 @@ typedef struct {
                                  configurations and keep the fastest (slower first call) */
 #define KNN_BATCH_NO_GRAPH 2  /* enqueue the instances one after another, each planned
                                  as a lone search (the one-launch-per-instance form) */
+#define KNN_BATCH_BRANCHES 4  /* a CUDA graph of the instances' own launches on parallel
+                                 branches instead of the persistent kernel */
 
 /*
  * Search every instance of inst[0..count) with the handle's precision and
  * re-rank factor (the handle's own reference set is not used), results as in
  * knn_search.  All pointers are device pointers; the call only enqueues work
  * on cuda_stream (NULL = the handle's stream) and returns (asynchronous).
- * The instances are planned together, given workspace slices of their own,
- * and captured into one CUDA graph whose parallel branches run them side by
- * side (largest first onto the least loaded branch); the graph is cached, so
- * a repeated batch (same shapes and pointers) is one cudaGraphLaunch.  The
- * launch configuration (branches, SMs each instance is planned to fill) is
- * the tuned one for this batch shape when KNN_BATCH_AUTOTUNE found one, else
- * a default (8 branches, a quarter of the SMs each).  Growing the workspace
- * drops the cached graphs (they point into it).
+ *
+ * Tensor-core precisions with every instance Euclidean (the persistent form):
+ * the whole batch is ONE kernel launch.  One CTA per SM stays resident and
+ * pops work items -- (instance, stage, query tile or rows, reference split) --
+ * from a queue in device memory: for every instance its operand copies, pilot,
+ * per-query threshold, tensor-core filter, finalize and exact fallback, the
+ * items of each stage after those of the stage before (a per-instance
+ * counter, waited for with a bound).  The reference-split length of the
+ * filter and pilot items is, per (d, k) bucket of the batch, the one
+ * KNN_BATCH_AUTOTUNE found fastest for this batch shape (else the planner's
+ * own choice).  The launch and its counter resets are captured in a CUDA
+ * graph, cached by the batch's exact signature (shapes and pointers), so a
+ * repeated batch is one cudaGraphLaunch; growing the workspace drops cached
+ * graphs (they point into it).  A wait of the kernel that gives up raises the
+ * handle's error flag (KNN_ERR_TIMEOUT from knn_sync).
+ *
+ * Otherwise (float32, another distance in the batch, or KNN_BATCH_BRANCHES):
+ * the instances are planned together, given workspace slices of their own,
+ * and their launches captured into one CUDA graph whose parallel branches run
+ * them side by side (largest first onto the least loaded branch); the
+ * configuration (branches, SMs each instance is planned to fill) is the one
+ * KNN_BATCH_AUTOTUNE found for this batch shape, else a default (8 branches,
+ * a quarter of the SMs each).
  * Errors: KNN_ERR_INVALID (h NULL, count < 0, inst NULL with count > 0, an
  * instance with a null pointer, m < 1, d < 1, k < 1, k > m or a bad metric),
  * KNN_ERR_UNSUPPORTED (k > KNN_K_MAX), KNN_ERR_OOM, KNN_ERR_CUDA.
@@ -388,9 +405,23 @@ typedef struct {
     int64_t graph_nodes;    /* nodes of its graph (0 without a graph) */
     int32_t tuned;          /* 1 if that call ran the autotuner */
     double tune_ms;         /* device time the autotuner spent */
+    int32_t persistent;     /* 1: the batch ran as one persistent kernel launch */
+    int32_t items;          /* persistent: work items in its queue */
 } knn_batch_info;
 
 knn_status knn_batch_info_get(knn_handle h, knn_batch_info* out);
+
+/*
+ * Self-test of the persistent batch kernel's bounded waits: enqueues on the
+ * handle's stream one launch of the persistent kernel on a one-instance batch
+ * whose "ready" word is withheld (the host never sets it), so every CTA's
+ * first wait gives up after limit_ms (1..1000), raises the handle's error
+ * flag and leaves without touching the batch; then does knn_sync.  Returns
+ * KNN_ERR_TIMEOUT when the detection works; the handle stays usable.  No
+ * fault, trap or hang is involved.  Errors: KNN_ERR_INVALID, KNN_ERR_OOM,
+ * KNN_ERR_CUDA.
+ */
+knn_status knn_selftest_batch_queue(knn_handle h, int32_t limit_ms);
 
 /* Release the handle and everything it owns.  NULL is accepted. */
 knn_status knn_destroy(knn_handle h);

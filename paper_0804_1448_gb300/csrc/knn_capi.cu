@@ -13,6 +13,7 @@
 #include <string>
 
 #include "../../include/knn.h"
+#include "knn_batch.cuh"
 #include "knn_internal.cuh"
 
 using namespace knn;
@@ -84,9 +85,13 @@ struct knn_ctx {
         int sm_share = 0;
         int launches = 0;
         size_t nodes = 0;
+        PersistBatch pb{};     // the persistent form: its descriptors (owned)
+        bool persistent = false;
     };
     std::map<uint64_t, BatchGraph> graphs;
     std::map<uint64_t, std::pair<int, int>> tuned;   // shape -> (branches, sm_share)
+    // persistent form: shape -> reference-split length per (d, k) bucket
+    std::map<uint64_t, std::map<uint64_t, int64_t>> tuned_chunks;
     cudaStream_t cap_stream = nullptr;
     cudaStream_t branch[16] = {};
     cudaEvent_t fork_ev = nullptr, join_ev[16] = {}, t_ev[2] = {};
@@ -125,8 +130,10 @@ bool fault_inject_oom() {
 }
 
 void drop_graphs(knn_ctx* h) {
-    for (auto& kv : h->graphs)
+    for (auto& kv : h->graphs) {
         if (kv.second.exec) cudaGraphExecDestroy(kv.second.exec);
+        persist_free(&kv.second.pb);
+    }
     h->graphs.clear();
 }
 
@@ -673,6 +680,125 @@ knn_status build_batch(knn_ctx* h, const knn_instance* inst, int32_t count, int 
     return s;
 }
 
+// ------------------------------------------------------- persistent batches
+
+// Bound of every wait of the persistent kernel in a normal run.
+constexpr uint64_t kPersistWaitNs = 1000000000ull;
+
+// (d, k) bucket of an instance: the unit the autotuner picks split lengths for.
+uint64_t bucket_of(const knn_instance& x) {
+    return (static_cast<uint64_t>(static_cast<uint32_t>(x.d)) << 32) | static_cast<uint32_t>(x.k);
+}
+
+// True when every instance can take the persistent tensor-core form.
+bool persistent_eligible(const knn_ctx* h, const knn_instance* inst, int32_t count) {
+    if (h->opt.precision == KNN_FP32) return false;
+    for (int32_t i = 0; i < count; ++i)
+        if (inst[i].metric != KNN_L2) return false;
+    return true;
+}
+
+std::vector<PersistInst> persist_inputs(const knn_instance* inst, int32_t count,
+                                        const std::map<uint64_t, int64_t>& chunks) {
+    std::vector<PersistInst> v(count);
+    for (int32_t i = 0; i < count; ++i) {
+        const knn_instance& x = inst[i];
+        auto it = chunks.find(bucket_of(x));
+        v[i] = PersistInst{x.R, x.m, x.Q, x.n, x.d, x.k, x.dist_out, x.idx_out,
+                           it == chunks.end() ? 0 : it->second};
+    }
+    return v;
+}
+
+// Plan, size the workspace, build and capture (counters reset, ready word
+// set, one kernel) one persistent batch.  KNN_ERR_UNSUPPORTED when some
+// instance cannot run in that form.
+knn_status build_persistent(knn_ctx* h, const std::vector<PersistInst>& pin, knn_ctx::BatchGraph* out) {
+    const int prec = h->opt.precision == KNN_BF16 ? kBF16 : kTF32;
+    PersistPlan pp;
+    cudaError_t err = persist_plan(pin, prec, h->opt.rerank_factor, h->num_sms, &pp);
+    if (err == cudaErrorNotSupported) return KNN_ERR_UNSUPPORTED;
+    if (err != cudaSuccess) return cuda_fail(h, err, "persist_plan");
+    knn_status s = ensure_workspace(h, pp.ws_bytes);
+    if (s != KNN_OK) return s;
+    s = batch_streams(h);
+    if (s != KNN_OK) return s;
+    PersistCounters ctr{&h->counters->error_flag, &h->counters->recheck_total,
+                        &h->counters->fallback_total, h->counters->fallback_reason};
+    PersistBatch pb;
+    KNN_CUDA(h, persist_build(pin, pp, prec, h->ws, ctr, &pb));
+    KNN_CUDA(h, cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeRelaxed));
+    err = persist_launch(pb, h->num_sms, true, kPersistWaitNs, h->cap_stream);
+    cudaGraph_t graph = nullptr;
+    const cudaError_t err2 = cudaStreamEndCapture(h->cap_stream, &graph);
+    if (err != cudaSuccess || err2 != cudaSuccess) {
+        if (graph) cudaGraphDestroy(graph);
+        persist_free(&pb);
+        (void)cudaGetLastError();
+        return cuda_fail(h, err != cudaSuccess ? err : err2, "persistent batch capture");
+    }
+    size_t nodes = 0;
+    cudaGraphGetNodes(graph, nullptr, &nodes);
+    cudaGraphExec_t exec = nullptr;
+    err = cudaGraphInstantiate(&exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (err != cudaSuccess) {
+        persist_free(&pb);
+        return cuda_fail(h, err, "cudaGraphInstantiate");
+    }
+    out->exec = exec;
+    out->pb = pb;
+    out->persistent = true;
+    out->branches = 1;
+    out->sm_share = h->num_sms;
+    out->launches = 1;
+    out->nodes = nodes;
+    return KNN_OK;
+}
+
+// Split lengths the autotuner tries for every (d, k) bucket (0: the planner's
+// own choice, by how full the last wave of a lone search would be).
+constexpr int64_t kChunkChoices[] = {0, 16384, 32768, 65536};
+
+// Time each split length on the sub-batch of each (d, k) bucket and keep the
+// fastest per bucket.
+knn_status tune_persistent(knn_ctx* h, const knn_instance* inst, int32_t count, cudaStream_t st,
+                           std::map<uint64_t, int64_t>* best, float* tune_ms) {
+    std::map<uint64_t, std::vector<knn_instance>> buckets;
+    for (int32_t i = 0; i < count; ++i)
+        if (inst[i].n > 0) buckets[bucket_of(inst[i])].push_back(inst[i]);
+    for (auto& kv : buckets) {
+        float best_ms = 0.f;
+        int64_t best_chunk = 0;
+        bool have = false;
+        for (int64_t ch : kChunkChoices) {
+            std::map<uint64_t, int64_t> one{{kv.first, ch}};
+            std::vector<PersistInst> pin =
+                persist_inputs(kv.second.data(), static_cast<int32_t>(kv.second.size()), one);
+            knn_ctx::BatchGraph g;
+            knn_status s = build_persistent(h, pin, &g);
+            if (s != KNN_OK) return s;
+            KNN_CUDA(h, cudaGraphLaunch(g.exec, st));   // warm
+            KNN_CUDA(h, cudaEventRecord(h->t_ev[0], st));
+            KNN_CUDA(h, cudaGraphLaunch(g.exec, st));
+            KNN_CUDA(h, cudaEventRecord(h->t_ev[1], st));
+            KNN_CUDA(h, cudaEventSynchronize(h->t_ev[1]));
+            float ms = 0.f;
+            KNN_CUDA(h, cudaEventElapsedTime(&ms, h->t_ev[0], h->t_ev[1]));
+            *tune_ms += 2.f * ms;
+            cudaGraphExecDestroy(g.exec);
+            persist_free(&g.pb);
+            if (!have || ms < best_ms) {
+                best_ms = ms;
+                best_chunk = ch;
+                have = true;
+            }
+        }
+        (*best)[kv.first] = best_chunk;
+    }
+    return KNN_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -982,13 +1108,46 @@ knn_status knn_search_batch(knn_handle h, const knn_instance* inst, int32_t coun
         }
         h->launches += l;
         h->searches += count;
-        h->last_batch = knn_batch_info{1, h->num_sms, l, 0, 0, 0.0};
+        h->last_batch = knn_batch_info{1, h->num_sms, l, 0, 0, 0.0, 0, 0};
         return KNN_OK;
     }
 
-    const uint64_t exact = batch_signature(h, inst, count, true);
-    const uint64_t shape = batch_signature(h, inst, count, false);
+    // the persistent form (every instance in one kernel launch) unless the
+    // graph of per-instance launches is asked for or some instance needs it
+    const bool want_persistent = !(flags & KNN_BATCH_BRANCHES) && persistent_eligible(h, inst, count);
+    const uint64_t form = want_persistent ? 0x7e57ull : 0x6a0full;
+    const uint64_t exact = mix64(batch_signature(h, inst, count, true), form);
+    const uint64_t shape = mix64(batch_signature(h, inst, count, false), form);
     auto it = h->graphs.find(exact);
+    bool fresh = false;   // built (and described in last_batch) by this call
+    if (it == h->graphs.end() && want_persistent) {
+        float tune_ms = 0.f;
+        bool tuned_now = false;
+        auto tk = h->tuned_chunks.find(shape);
+        if (tk == h->tuned_chunks.end() && (flags & KNN_BATCH_AUTOTUNE)) {
+            KNN_CUDA(h, cudaStreamSynchronize(st));
+            std::map<uint64_t, int64_t> best;
+            knn_status s = tune_persistent(h, inst, count, st, &best, &tune_ms);
+            if (s != KNN_OK && s != KNN_ERR_UNSUPPORTED) return s;
+            if (s == KNN_OK) {
+                tk = h->tuned_chunks.emplace(shape, best).first;
+                tuned_now = true;
+            }
+        }
+        static const std::map<uint64_t, int64_t> kNone;
+        knn_ctx::BatchGraph g;
+        knn_status s = build_persistent(
+            h, persist_inputs(inst, count, tk == h->tuned_chunks.end() ? kNone : tk->second), &g);
+        if (s == KNN_OK) {
+            it = h->graphs.emplace(exact, g).first;
+            fresh = true;
+            h->last_batch = knn_batch_info{1, h->num_sms, 1, static_cast<int64_t>(g.nodes),
+                                           tuned_now ? 1 : 0, static_cast<double>(tune_ms), 1,
+                                           g.pb.nitems};
+        } else if (s != KNN_ERR_UNSUPPORTED) {
+            return s;
+        }
+    }
     if (it == h->graphs.end()) {
         knn_ctx::BatchGraph best;
         float tune_ms = 0.f;
@@ -1048,11 +1207,12 @@ knn_status knn_search_batch(knn_handle h, const knn_instance* inst, int32_t coun
         it = h->graphs.emplace(exact, best).first;
         h->last_batch = knn_batch_info{best.branches, best.sm_share, best.launches,
                                        static_cast<int64_t>(best.nodes), tuned_now ? 1 : 0,
-                                       static_cast<double>(tune_ms)};
-    } else {
+                                       static_cast<double>(tune_ms), 0, 0};
+    } else if (!fresh) {
         const knn_ctx::BatchGraph& g = it->second;
         h->last_batch = knn_batch_info{g.branches, g.sm_share, g.launches,
-                                       static_cast<int64_t>(g.nodes), 0, 0.0};
+                                       static_cast<int64_t>(g.nodes), 0, 0.0,
+                                       g.persistent ? 1 : 0, g.persistent ? g.pb.nitems : 0};
     }
     KNN_CUDA(h, cudaGraphLaunch(it->second.exec, st));
     h->launches += it->second.launches;
@@ -1166,6 +1326,45 @@ knn_status knn_selftest_bounded_wait(knn_handle h, int32_t limit_ms) {
     KNN_CUDA(h, launch_wait_probe(&h->counters->error_flag,
                                   static_cast<uint64_t>(limit_ms) * 1000000ull, h->stream));
     return knn_sync(h);
+}
+
+knn_status knn_selftest_batch_queue(knn_handle h, int32_t limit_ms) {
+    if (!h || limit_ms < 1 || limit_ms > 1000) return KNN_ERR_INVALID;
+    KNN_CUDA(h, cudaSetDevice(h->device));
+    KNN_CUDA(h, cudaStreamSynchronize(h->stream));
+    // a one-instance batch (64 points in d = 32) whose buffers the kernel never
+    // reaches: every CTA gives up at the withheld ready word
+    constexpr int64_t n = 64;
+    constexpr int32_t d = 32, k = 4;
+    unsigned char* buf = nullptr;
+    const size_t pts = static_cast<size_t>(n) * d * sizeof(float);
+    const size_t outs = static_cast<size_t>(n) * k * sizeof(float);
+    KNN_CUDA(h, cudaMalloc(&buf, 2 * pts + 2 * outs));
+    const float* R = reinterpret_cast<const float*>(buf);
+    const float* Q = reinterpret_cast<const float*>(buf + pts);
+    float* dist = reinterpret_cast<float*>(buf + 2 * pts);
+    int32_t* idx = reinterpret_cast<int32_t*>(buf + 2 * pts + outs);
+    const std::vector<PersistInst> pin{PersistInst{R, n, Q, n, d, k, dist, idx, 0}};
+    PersistPlan pp;
+    PersistBatch pb;
+    knn_status s = KNN_OK;
+    cudaError_t err = persist_plan(pin, kBF16, h->opt.rerank_factor, h->num_sms, &pp);
+    if (err != cudaSuccess) s = cuda_fail(h, err, "persist_plan");
+    if (s == KNN_OK) s = ensure_workspace(h, pp.ws_bytes);
+    if (s == KNN_OK) {
+        PersistCounters ctr{&h->counters->error_flag, &h->counters->recheck_total,
+                            &h->counters->fallback_total, h->counters->fallback_reason};
+        err = persist_build(pin, pp, kBF16, h->ws, ctr, &pb);
+        if (err == cudaSuccess)
+            err = persist_launch(pb, h->num_sms, false, static_cast<uint64_t>(limit_ms) * 1000000ull,
+                                 h->stream);
+        if (err != cudaSuccess) s = cuda_fail(h, err, "persistent batch self-test");
+    }
+    if (s == KNN_OK) s = knn_sync(h);
+    else cudaDeviceSynchronize();
+    persist_free(&pb);
+    cudaFree(buf);
+    return s;
 }
 
 knn_status knn_get_stats(knn_handle h, knn_stats* out) {

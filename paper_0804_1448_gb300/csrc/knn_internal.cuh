@@ -222,7 +222,12 @@ struct TcPlan {
     int32_t raw;         // filter stages hit values as float32 (else 16-bit codes)
     size_t smem_filter;
 };
-TcPlan tc_plan(int64_t n, int64_t m, int32_t d, int32_t kp, int prec, int32_t c, int num_sms);
+// smem_limit: the dynamic shared memory an item may use (the persistent batch
+// kernel keeps some for itself); force_chunk > 0: split the references into
+// pieces of about this length (rounded to whole tiles) instead of choosing the
+// split count by how full the last wave of CTAs is.
+TcPlan tc_plan(int64_t n, int64_t m, int32_t d, int32_t kp, int prec, int32_t c, int num_sms,
+               size_t smem_limit = 232448, int64_t force_chunk = 0);
 
 // Per-query scale of the 16-bit hit codes (a power of two B > |acc|): the
 // largest squared reference norm (float bits, set by launch_prepare_ref) and

@@ -50,11 +50,13 @@ class knn_instance(ctypes.Structure):
 class knn_batch_info(ctypes.Structure):
     _fields_ = [("branches", ctypes.c_int32), ("sm_share", ctypes.c_int32),
                 ("launches", ctypes.c_int32), ("graph_nodes", ctypes.c_int64),
-                ("tuned", ctypes.c_int32), ("tune_ms", ctypes.c_double)]
+                ("tuned", ctypes.c_int32), ("tune_ms", ctypes.c_double),
+                ("persistent", ctypes.c_int32), ("items", ctypes.c_int32)]
 
 
 KNN_BATCH_AUTOTUNE = 1
 KNN_BATCH_NO_GRAPH = 2
+KNN_BATCH_BRANCHES = 4
 
 
 class knn_stats(ctypes.Structure):
@@ -87,6 +89,7 @@ _SIGS = {
                                   ctypes.c_int, _P]),
     "knn_sync": (ctypes.c_int, [_H]),
     "knn_selftest_bounded_wait": (ctypes.c_int, [_H, _i32]),
+    "knn_selftest_batch_queue": (ctypes.c_int, [_H, _i32]),
     "knn_explain_plan": (ctypes.c_int, [_i64, _i64, _i32, _i32, ctypes.c_int, _i32, _i32, _i32,
                                         ctypes.POINTER(knn_plan)]),
     "knn_set_precision": (ctypes.c_int, [_H, _i32]),
@@ -120,6 +123,7 @@ knn_set_reference = _lib.knn_set_reference
 knn_search = _lib.knn_search
 knn_sync = _lib.knn_sync
 knn_selftest_bounded_wait = _lib.knn_selftest_bounded_wait
+knn_selftest_batch_queue = _lib.knn_selftest_batch_queue
 knn_explain_plan = _lib.knn_explain_plan
 
 knn_set_precision = _lib.knn_set_precision

@@ -1,7 +1,13 @@
-"""Batched search (knn_search_batch) on the GPU (needs a GB300): every
-instance of a mixed batch gives exactly what a lone knn_search gives, the
-float32 form matches the oracle under the parity rule, graph replays, the
-no-graph form and the autotuned form agree, and bad instances are refused."""
+"""Batched search (knn_search_batch) on the GPU (needs a GB300).
+
+Mixed batches (some Manhattan instances) and float32 batches run as a graph of
+the instances' own launches: every instance gives exactly what a lone
+knn_search gives, the float32 form matches the oracle under the parity rule,
+graph replays, the no-graph form and the autotuned form agree, and bad
+instances are refused.  Euclidean batches in bf16 / tf32 run as ONE persistent
+kernel launch popping work items from a device queue: every instance matches
+the oracle (recall 1.0 and the parity rule on every row), the launch count is
+one, replays and the autotuned split lengths give the same results."""
 import numpy as np
 import pytest
 
@@ -21,10 +27,11 @@ def knn():
     return mod
 
 
-def make_batch(count, seed, m_rng=(1000, 20000), n_rng=(16, 512)):
+def make_batch(count, seed, m_rng=(1000, 20000), n_rng=(16, 512), l1_every=5):
     """Instances with m, n uniform in the ranges, d in {32, 64, 128}, k in
     {1, 10, 50} (k <= m), float32 uniform data (the batching workload's
-    distribution at test sizes)."""
+    distribution at test sizes); every l1_every-th instance Manhattan (0:
+    none)."""
     import torch
     g = np.random.default_rng(seed)
     out = []
@@ -38,7 +45,8 @@ def make_batch(count, seed, m_rng=(1000, 20000), n_rng=(16, 512)):
         out.append(dict(R=torch.from_numpy(R).cuda(), Q=torch.from_numpy(Q).cuda(), k=k,
                         dist=torch.empty((n, k), device="cuda"),
                         idx=torch.empty((n, k), dtype=torch.int32, device="cuda"),
-                        R_host=R, Q_host=Q, metric="l2" if i % 5 else "l1"))
+                        R_host=R, Q_host=Q,
+                        metric="l1" if l1_every and i % l1_every == 0 else "l2"))
     return out
 
 
@@ -136,4 +144,102 @@ def test_bad_instances_are_refused(knn):
         ix.search_batch([batch[0], bad, batch[2]])
     assert e.value.status == 1
     ix.search_batch([])                          # an empty batch is a no-op
+    ix.close()
+
+
+# ------------------------------------------------------------- persistent form
+
+def check_instances(batch):
+    """Every row of every instance against the oracle: recall@k 1.0 and the
+    parity rule."""
+    for j, x in enumerate(batch):
+        R, Q, k = x["R_host"], x["Q_host"], x["k"]
+        o_dist, o_idx = oracle.knn(R, Q, parity.oracle_k(k, R.shape[0]), x["metric"])
+        g_dist, g_idx = x["dist"].cpu().numpy(), x["idx"].cpu().numpy()
+        assert parity.recall(g_idx, o_idx, k) == 1.0, f"instance {j}"
+        parity.compare(g_dist, g_idx, o_dist, o_idx, k, R.shape[0])
+
+
+@pytest.mark.parametrize("precision", ["bf16", "tf32"])
+def test_persistent_batch_matches_the_oracle(knn, precision):
+    """24 Euclidean instances (m from 1000, below the size the pilot needs, to
+    20000; n from 16 to 512; d in {32, 64, 128}; k in {1, 10, 50}) in one
+    kernel launch."""
+    batch = make_batch(24, seed=11, l1_every=0)
+    ix = knn.Index(0, precision)
+    ix.search_batch(batch)
+    ix.sync()
+    info = ix.batch_info()
+    assert info["persistent"] == 1 and info["launches"] == 1 and info["items"] > 24
+    check_instances(batch)
+    st = ix.stats()
+    assert st["searches"] == 24
+    ix.close()
+
+
+def test_persistent_replay_and_autotune(knn):
+    import torch
+    batch = make_batch(16, seed=12, l1_every=0)
+    ix = knn.Index(0, "bf16")
+    ix.search_batch(batch)
+    ix.sync()
+    ref = [(x["dist"].cpu().clone(), x["idx"].cpu().clone()) for x in batch]
+    for x in batch:
+        x["dist"].fill_(-1.0)
+        x["idx"].fill_(-1)
+    ix.search_batch(batch)                       # cached graph: the same launch again
+    ix.sync()
+    info = ix.batch_info()
+    assert info["persistent"] == 1 and info["tuned"] == 0
+    for x, (d, i) in zip(batch, ref):
+        assert torch.equal(x["dist"].cpu(), d) and torch.equal(x["idx"].cpu(), i)
+    ix.close()
+    ix = knn.Index(0, "bf16")
+    ix.search_batch(batch, flags=knn.KNN_BATCH_AUTOTUNE)
+    ix.sync()
+    first = ix.batch_info()
+    assert first["persistent"] == 1 and first["tuned"] == 1 and first["tune_ms"] > 0
+    check_instances(batch)
+    ix.search_batch(batch, flags=knn.KNN_BATCH_AUTOTUNE)   # tuned shape: no new tuning
+    ix.sync()
+    assert ix.batch_info()["tuned"] == 0
+    check_instances(batch)
+    # the graph of per-instance launches, asked for explicitly, agrees
+    for x in batch:
+        x["idx"].fill_(-1)
+    ix.search_batch(batch, flags=knn.KNN_BATCH_BRANCHES)
+    ix.sync()
+    assert ix.batch_info()["persistent"] == 0
+    check_instances(batch)
+    ix.close()
+
+
+def test_persistent_edge_instances(knn):
+    """Instances at the edges: one query, n = 129 (a ragged second query
+    tile), k = m, m below one reference tile, duplicated references (exact
+    fallback), a reference set with every point equal."""
+    import torch
+    rng_seed = 13
+    specs = [(1, 5000, 32, 10), (129, 3000, 64, 50), (40, 50, 32, 50), (77, 200, 128, 1)]
+    batch = []
+    for j, (n, m, d, k) in enumerate(specs):
+        R = inputs.uniform(m, d, seed=20000 + 2 * j)
+        Q = inputs.uniform(n, d, seed=20001 + 2 * j)
+        batch.append(dict(R_host=R, Q_host=Q, k=k, metric="l2"))
+    base = inputs.uniform(800, 32, seed=20100)
+    batch.append(dict(R_host=np.concatenate([base, base, base]), Q_host=base[:60].copy(), k=9,
+                      metric="l2"))
+    batch.append(dict(R_host=np.full((3000, 32), 0.5, dtype=np.float32),
+                      Q_host=inputs.uniform(20, 32, seed=20101), k=10, metric="l2"))
+    for x in batch:
+        n, k = x["Q_host"].shape[0], x["k"]
+        x.update(R=torch.from_numpy(x["R_host"]).cuda(), Q=torch.from_numpy(x["Q_host"]).cuda(),
+                 dist=torch.empty((n, k), device="cuda"),
+                 idx=torch.empty((n, k), dtype=torch.int32, device="cuda"))
+    ix = knn.Index(0, "bf16")
+    ix.search_batch(batch)
+    ix.sync()
+    assert ix.batch_info()["persistent"] == 1
+    check_instances(batch)
+    assert ix.stats()["fallback_queries"] >= 20   # the equal-points instance
     ix.close()
