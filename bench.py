@@ -75,6 +75,13 @@ def parse_args():
     p.add_argument("--configs", action="store_true",
                    help="timings of the other forms and shapes (configs 1-3) instead of the bench line")
     p.add_argument("--serve-requests", type=int, default=1000)
+    p.add_argument("--profile-search", nargs=3, metavar=("PRECISION", "WORKLOAD", "DISTANCE"),
+                   help="run --reps searches of a workload (fp32/bf16/tf32, a workload name, "
+                        "l2/l1/linf) and exit: the command of an ncu capture")
+    p.add_argument("--profile-batch", type=int, default=0,
+                   help="run --reps bf16 batches of this many Euclidean instances of the test "
+                        "distribution and exit: the command of an ncu capture")
+    p.add_argument("--reps", type=int, default=4)
     p.add_argument("--serve-batch", type=int, default=0,
                    help="time searches of this many queries on the serving reference set "
                         "(m = 4,194,304, d = 96, k = 20) instead of the bench line")
@@ -277,12 +284,17 @@ def serve_bench(local, args):
             "inputs": "reference set and query pool resident on the device"}
 
 
-def batch_bench(local, args, peak_tflops):
+def batch_bench(local, args, peak_tflops, hbm_gbs):
     """Batching form: 512 independent instances, m uniform in [1000, 200000],
     n uniform in [16, 4096], d in {32, 64, 128}, k in {1, 10, 50}, float32
     uniform data (generated on the device from a fixed seed), Euclidean,
-    bf16 + re-rank.  Timed: one graph launch of the autotuned batch against
-    the same instances enqueued one after another, each planned alone."""
+    bf16 + re-rank.  Timed: the persistent form (one kernel launch, split
+    lengths autotuned per (d, k) bucket), the graph of the instances' own
+    launches on parallel branches (autotuned), and the same instances enqueued
+    one after another, each planned alone.  The roofline of the batch is the
+    sum over instances of max(2 n m d / tensor peak, 4 d (m + n) + 8 n k bytes
+    / HBM bandwidth): each instance's contraction at the bf16 peak, or its
+    float32 inputs read and outputs written once, whichever takes longer."""
     import numpy as np
     import torch
     from paper_0804_1448_gb300 import knn
@@ -294,6 +306,7 @@ def batch_bench(local, args, peak_tflops):
     inst = []
     flops = 0.0
     queries = 0
+    roof_s = 0.0
     for _ in range(count):
         m = int(g.integers(1000, 200001))
         n = int(g.integers(16, 4097))
@@ -303,8 +316,10 @@ def batch_bench(local, args, peak_tflops):
         Q = torch.rand((n, d), generator=gen, device=dev)
         inst.append(dict(R=R, Q=Q, k=k, dist=torch.empty((n, k), device=dev),
                          idx=torch.empty((n, k), dtype=torch.int32, device=dev)))
-        flops += 2.0 * n * m * d
+        f = 2.0 * n * m * d
+        flops += f
         queries += n
+        roof_s += max(f / (peak_tflops * 1e12), (4.0 * d * (m + n) + 8.0 * n * k) / (hbm_gbs * 1e9))
     ix = knn.Index(local, "bf16")
     stream = torch.cuda.current_stream(dev)
 
@@ -320,23 +335,36 @@ def batch_bench(local, args, peak_tflops):
 
     ix.search_batch(inst, flags=knn.KNN_BATCH_NO_GRAPH, stream=stream)   # warm-up
     t_seq = timed(knn.KNN_BATCH_NO_GRAPH, 3)
+    # graph of per-instance launches on parallel branches (autotuned)
+    br = knn.KNN_BATCH_BRANCHES | knn.KNN_BATCH_AUTOTUNE
+    ix.search_batch(inst, flags=br, stream=stream)
+    torch.cuda.synchronize(dev)
+    branches = ix.batch_info()
+    t_branches = timed(br, 5)
+    # the persistent form (autotuned split lengths)
     t0 = time.perf_counter()
     ix.search_batch(inst, flags=knn.KNN_BATCH_AUTOTUNE, stream=stream)   # tunes, captures
     torch.cuda.synchronize(dev)
     tune_s = time.perf_counter() - t0
     tuned = ix.batch_info()
-    t_graph = timed(knn.KNN_BATCH_AUTOTUNE, 5)
+    t_pers = timed(knn.KNN_BATCH_AUTOTUNE, 5)
+    after = ix.batch_info()
     ix.close()
-    tflops = flops / (t_graph / 1e3) / 1e12
+    tflops = flops / (t_pers / 1e3) / 1e12
     return {"workload": "batch_512_uniform", "instances": count, "queries": queries,
             "flop": flops, "precision": "bf16", "distance": "l2",
-            "graph_ms": t_graph, "queries_per_s": queries / (t_graph / 1e3),
-            "per_instance_ms": t_seq, "per_instance_queries_per_s": queries / (t_seq / 1e3),
-            "speedup_vs_per_instance": t_seq / t_graph,
+            "persistent_ms": t_pers, "queries_per_s": queries / (t_pers / 1e3),
+            "launches": after["launches"], "work_items": after["items"],
+            "graph_nodes": after["graph_nodes"],
+            "roofline_ms": roof_s * 1e3, "frac_of_roofline": roof_s * 1e3 / t_pers,
+            "roofline": "sum over instances of max(2nmd / bf16 peak, (4d(m+n) + 8nk) B / HBM)",
             "achieved_tflops": tflops, "frac_of_peak": tflops / peak_tflops if peak_tflops else None,
-            "tuned": {"branches": tuned["branches"], "sm_share": tuned["sm_share"],
-                      "graph_nodes": tuned["graph_nodes"], "launches": tuned["launches"],
-                      "tune_device_ms": tuned["tune_ms"], "tune_wall_s": tune_s}}
+            "branches_graph_ms": t_branches, "branches_graph_launches": branches["launches"],
+            "per_instance_ms": t_seq, "per_instance_queries_per_s": queries / (t_seq / 1e3),
+            "speedup_vs_per_instance": t_seq / t_pers, "speedup_vs_branches_graph": t_branches / t_pers,
+            "tuned": {"tune_device_ms": tuned["tune_ms"], "tune_wall_s": tune_s,
+                      "branches_graph": {"branches": branches["branches"],
+                                         "sm_share": branches["sm_share"]}}}
 
 
 # Table 1 of the paper, BF-CUDA seconds (8800 GTX, float32, host<->device copies
@@ -576,6 +604,50 @@ def sweep(args):
     print(json.dumps({"sweep": "table1", "k": 20, "distance": "l2", "rows": rows}), flush=True)
 
 
+def profile_search(args):
+    """--reps searches of one workload in one precision and distance, inputs
+    resident, nothing timed (for ncu: the last launches are the warm ones)."""
+    import torch
+    from paper_0804_1448_gb300 import inputs, knn
+    precision, workload, distance = args.profile_search
+    R, Q, k = inputs.workload(workload)
+    Rd, Qd = torch.from_numpy(R).cuda(), torch.from_numpy(Q).cuda()
+    ix = knn.Index(0, precision)
+    ix.set_reference(Rd)
+    for _ in range(args.reps):
+        ix.search(Qd, k, distance)
+    ix.sync()
+    ix.close()
+    print(json.dumps({"profile_search": [precision, workload, distance], "reps": args.reps}))
+
+
+def profile_batch(args):
+    """--reps runs of one bf16 batch of Euclidean instances with the batch GPU
+    test's distribution (m 1000..20000, n 16..512, d in {32, 64, 128}, k in
+    {1, 10, 50}; seeded), device inputs (for ncu)."""
+    import numpy as np
+    import torch
+    from paper_0804_1448_gb300 import inputs, knn
+    g = np.random.default_rng(11)
+    inst = []
+    for i in range(args.profile_batch):
+        m = int(g.integers(1000, 20001))
+        n = int(g.integers(16, 513))
+        d = int(g.choice([32, 64, 128]))
+        k = int(g.choice([1, 10, 50]))
+        R = torch.from_numpy(inputs.uniform(m, d, seed=10000 + 2 * (11000 + i))).cuda()
+        Q = torch.from_numpy(inputs.uniform(n, d, seed=10001 + 2 * (11000 + i))).cuda()
+        inst.append(dict(R=R, Q=Q, k=k, dist=torch.empty((n, k), device="cuda"),
+                         idx=torch.empty((n, k), dtype=torch.int32, device="cuda")))
+    ix = knn.Index(0, "bf16")
+    for _ in range(args.reps):
+        ix.search_batch(inst)
+    ix.sync()
+    info = ix.batch_info()
+    ix.close()
+    print(json.dumps({"profile_batch": args.profile_batch, "reps": args.reps, "batch_info": info}))
+
+
 def main():
     args = parse_args()
     if args.impl == "reference":
@@ -586,6 +658,12 @@ def main():
         return
     if args.serve_batch > 0:
         serve_batch(args)
+        return
+    if args.profile_search:
+        profile_search(args)
+        return
+    if args.profile_batch > 0:
+        profile_batch(args)
         return
     if args.sweep:
         sweep(args)
@@ -725,7 +803,7 @@ def main():
     if not args.no_serve:
         line["serve"] = serve_bench(local, args)
     if not args.no_batch:
-        line["batch"] = batch_bench(local, args, peak)
+        line["batch"] = batch_bench(local, args, tensor_peak(peaks, "bf16"), peaks["hbm_gbs"])
     if not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(R, Q, k, args.cpu_seconds)
     print(json.dumps(line), flush=True)

@@ -143,18 +143,69 @@ __device__ __noinline__ void final_rows(const FinalizeArgs& fa, const BatchInst&
         finalize_query<kL2, NV>(fa, I.fin_P, I.fin_se, q, scratch, lane);
 }
 
+// Rows [r0, r1) of R (REF) or Q into the instance's augmented low-precision
+// copy, the operation of prepare_row (same arithmetic, same order), with
+// kPrepInFlight rows per warp loaded before any is used: one row at a time
+// leaves a warp waiting on memory for every row.  Needs d <= 128 (four
+// coordinates per lane).  REF: the largest squared norm of the warp's rows is
+// raised into the instance's maximum once.  QUERY: the pilot maxima rows are
+// zeroed, or without a pilot the hit-code scale is set.
+constexpr int kPrepInFlight = 8;
+
 template <int PREC, bool REF>
 __device__ __noinline__ void prep_rows(const BatchInst& I, int64_t r0, int64_t r1, int warp, int lane) {
-    for (int64_t r = r0 + warp; r < r1; r += kBWarps) {
-        if (REF) {
-            prepare_row<PREC, true>(I.R, r, I.d, I.kp, I.R_lp, nullptr, I.rmax2, nullptr, nullptr, lane);
-        } else {
-            prepare_row<PREC, false>(I.Q, r, I.d, I.kp, I.Q_lp, nullptr, I.rmax2,
-                                     I.pilot ? nullptr : I.qscale, nullptr, lane);
-            if (I.pilot)
+    const float* X = REF ? I.R : I.Q;
+    const int d = I.d, kp = I.kp;
+    const size_t elt = (PREC == kBF16) ? 2 : 4;
+    float nmax = 0.f;
+    for (int64_t rb = r0 + static_cast<int64_t>(warp) * kPrepInFlight; rb < r1;
+         rb += static_cast<int64_t>(kBWarps) * kPrepInFlight) {
+        float xv[kPrepInFlight][4];
+#pragma unroll
+        for (int u = 0; u < kPrepInFlight; ++u)
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                const int t = lane + 32 * j;
+                xv[u][j] = (rb + u < r1 && t < d) ? X[(rb + u) * d + t] : 0.f;
+            }
+        float nr[kPrepInFlight];
+#pragma unroll
+        for (int u = 0; u < kPrepInFlight; ++u) {
+            nr[u] = 0.f;
+#pragma unroll
+            for (int j = 0; j < 4; ++j)
+                if (lane + 32 * j < d) nr[u] = fmaf(xv[u][j], xv[u][j], nr[u]);
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+            for (int u = 0; u < kPrepInFlight; ++u) nr[u] += __shfl_xor_sync(0xffffffffu, nr[u], o);
+#pragma unroll
+        for (int u = 0; u < kPrepInFlight; ++u) {
+            const int64_t r = rb + u;
+            if (r >= r1) break;
+            if (REF) nmax = fmaxf(nmax, nr[u]);
+            if (!REF && lane == 0 && !I.pilot) I.qscale[r] = hit_scale(nr[u], __uint_as_float(*I.rmax2), 0.f);
+            if (!REF && I.pilot)
                 for (int g = lane; g < I.G; g += 32) I.gmax[r * I.G + g] = 0u;
+            const float h = -0.5f * nr[u];
+            const float hi = lowp_round<PREC>(h);
+            const float lo = lowp_round<PREC>(h - hi);
+            void* row = static_cast<unsigned char*>(REF ? I.R_lp : I.Q_lp) + static_cast<size_t>(r) * kp * elt;
+#pragma unroll
+            for (int j = 0; j < 8; ++j) {
+                const int t = lane + 32 * j;
+                if (t >= kp) break;
+                float v = 0.f;
+                if (t < d) v = xv[u][j < 4 ? j : 0];
+                else if (t == d) v = REF ? hi : 1.f;
+                else if (t == d + 1) v = REF ? lo : 1.f;
+                else if (t == d + 2 || t == d + 3) v = REF ? 1.f : 0.f;
+                put<PREC>(row, t, v);
+            }
         }
     }
+    if (REF && lane == 0) atomicMax(I.rmax2, __float_as_uint(nmax));
 }
 
 // The instance's queued queries, one after another, by the whole CTA.
@@ -319,6 +370,7 @@ cudaError_t persist_plan(const std::vector<PersistInst>& in, int prec, int reran
         pi.kp = tc_padded_dim(x.d, prec);
         pi.plan = tc_plan(x.n, x.m, x.d, pi.kp, prec, c, num_sms, kBatchDyn, x.chunk);
         if (pi.plan.stages == 0) return cudaErrorNotSupported;   // rows too long for the tile
+        if (x.d > 128 || pi.kp > 256) return cudaErrorNotSupported;   // the preparation's row layout
         if (x.k > kFbMaxK) return cudaErrorNotSupported;
         pi.P = (2 * c + 32 + 3) & ~3;
         if (pi.P > kMaxPool) return cudaErrorNotSupported;

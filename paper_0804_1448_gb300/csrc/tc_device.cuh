@@ -602,12 +602,15 @@ __device__ __forceinline__ float hit_scale(float nq2, float rmax2, float t) {
 // non-negative float); QUERY: [x, 1, 1, 0, 0, 0..] (threshold words filled
 // later) and, when qscale is given (no threshold pass follows), the hit-code
 // scale for t = 0.
+// Returns the row's squared float32 norm (REF, or QUERY with qscale) on every
+// lane; with rmax2 and REF it also raises *rmax2 to it (one atomic per row;
+// callers converting many rows per warp pass nullptr and raise it once).
 template <int PREC, bool REF>
-__device__ __forceinline__ void prepare_row(const float* __restrict__ X, int64_t r, int32_t d,
-                                            int32_t kp, void* __restrict__ out,
-                                            float* __restrict__ norms, uint32_t* __restrict__ rmax2,
-                                            float* __restrict__ qscale, float* __restrict__ xcopy,
-                                            int lane) {
+__device__ __forceinline__ float prepare_row(const float* __restrict__ X, int64_t r, int32_t d,
+                                             int32_t kp, void* __restrict__ out,
+                                             float* __restrict__ norms, uint32_t* __restrict__ rmax2,
+                                             float* __restrict__ qscale, float* __restrict__ xcopy,
+                                             int lane) {
     const float* x = X + r * d;
     const size_t elt = (PREC == kBF16) ? 2 : 4;
     void* row = static_cast<unsigned char*>(out) + static_cast<size_t>(r) * kp * elt;
@@ -635,6 +638,7 @@ __device__ __forceinline__ void prepare_row(const float* __restrict__ X, int64_t
         else if (t == d + 2 || t == d + 3) v = REF ? 1.f : 0.f;
         put<PREC>(row, t, v);
     }
+    return nr;
 }
 
 template <int PREC, bool REF>
