@@ -24,6 +24,7 @@ from __future__ import annotations
 import argparse
 import json
 import os
+import re
 import statistics
 import subprocess
 import sys
@@ -40,11 +41,13 @@ WORKLOAD = "uniform_n38400_d96_k20"
 SERVE_WORKLOAD = "serve_m4194304_d96"
 PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
 # DRAM traffic of one tensor-core filter launch on this workload, from one ncu
-# capture (dram__bytes_read.sum + dram__bytes_write.sum: 36.43 + 62.70 MB; see
-# profiles/tc_filter_uniform_n38400_d96_k20.md), valid only for the kernel
-# source it was measured on (sha256 prefix below); otherwise reported as null.
-FILTER_TRAFFIC_BYTES = 99.13e6
-FILTER_TRAFFIC_SRC = "f09a4600e257e1b7"
+# capture (dram__bytes_read.sum + dram__bytes_write.sum: 36.44 + 62.79 MB; see
+# profiles/tc_filter_uniform_n38400_d96_k20.md), valid only for the kernel's
+# device source it was measured on (sha256 prefix of tc_device.cuh followed by
+# tc_ptx.cuh); otherwise reported as null.
+FILTER_TRAFFIC_BYTES = 99.23e6
+FILTER_TRAFFIC_SRC = "8b5c033f455eb4f5"
+FILTER_SOURCES = ("tc_device.cuh", "tc_ptx.cuh")
 
 CLOCK_HOLD_S = 0.3
 
@@ -76,8 +79,9 @@ def parse_args():
                    help="timings of the other forms and shapes (configs 1-3) instead of the bench line")
     p.add_argument("--serve-requests", type=int, default=1000)
     p.add_argument("--profile-search", nargs=3, metavar=("PRECISION", "WORKLOAD", "DISTANCE"),
-                   help="run --reps searches of a workload (fp32/bf16/tf32, a workload name, "
-                        "l2/l1/linf) and exit: the command of an ncu capture")
+                   help="run --reps searches of a workload (fp32/bf16/tf32, a workload name or a "
+                        "Table 1 point table1_n<N>_d<D>, l2/l1/linf) and exit: the command "
+                        "of an ncu capture")
     p.add_argument("--profile-batch", type=int, default=0,
                    help="run --reps bf16 batches of this many Euclidean instances of the test "
                         "distribution and exit: the command of an ncu capture")
@@ -172,12 +176,14 @@ def filter_traffic(precision):
     """Measured DRAM bytes per filter launch, or None when the kernel source
     has changed since the measurement (or for another precision)."""
     import hashlib
-    src = os.path.join(ROOT, "paper_0804_1448_gb300", "csrc", "knn_tc.cu")
+    h = hashlib.sha256()
     try:
-        with open(src, "rb") as f:
-            cur = hashlib.sha256(f.read()).hexdigest()[:16]
+        for name in FILTER_SOURCES:
+            with open(os.path.join(ROOT, "paper_0804_1448_gb300", "csrc", name), "rb") as f:
+                h.update(f.read())
     except OSError:
         return None
+    cur = h.hexdigest()[:16]
     return FILTER_TRAFFIC_BYTES if (cur == FILTER_TRAFFIC_SRC and precision == "bf16") else None
 
 
@@ -610,7 +616,12 @@ def profile_search(args):
     import torch
     from paper_0804_1448_gb300 import inputs, knn
     precision, workload, distance = args.profile_search
-    R, Q, k = inputs.workload(workload)
+    grid = re.fullmatch(r"table1_n(\d+)_d(\d+)", workload)
+    if grid:   # a point of the Table 1 grid, drawn as --sweep draws it
+        N, D = int(grid.group(1)), int(grid.group(2))
+        R, Q, k = inputs.uniform(N, D, seed=1000 + D), inputs.uniform(N, D, seed=2000 + D), 20
+    else:
+        R, Q, k = inputs.workload(workload)
     Rd, Qd = torch.from_numpy(R).cuda(), torch.from_numpy(Q).cuda()
     ix = knn.Index(0, precision)
     ix.set_reference(Rd)

@@ -251,26 +251,19 @@ __device__ __forceinline__ WarpScratch carve(unsigned char* base, int P, int L, 
     return w;
 }
 
-// Two-lane float32 arithmetic (one instruction for a pair of coordinates):
-// the differences of (a0, a1) and (b0, b1), the fused square-accumulate of a
-// pair of differences, and the sum of a pair.
-__device__ __forceinline__ uint64_t f2_sub(float a0, float a1, float b0, float b1) {
-    uint64_t d;
-    asm("{\n .reg .b64 p, q;\n mov.b64 p, {%1, %2};\n mov.b64 q, {%3, %4};\n"
-        " sub.rn.f32x2 %0, p, q;\n}"
-        : "=l"(d) : "f"(a0), "f"(a1), "f"(b0), "f"(b1));
-    return d;
-}
-__device__ __forceinline__ uint64_t f2_sqacc(uint64_t diff, uint64_t acc) {
+// Two-lane float32 arithmetic on pairs of consecutive coordinates held as
+// 64-bit registers (as loaded, 16 bytes = two pairs): acc + (a - b)^2 per lane
+// (one two-lane subtraction, one two-lane fused multiply-add), and the sum of
+// a pair.
+__device__ __forceinline__ uint64_t f2_sqdiff_acc(uint64_t a, uint64_t b, uint64_t acc) {
     uint64_t r;
-    asm("fma.rn.f32x2 %0, %1, %1, %2;" : "=l"(r) : "l"(diff), "l"(acc));
+    asm("{\n .reg .b64 t;\n sub.rn.f32x2 t, %1, %2;\n fma.rn.f32x2 %0, t, t, %3;\n}"
+        : "=l"(r) : "l"(a), "l"(b), "l"(acc));
     return r;
 }
-__device__ __forceinline__ float f2_sum(uint64_t v) {
-    float lo, hi;
-    asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(v));
-    return lo + hi;
-}
+__device__ __forceinline__ float pair_lo(uint64_t v) { return __uint_as_float(static_cast<uint32_t>(v)); }
+__device__ __forceinline__ float pair_hi(uint64_t v) { return __uint_as_float(static_cast<uint32_t>(v >> 32)); }
+__device__ __forceinline__ float f2_sum(uint64_t v) { return pair_lo(v) + pair_hi(v); }
 
 // Replace raw reference indices keys[0..cnt) (kEmptyKey = none) by exact
 // float32 keys.  NV > 0 (d % 4 == 0, d <= 128, NV = ceil(d/32)): eight lanes
@@ -287,21 +280,20 @@ __device__ void exact_keys(uint64_t* keys, int cnt, const float* __restrict__ R,
     if constexpr (NV > 0) {
         constexpr int G = NV >= 3 ? 2 : (NV == 2 ? 3 : 4);
         const int g = lane >> 3, sub = lane & 7, d4 = d >> 2;
-        const float4* q4 = reinterpret_cast<const float4*>(qrow);
+        const ulonglong2* q4 = reinterpret_cast<const ulonglong2*>(qrow);
         for (int e0 = 0; e0 < cnt; e0 += 4 * G) {
             uint64_t raw[G];
-            float4 x[G][NV];
+            ulonglong2 x[G][NV];   // four coordinates as two pairs
 #pragma unroll
             for (int u = 0; u < G; ++u) {
                 const int e = e0 + 4 * u + g;
                 raw[u] = (e < cnt) ? keys[e] : kEmptyKey;
-                const float4* row = reinterpret_cast<const float4*>(
+                const ulonglong2* row = reinterpret_cast<const ulonglong2*>(
                     R + static_cast<int64_t>(raw[u] == kEmptyKey ? 0 : raw[u]) * d);
 #pragma unroll
                 for (int v = 0; v < NV; ++v) {
                     const int t = sub + 8 * v;
-                    x[u][v] = (raw[u] != kEmptyKey && t < d4) ? __ldg(row + t)
-                                                              : make_float4(0.f, 0.f, 0.f, 0.f);
+                    x[u][v] = (raw[u] != kEmptyKey && t < d4) ? __ldg(row + t) : make_ulonglong2(0ull, 0ull);
                 }
             }
             float acc[G];
@@ -313,12 +305,11 @@ __device__ void exact_keys(uint64_t* keys, int cnt, const float* __restrict__ R,
                 for (int v = 0; v < NV; ++v) {
                     const int t = sub + 8 * v;
                     if (t < d4) {
-                        const float4 y = q4[t];
+                        const ulonglong2 y = q4[t];
 #pragma unroll
                         for (int u = 0; u < G; ++u) {
-                            const float4 r = x[u][v];
-                            s01[u] = f2_sqacc(f2_sub(y.x, y.y, r.x, r.y), s01[u]);
-                            s23[u] = f2_sqacc(f2_sub(y.z, y.w, r.z, r.w), s23[u]);
+                            s01[u] = f2_sqdiff_acc(y.x, x[u][v].x, s01[u]);
+                            s23[u] = f2_sqdiff_acc(y.y, x[u][v].y, s23[u]);
                         }
                     }
                 }
@@ -331,14 +322,14 @@ __device__ void exact_keys(uint64_t* keys, int cnt, const float* __restrict__ R,
                 for (int v = 0; v < NV; ++v) {
                     const int t = sub + 8 * v;
                     if (t < d4) {
-                        const float4 y = q4[t];
+                        const ulonglong2 y = q4[t];
 #pragma unroll
                         for (int u = 0; u < G; ++u) {
-                            const float4 r = x[u][v];
-                            acc[u] = acc_f32<METRIC>(acc[u], y.x - r.x);
-                            acc[u] = acc_f32<METRIC>(acc[u], y.y - r.y);
-                            acc[u] = acc_f32<METRIC>(acc[u], y.z - r.z);
-                            acc[u] = acc_f32<METRIC>(acc[u], y.w - r.w);
+                            const ulonglong2 r = x[u][v];
+                            acc[u] = acc_f32<METRIC>(acc[u], pair_lo(y.x) - pair_lo(r.x));
+                            acc[u] = acc_f32<METRIC>(acc[u], pair_hi(y.x) - pair_hi(r.x));
+                            acc[u] = acc_f32<METRIC>(acc[u], pair_lo(y.y) - pair_lo(r.y));
+                            acc[u] = acc_f32<METRIC>(acc[u], pair_hi(y.y) - pair_hi(r.y));
                         }
                     }
                 }

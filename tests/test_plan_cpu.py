@@ -139,7 +139,7 @@ def test_fp32_split_invariants(n, m, k):
 
 
 @pytest.mark.parametrize("m,d,small", [(1200, 8, 1), (4096, 96, 1), (4097, 96, 0), (4096, 256, 1),
-                                       (4096, 444, 0), (2000, 200, 1)])
+                                       (4096, 444, 1), (4096, 3000, 0), (2000, 200, 1)])
 def test_small_reference_sets_use_the_small_select(m, d, small):
     """Reference sets of at most 4096 points whose distances, eight query rows
     of them, fit one CTA's shared memory take the small-set select (one split
