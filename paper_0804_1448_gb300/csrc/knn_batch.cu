@@ -158,6 +158,60 @@ __device__ __noinline__ void prep_rows(const BatchInst& I, int64_t r0, int64_t r
     const int d = I.d, kp = I.kp;
     const size_t elt = (PREC == kBF16) ? 2 : 4;
     float nmax = 0.f;
+    const int dg = d / 4;   // float4s of data per row
+    if ((d & 3) == 0 && (dg == 8 || dg == 16 || dg == 32) && (reinterpret_cast<uintptr_t>(X) & 15) == 0) {
+        // rows packed into the warp, 32 / dg rows per pack and lane (row
+        // lane / dg, float4 lane % dg): one 16-byte load per lane and pack,
+        // kPrepInFlight packs in flight, so short rows keep as many bytes in
+        // flight as long ones; one 8- or 16-byte store per lane and four
+        // elements, the augmentation and padding by the same lanes
+        const int rpp = 32 / dg, pr = lane / dg, g0 = lane % dg, ng = kp / 4;
+        const int64_t rows_per_iter = static_cast<int64_t>(rpp) * kPrepInFlight;
+        for (int64_t rb = r0 + static_cast<int64_t>(warp) * rows_per_iter; rb < r1;
+             rb += static_cast<int64_t>(kBWarps) * rows_per_iter) {
+            float4 xv[kPrepInFlight];
+#pragma unroll
+            for (int u = 0; u < kPrepInFlight; ++u) {
+                const int64_t r = rb + static_cast<int64_t>(u) * rpp + pr;
+                xv[u] = r < r1 ? reinterpret_cast<const float4*>(X + r * d)[g0] : make_float4(0.f, 0.f, 0.f, 0.f);
+            }
+            float nr[kPrepInFlight];
+#pragma unroll
+            for (int u = 0; u < kPrepInFlight; ++u) {
+                float a2 = fmaf(xv[u].x, xv[u].x, 0.f);
+                a2 = fmaf(xv[u].y, xv[u].y, a2);
+                a2 = fmaf(xv[u].z, xv[u].z, a2);
+                nr[u] = fmaf(xv[u].w, xv[u].w, a2);
+            }
+            // sum over the dg lanes of each row (aligned groups of dg lanes)
+            for (int o = dg / 2; o > 0; o >>= 1)
+#pragma unroll
+                for (int u = 0; u < kPrepInFlight; ++u) nr[u] += __shfl_xor_sync(0xffffffffu, nr[u], o);
+#pragma unroll
+            for (int u = 0; u < kPrepInFlight; ++u) {
+                const int64_t r = rb + static_cast<int64_t>(u) * rpp + pr;
+                if (r >= r1) continue;
+                if (REF) nmax = fmaxf(nmax, nr[u]);
+                if (!REF && g0 == 0 && !I.pilot) I.qscale[r] = hit_scale(nr[u], __uint_as_float(*I.rmax2), 0.f);
+                if (!REF && I.pilot)
+                    for (int g = g0; g < I.G; g += dg) I.gmax[r * I.G + g] = 0u;
+                const float h = -0.5f * nr[u];
+                const float hi = lowp_round<PREC>(h);
+                const float lo = lowp_round<PREC>(h - hi);
+                void* row = static_cast<unsigned char*>(REF ? I.R_lp : I.Q_lp) + static_cast<size_t>(r) * kp * elt;
+                put4<PREC>(row, 4 * g0, xv[u]);
+                for (int g = dg + g0; g < ng; g += dg) {
+                    const float4 v = g == dg ? (REF ? make_float4(hi, lo, 1.f, 1.f) : make_float4(1.f, 1.f, 0.f, 0.f))
+                                             : make_float4(0.f, 0.f, 0.f, 0.f);
+                    put4<PREC>(row, 4 * g, v);
+                }
+            }
+        }
+        // every lane's rows are in nmax; the warp's largest goes to the atomic
+        for (int o = 16; o > 0; o >>= 1) nmax = fmaxf(nmax, __shfl_xor_sync(0xffffffffu, nmax, o));
+        if (REF && lane == 0) atomicMax(I.rmax2, __float_as_uint(nmax));
+        return;
+    }
     for (int64_t rb = r0 + static_cast<int64_t>(warp) * kPrepInFlight; rb < r1;
          rb += static_cast<int64_t>(kBWarps) * kPrepInFlight) {
         float xv[kPrepInFlight][4];

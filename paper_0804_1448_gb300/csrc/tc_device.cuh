@@ -576,6 +576,26 @@ __device__ __forceinline__ float get(const void* row, int t) {
     if (PREC == kBF16) return __bfloat162float(reinterpret_cast<const __nv_bfloat16*>(row)[t]);
     return __uint_as_float(reinterpret_cast<const uint32_t*>(row)[t]);
 }
+// Four consecutive row elements t .. t+3 (t a multiple of 4; the row 8-byte
+// aligned for bf16, 16-byte aligned for tf32) in one store.
+template <int PREC>
+__device__ __forceinline__ void put4(void* row, int t, float4 v) {
+    if (PREC == kBF16) {
+        const __nv_bfloat162 a = __floats2bfloat162_rn(v.x, v.y);
+        const __nv_bfloat162 b = __floats2bfloat162_rn(v.z, v.w);
+        uint2 w;
+        w.x = *reinterpret_cast<const uint32_t*>(&a);
+        w.y = *reinterpret_cast<const uint32_t*>(&b);
+        reinterpret_cast<uint2*>(row)[t / 4] = w;
+    } else {
+        uint4 w;
+        asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(w.x) : "f"(v.x));
+        asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(w.y) : "f"(v.y));
+        asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(w.z) : "f"(v.z));
+        asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(w.w) : "f"(v.w));
+        reinterpret_cast<uint4*>(row)[t / 4] = w;
+    }
+}
 template <int PREC>
 __device__ __forceinline__ float lowp_round(float v) {
     if (PREC == kBF16) return __bfloat162float(__float2bfloat16_rn(v));
