@@ -355,13 +355,18 @@ def batch_bench(local, args, peak_tflops, hbm_gbs):
     tuned = ix.batch_info()
     t_pers = timed(knn.KNN_BATCH_AUTOTUNE, 5)
     after = ix.batch_info()
+    # the last run's CTA time per stage, averaged over the SMs' CTAs
+    ctas = torch.cuda.get_device_properties(dev).multi_processor_count
+    stages = {name: {"work_ms_per_cta": v["work_ms"] / ctas, "wait_ms_per_cta": v["wait_ms"] / ctas,
+                     "items": v["items"]}
+              for name, v in ix.batch_stage_times().items()}
     ix.close()
     tflops = flops / (t_pers / 1e3) / 1e12
     return {"workload": "batch_512_uniform", "instances": count, "queries": queries,
             "flop": flops, "precision": "bf16", "distance": "l2",
             "persistent_ms": t_pers, "queries_per_s": queries / (t_pers / 1e3),
             "launches": after["launches"], "work_items": after["items"],
-            "graph_nodes": after["graph_nodes"],
+            "graph_nodes": after["graph_nodes"], "stages": stages,
             "roofline_ms": roof_s * 1e3, "frac_of_roofline": roof_s * 1e3 / t_pers,
             "roofline": "sum over instances of max(2nmd / bf16 peak, (4d(m+n) + 8nk) B / HBM)",
             "achieved_tflops": tflops, "frac_of_peak": tflops / peak_tflops if peak_tflops else None,

@@ -412,6 +412,20 @@ typedef struct {
 knn_status knn_batch_info_get(knn_handle h, knn_batch_info* out);
 
 /*
+ * Where the last persistent batch run spent its time, per stage of its work
+ * items -- 0 operand rows of R, 1 of Q, 2 pilot, 3 threshold, 4 filter,
+ * 5 finalize, 6 exact fallback: wait_ms[s] and work_ms[s], the CTA time (summed
+ * over the CTAs, from the GPU's global timer) its items spent waiting for
+ * their instance's previous stage and working, and items[s], how many ran.
+ * Each array holds 7 entries (HOST pointers).  Waits for the batch's stream.
+ * Valid after a knn_search_batch that ran in the persistent form, until the
+ * handle's next search of any kind.  The paper has no counterpart: it is the
+ * measurement of this library's batching form.  Errors: KNN_ERR_INVALID,
+ * KNN_ERR_UNSUPPORTED (no persistent run to report), KNN_ERR_CUDA.
+ */
+knn_status knn_batch_stage_times(knn_handle h, double* wait_ms, double* work_ms, int64_t* items);
+
+/*
  * Self-test of the persistent batch kernel's bounded waits: enqueues on the
  * handle's stream one launch of the persistent kernel on a one-instance batch
  * whose "ready" word is withheld (the host never sets it), so every CTA's

@@ -44,6 +44,7 @@ enum BatchStage : int32_t {
     kStPrepR = 0, kStPrepQ, kStPilot, kStThresh, kStFilter, kStFinal, kStFallback, kNumStages
 };
 
+static_assert(kNumStages == kPersistStages, "stage count");
 constexpr int kBWarps = kTcThreads / 32;        // 18
 constexpr int kPrepRows = kBWarps * 128;        // rows per preparation item
 constexpr int kThreshQueries = kBWarps * 4;     // queries per threshold item
@@ -87,6 +88,7 @@ struct BatchDesc {
     const int32_t* ready;       // non-zero: the host lets the kernel start
     int32_t* error_flag;        // raised by a wait that gave up (any CTA)
     uint64_t wait_ns;           // bound of every wait
+    unsigned long long* stage_ns;   // [3][kNumStages]: CTA time waiting, CTA time working, items
 };
 
 __device__ __forceinline__ int32_t ld_volatile(const int32_t* p) {
@@ -303,7 +305,9 @@ batch_kernel(const __grid_constant__ BatchDesc bd) {
         if (idx >= bd.nitems) break;   // CTA-uniform: s_next is stable since the last barrier
         const BatchItem it = bd.items[idx];
         const BatchInst& I = bd.insts[it.inst];
+        uint64_t t_wait = 0, t_work = 0;   // thread 0: when the item's wait began and ended
         if (threadIdx.x == 0) {
+            t_wait = globaltimer();
             const int ps = I.prev[it.stage];
             if (ps >= 0 && !wait_geq(&bd.done[it.inst * kNumStages + ps], I.need[ps], bd.error_flag,
                                      bd.wait_ns)) {
@@ -319,6 +323,7 @@ batch_kernel(const __grid_constant__ BatchDesc bd) {
             if (it.stage == kStFallback) s_count = ld_volatile(I.fa.fallback_count);
             // the next item, popped now so that its latency overlaps this one
             s_pre = s_abort ? bd.nitems : atomicAdd(bd.head, 1);
+            t_work = globaltimer();
         }
         __syncthreads();
         if (s_abort) break;   // CTA-uniform
@@ -373,6 +378,10 @@ batch_kernel(const __grid_constant__ BatchDesc bd) {
         if (threadIdx.x == 0) {
             fence_proxy_async();
             atomicAdd(&bd.done[it.inst * kNumStages + it.stage], 1);
+            const uint64_t t_end = globaltimer();
+            atomicAdd(&bd.stage_ns[it.stage], static_cast<unsigned long long>(t_work - t_wait));
+            atomicAdd(&bd.stage_ns[kNumStages + it.stage], static_cast<unsigned long long>(t_end - t_work));
+            atomicAdd(&bd.stage_ns[2 * kNumStages + it.stage], 1ull);
             // another CTA gave up: stop popping
             s_next = ld_volatile(bd.error_flag) != 0 ? bd.nitems : s_pre;
         }
@@ -410,6 +419,7 @@ cudaError_t persist_plan(const std::vector<PersistInst>& in, int prec, int reran
     pp.off_done = take(sizeof(int32_t) * kNumStages * static_cast<size_t>(ninst));
     pp.off_rmax = take(sizeof(uint32_t) * static_cast<size_t>(ninst));
     pp.off_fbc = take(sizeof(int32_t) * static_cast<size_t>(ninst));
+    pp.off_stage_ns = take(sizeof(unsigned long long) * 3 * kNumStages);
     pp.counters_bytes = off;
     pp.off_ready = take(sizeof(int32_t));
     pp.inst.resize(ninst);
@@ -606,6 +616,7 @@ cudaError_t persist_build(const std::vector<PersistInst>& in, const PersistPlan&
     out->ready = reinterpret_cast<int32_t*>(ws + pp.off_ready);
     out->head = reinterpret_cast<int32_t*>(ws + pp.off_head);
     out->done = reinterpret_cast<int32_t*>(ws + pp.off_done);
+    out->stage_ns = reinterpret_cast<unsigned long long*>(ws + pp.off_stage_ns);
     out->error_flag = ctr.error_flag;
     out->prec = prec;
     return cudaSuccess;
@@ -628,6 +639,7 @@ cudaError_t persist_launch(const PersistBatch& b, int grid_ctas, bool set_ready,
     bd.ready = b.ready;
     bd.error_flag = b.error_flag;
     bd.wait_ns = wait_ns;
+    bd.stage_ns = b.stage_ns;
     const unsigned grid = static_cast<unsigned>(std::max(1, grid_ctas));
     if (b.prec == kBF16) {
         err = allow_smem<batch_kernel<kBF16>>(kBatchDyn);

@@ -34,7 +34,7 @@ struct PersistPlan {
         size_t off_qs = 0, off_list = 0, off_scr = 0;
     };
     std::vector<Inst> inst;
-    size_t off_head = 0, off_done = 0, off_rmax = 0, off_fbc = 0, off_ready = 0;
+    size_t off_head = 0, off_done = 0, off_rmax = 0, off_fbc = 0, off_ready = 0, off_stage_ns = 0;
     size_t counters_bytes = 0;   // [0, counters_bytes) is zeroed before every run
     size_t ws_bytes = 0;
 };
@@ -59,6 +59,7 @@ struct PersistBatch {
     int32_t* ready = nullptr;
     int32_t* head = nullptr;
     int32_t* done = nullptr;
+    unsigned long long* stage_ns = nullptr;   // [3][stages]: waiting ns, working ns, items (summed over CTAs)
     int32_t* error_flag = nullptr;
     int prec = 0;
 };
@@ -73,5 +74,8 @@ cudaError_t persist_launch(const PersistBatch& b, int grid_ctas, bool set_ready,
                            cudaStream_t st);
 void persist_free(PersistBatch* b);
 size_t persist_item_smem();
+// Stages of the persistent batch: operand rows of R, of Q, pilot, threshold,
+// filter, finalize, exact fallback.
+constexpr int kPersistStages = 7;
 
 }  // namespace knn

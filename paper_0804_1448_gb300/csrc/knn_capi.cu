@@ -96,6 +96,10 @@ struct knn_ctx {
     cudaStream_t branch[16] = {};
     cudaEvent_t fork_ev = nullptr, join_ev[16] = {}, t_ev[2] = {};
     knn_batch_info last_batch{};
+    // per-stage time counters of the last persistent batch run (in the
+    // workspace; cleared by the next search of any kind), and its stream
+    unsigned long long* last_stage_ns = nullptr;
+    cudaStream_t last_stage_stream = nullptr;
 
     // Mahalanobis distance: the Cholesky factor L of the inverse covariance
     // (device, float32, row-major), the whitened reference set built from
@@ -986,6 +990,7 @@ knn_status knn_search(knn_handle h, const float* Q, int64_t n, int32_t d, int32_
                       void* cuda_stream) {
     knn_status s0 = check_search_args(h, n, d, k, metric);
     if (s0 != KNN_OK) return s0;
+    h->last_stage_ns = nullptr;
     if (n > 0 && (!Q || !dist_out || !idx_out)) return KNN_ERR_INVALID;
     if (n == 0) return KNN_OK;
     KNN_CUDA(h, cudaSetDevice(h->device));
@@ -1086,6 +1091,7 @@ knn_status knn_search(knn_handle h, const float* Q, int64_t n, int32_t d, int32_
 knn_status knn_search_batch(knn_handle h, const knn_instance* inst, int32_t count, int32_t flags,
                             void* cuda_stream) {
     if (!h || count < 0 || (count > 0 && !inst)) return KNN_ERR_INVALID;
+    h->last_stage_ns = nullptr;
     for (int32_t i = 0; i < count; ++i) {
         knn_status s = check_instance(inst[i]);
         if (s != KNN_OK) return s;
@@ -1217,6 +1223,10 @@ knn_status knn_search_batch(knn_handle h, const knn_instance* inst, int32_t coun
     KNN_CUDA(h, cudaGraphLaunch(it->second.exec, st));
     h->launches += it->second.launches;
     h->searches += count;
+    if (it->second.persistent) {
+        h->last_stage_ns = it->second.pb.stage_ns;
+        h->last_stage_stream = st;
+    }
     return KNN_OK;
 }
 
@@ -1226,9 +1236,25 @@ knn_status knn_batch_info_get(knn_handle h, knn_batch_info* out) {
     return KNN_OK;
 }
 
+knn_status knn_batch_stage_times(knn_handle h, double* wait_ms, double* work_ms, int64_t* items) {
+    if (!h || !wait_ms || !work_ms || !items) return KNN_ERR_INVALID;
+    if (!h->last_stage_ns) return KNN_ERR_UNSUPPORTED;
+    KNN_CUDA(h, cudaSetDevice(h->device));
+    KNN_CUDA(h, cudaStreamSynchronize(h->last_stage_stream));
+    unsigned long long v[3 * kPersistStages];
+    KNN_CUDA(h, cudaMemcpy(v, h->last_stage_ns, sizeof(v), cudaMemcpyDeviceToHost));
+    for (int s = 0; s < kPersistStages; ++s) {
+        wait_ms[s] = static_cast<double>(v[s]) * 1e-6;
+        work_ms[s] = static_cast<double>(v[kPersistStages + s]) * 1e-6;
+        items[s] = static_cast<int64_t>(v[2 * kPersistStages + s]);
+    }
+    return KNN_OK;
+}
+
 knn_status knn_search_self(knn_handle h, int32_t k, knn_metric metric, float* dist_out,
                            int32_t* idx_out, void* cuda_stream) {
     if (!h || !dist_out || !idx_out) return KNN_ERR_INVALID;
+    h->last_stage_ns = nullptr;
     if (!h->ref) return KNN_ERR_NOREF;
     if (k < 1 || static_cast<int64_t>(k) + 1 > h->ref->m) return KNN_ERR_INVALID;
     knn_status s = check_search_args(h, h->ref->m, h->ref->d, k + 1, metric);

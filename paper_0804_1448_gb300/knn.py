@@ -57,6 +57,8 @@ class knn_batch_info(ctypes.Structure):
 KNN_BATCH_AUTOTUNE = 1
 KNN_BATCH_NO_GRAPH = 2
 KNN_BATCH_BRANCHES = 4
+# stages of the persistent batch, in the order of knn_batch_stage_times
+BATCH_STAGES = ("prepare_r", "prepare_q", "pilot", "threshold", "filter", "finalize", "fallback")
 
 
 class knn_stats(ctypes.Structure):
@@ -107,6 +109,8 @@ _SIGS = {
     "knn_search_batch": (ctypes.c_int, [_H, ctypes.POINTER(knn_instance), _i32, _i32, _P]),
     "knn_search_self": (ctypes.c_int, [_H, _i32, ctypes.c_int, _P, _P, _P]),
     "knn_batch_info_get": (ctypes.c_int, [_H, ctypes.POINTER(knn_batch_info)]),
+    "knn_batch_stage_times": (ctypes.c_int, [_H, ctypes.POINTER(ctypes.c_double),
+                                             ctypes.POINTER(ctypes.c_double), ctypes.POINTER(_i64)]),
     "knn_destroy": (ctypes.c_int, [_H]),
     "knn_status_string": (ctypes.c_char_p, [ctypes.c_int]),
     "knn_last_error": (ctypes.c_char_p, [_H]),
@@ -138,6 +142,7 @@ knn_reserve = _lib.knn_reserve
 knn_search_batch = _lib.knn_search_batch
 knn_search_self = _lib.knn_search_self
 knn_batch_info_get = _lib.knn_batch_info_get
+knn_batch_stage_times = _lib.knn_batch_stage_times
 knn_destroy = _lib.knn_destroy
 knn_status_string = _lib.knn_status_string
 knn_last_error = _lib.knn_last_error
@@ -324,6 +329,15 @@ class Index:
         b = knn_batch_info()
         self._check(knn_batch_info_get(self.h, ctypes.byref(b)), "knn_batch_info_get")
         return {f: getattr(b, f) for f, _ in knn_batch_info._fields_}
+
+    def batch_stage_times(self) -> dict:
+        """knn_batch_stage_times: per stage of the last persistent batch run,
+        the CTA time its items waited and worked (ms, summed over CTAs) and how
+        many ran."""
+        w, t, n = (ctypes.c_double * 7)(), (ctypes.c_double * 7)(), (_i64 * 7)()
+        self._check(knn_batch_stage_times(self.h, w, t, n), "knn_batch_stage_times")
+        return {name: {"wait_ms": w[i], "work_ms": t[i], "items": n[i]}
+                for i, name in enumerate(BATCH_STAGES)}
 
     def sync(self):
         self._check(knn_sync(self.h), "knn_sync")

@@ -70,6 +70,8 @@ def test_every_entry_point_refuses_a_null_handle(lib):
     assert knn.knn_reserve(None, 1 << 20) == 1
     assert knn.knn_search_batch(None, None, 0, 0, None) == 1
     assert knn.knn_batch_info_get(None, ctypes.byref(info)) == 1
+    w, t, n = (ctypes.c_double * 7)(), (ctypes.c_double * 7)(), (ctypes.c_int64 * 7)()
+    assert knn.knn_batch_stage_times(None, w, t, n) == 1
     assert knn.knn_last_error(None) == b""
 
 

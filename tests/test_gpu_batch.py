@@ -174,6 +174,17 @@ def test_persistent_batch_matches_the_oracle(knn, precision):
     check_instances(batch)
     st = ix.stats()
     assert st["searches"] == 24
+    # where the launch spent its time: every item counted once, per stage
+    times = ix.batch_stage_times()
+    assert sum(v["items"] for v in times.values()) == info["items"]
+    assert times["filter"]["items"] > 0 and times["filter"]["work_ms"] > 0
+    assert times["finalize"]["items"] > 0 and all(v["wait_ms"] >= 0 for v in times.values())
+    # a later search clears them
+    ix.set_reference(batch[0]["R"])
+    ix.search(batch[0]["Q"], 1, "l2")
+    with pytest.raises(knn.KnnError) as e:
+        ix.batch_stage_times()
+    assert e.value.status == 7   # KNN_ERR_UNSUPPORTED
     ix.close()
 
 
