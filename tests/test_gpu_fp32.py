@@ -68,6 +68,8 @@ def test_uniform_n1200_d8_k20(knn, metric):
     (65, 4099, 7, 1),        # k = 1, many splits
     (100, 2000, 96, 64),
     (50, 700, 200, 100),     # d over several stages, large k
+    (300, 1500, 64, 10),     # small-set select, selection in registers (48 per lane)
+    (40, 3000, 37, 30),      # small-set select, radix selection, rows not whole float4s
 ])
 def test_ragged_shapes(knn, metric, n, m, d, k):
     R = inputs.uniform(m, d, seed=1000 + m)
