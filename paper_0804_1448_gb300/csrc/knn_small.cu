@@ -4,14 +4,13 @@
 //
 // Steps 1-3 of the brute-force algorithm of Sec. 2.1 for the eight queries of
 // a CTA (their rows staged in shared memory): the references go by in tiles of
-// 256 rows, each thread owning one row of a tile, which it reads 16
-// coordinates at a time straight into registers (three such steps in flight)
-// and accumulates its float32 distances to all eight queries at once
-// (coordinate differences;
-// Euclidean two coordinates to an instruction, as even and odd partial sums
-// added at the end; the float32 rounding bound the later stages use holds for
-// any order of the additions), and writes them to the queries' rows of m
-// distances in shared memory.  Then each warp selects for its query: the c-th
+// 512 rows, each thread owning two rows of a tile, which it reads 16
+// coordinates at a time straight into registers (the next step's loads in
+// flight while one is used) and accumulates their float32 distances to all
+// eight queries at once (coordinate differences; Euclidean two coordinates to
+// an instruction, as even and odd partial sums added at the end; the float32
+// rounding bound the later stages use holds for any order of the additions),
+// and writes them to the queries' rows of m distances in shared memory.  Then each warp selects for its query: the c-th
 // smallest distance is found by a bisection over the order-preserving bit
 // patterns (each step a warp-wide count over distances held in registers) or,
 // for rows longer than 48 per lane, by a radix selection of 8 bits per pass
@@ -127,11 +126,12 @@ small_select_kernel(const float* __restrict__ Q, int64_t n, const float* __restr
     const int nch = pq / kChunk;
     const int ntiles = (m + kTileRefs - 1) / kTileRefs;
     const int steps = ntiles * nch;
-    // step s = (tile s / nch, chunk s % nch): each thread owns row
-    // tile * kTileRefs + threadIdx.x of every tile and is the only reader of
-    // it, so its chunks go straight from global memory into registers (zeros
-    // beyond the rows and coordinates; 16-byte loads when rows are whole
-    // float4s, d % 4 == 0 and R 16-byte aligned), three steps in flight
+    // step s = (tile s / nch, chunk s % nch): each thread owns rows
+    // tile * kTileRefs + r * kThreads + threadIdx.x (r < kRowsPerThread) of
+    // every tile and is their only reader, so their chunks go straight from
+    // global memory into registers (zeros beyond the rows and coordinates;
+    // 16-byte loads when rows are whole float4s, d % 4 == 0 and R 16-byte
+    // aligned), the next step's loads issued before the current step is used
     const bool vec = (d & 3) == 0 && (reinterpret_cast<uintptr_t>(R) & 15) == 0;
     const int me = threadIdx.x;
     auto pack = [](float a, float b) {
