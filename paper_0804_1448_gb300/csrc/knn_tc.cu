@@ -276,7 +276,8 @@ cudaError_t launch_prepare_ref(const float* R, int64_t m, int32_t d, int32_t kp,
                                int* launches) {
     cudaError_t err = cudaMemsetAsync(rmax2, 0, sizeof(uint32_t), st);
     if (err != cudaSuccess) return err;
-    const unsigned grid = static_cast<unsigned>((m * 32 + 255) / 256);
+    const int64_t warps = (m + kPrepRowsPerWarp - 1) / kPrepRowsPerWarp;
+    const unsigned grid = static_cast<unsigned>((warps * 32 + 255) / 256);
     if (prec == kBF16)
         prepare_kernel<kBF16, true><<<grid, 256, 0, st>>>(R, m, d, kp, R_lp, norms, rmax2, nullptr,
                                                            nullptr);
@@ -290,7 +291,8 @@ cudaError_t launch_prepare_ref(const float* R, int64_t m, int32_t d, int32_t kp,
 cudaError_t launch_prepare_query(const float* Q, int64_t n, int32_t d, int32_t kp, int prec,
                                  void* Q_lp, const HitScale& qs, float* Q_copy, cudaStream_t st,
                                  int* launches) {
-    const unsigned grid = static_cast<unsigned>((n * 32 + 255) / 256);
+    const int64_t warps = (n + kPrepRowsPerWarp - 1) / kPrepRowsPerWarp;
+    const unsigned grid = static_cast<unsigned>((warps * 32 + 255) / 256);
     if (prec == kBF16)
         prepare_kernel<kBF16, false><<<grid, 256, 0, st>>>(Q, n, d, kp, Q_lp, nullptr,
                                                             const_cast<uint32_t*>(qs.rmax2), qs.qscale,

@@ -661,14 +661,80 @@ __device__ __forceinline__ float prepare_row(const float* __restrict__ X, int64_
     return nr;
 }
 
+constexpr int kPrepRowsPerWarp = 4;
+
+// kPrepRowsPerWarp rows per warp.  Rows of up to 128 coordinates: every
+// lane's loads of all the rows are issued before any is used (over the
+// CPU-GPU link, when X is in host memory, the latency is long), then each row
+// as prepare_row does it, with the same arithmetic in the same order.  Longer
+// rows: prepare_row, one row after another.
 template <int PREC, bool REF>
 __global__ void prepare_kernel(const float* __restrict__ X, int64_t rows, int32_t d, int32_t kp,
                                void* __restrict__ out, float* __restrict__ norms,
                                uint32_t* __restrict__ rmax2, float* __restrict__ qscale,
                                float* __restrict__ xcopy) {
-    const int64_t r = (static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x) / 32;
-    if (r >= rows) return;
-    prepare_row<PREC, REF>(X, r, d, kp, out, norms, rmax2, qscale, xcopy, threadIdx.x % 32);
+    constexpr int RW = kPrepRowsPerWarp;
+    const int lane = threadIdx.x % 32;
+    const int64_t r0 = (static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x) / 32 * RW;
+    if (r0 >= rows) return;
+    if (d > 128) {
+        for (int u = 0; u < RW && r0 + u < rows; ++u)
+            prepare_row<PREC, REF>(X, r0 + u, d, kp, out, norms, rmax2, qscale, xcopy, lane);
+        return;
+    }
+    float xv[RW][4];
+#pragma unroll
+    for (int u = 0; u < RW; ++u)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const int t = lane + 32 * j;
+            xv[u][j] = (r0 + u < rows && t < d) ? X[(r0 + u) * d + t] : 0.f;
+        }
+    float nr[RW];
+#pragma unroll
+    for (int u = 0; u < RW; ++u) {
+        nr[u] = 0.f;
+        if (REF || qscale) {
+#pragma unroll
+            for (int j = 0; j < 4; ++j)
+                if (lane + 32 * j < d) nr[u] = fmaf(xv[u][j], xv[u][j], nr[u]);
+        }
+    }
+    if (REF || qscale) {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+            for (int u = 0; u < RW; ++u) nr[u] += __shfl_xor_sync(0xffffffffu, nr[u], o);
+    }
+    const size_t elt = (PREC == kBF16) ? 2 : 4;
+#pragma unroll
+    for (int u = 0; u < RW; ++u) {
+        const int64_t r = r0 + u;
+        if (r >= rows) break;
+        if (lane == 0) {
+            if (REF && norms) norms[r] = nr[u];
+            if (REF && rmax2) atomicMax(rmax2, __float_as_uint(nr[u]));
+            if (!REF && qscale) qscale[r] = hit_scale(nr[u], __uint_as_float(*rmax2), 0.f);
+        }
+        const float h = -0.5f * nr[u];
+        const float hi = lowp_round<PREC>(h);
+        const float lo = lowp_round<PREC>(h - hi);
+        void* row = static_cast<unsigned char*>(out) + static_cast<size_t>(r) * kp * elt;
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {   // kp <= 256 when d <= 128
+            const int t = lane + 32 * j;
+            if (t >= kp) break;
+            float v = 0.f;
+            if (t < d) {
+                v = xv[u][j < 4 ? j : 0];
+                if (!REF && xcopy) xcopy[r * d + t] = v;
+            }
+            else if (t == d) v = REF ? hi : 1.f;
+            else if (t == d + 1) v = REF ? lo : 1.f;
+            else if (t == d + 2 || t == d + 3) v = REF ? 1.f : 0.f;
+            put<PREC>(row, t, v);
+        }
+    }
 }
 
 // One warp per query: the cprime-th largest group maximum of the pilot becomes
