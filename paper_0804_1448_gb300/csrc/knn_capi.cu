@@ -67,6 +67,7 @@ struct knn_ctx {
     size_t ws_bytes = 0;
 
     Counters* counters = nullptr;  // device
+    int32_t* flag_host = nullptr;  // pinned host word: the error flag as a host-buffer search ends
     int64_t searches = 0;
     int64_t launches = 0;
 
@@ -830,6 +831,7 @@ static knn_status new_handle(knn_handle* out, int device, const knn_options& o) 
     if (err == cudaSuccess) err = cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking);
     if (err == cudaSuccess) err = cudaMalloc(&h->counters, sizeof(Counters));
     if (err == cudaSuccess) err = cudaMemset(h->counters, 0, sizeof(Counters));
+    if (err == cudaSuccess) err = cudaHostAlloc(&h->flag_host, sizeof(int32_t), cudaHostAllocDefault);
     for (int i = 0; err == cudaSuccess && i <= kMaxStages; ++i) err = cudaEventCreate(&h->ev[i]);
     if (err != cudaSuccess) {
         knn_destroy(h);
@@ -884,6 +886,7 @@ knn_status knn_destroy(knn_handle h) {
     if (h->t_ev[1]) cudaEventDestroy(h->t_ev[1]);
     if (h->ws) cudaFree(h->ws);
     if (h->counters) cudaFree(h->counters);
+    if (h->flag_host) cudaFreeHost(h->flag_host);
     h->mref.reset();
     if (h->mahal_L) cudaFree(h->mahal_L);
     if (h->qw) cudaFree(h->qw);
@@ -1076,9 +1079,12 @@ knn_status knn_search(knn_handle h, const float* Q, int64_t n, int32_t d, int32_
                                         cudaMemcpyDeviceToHost, st));
             stage(h, st, "d2h");
         }
+        // the error flag comes back with the stream's last copy, so the one
+        // synchronisation also ends the call
+        KNN_CUDA(h, cudaMemcpyAsync(h->flag_host, &ctr->error_flag, sizeof(int32_t),
+                                    cudaMemcpyDeviceToHost, st));
         KNN_CUDA(h, cudaStreamSynchronize(st));
-        int32_t flag = 0;
-        KNN_CUDA(h, cudaMemcpy(&flag, &ctr->error_flag, sizeof(flag), cudaMemcpyDeviceToHost));
+        const int32_t flag = *h->flag_host;
         if (flag) {
             KNN_CUDA(h, cudaMemset(&ctr->error_flag, 0, sizeof(flag)));
             h->last_error = "a bounded device-side wait gave up";
