@@ -41,12 +41,12 @@ WORKLOAD = "uniform_n38400_d96_k20"
 SERVE_WORKLOAD = "serve_m4194304_d96"
 PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
 # DRAM traffic of one tensor-core filter launch on this workload, from one ncu
-# capture (dram__bytes_read.sum + dram__bytes_write.sum: 36.38 + 62.57 MB; see
+# capture (dram__bytes_read.sum + dram__bytes_write.sum: 36.51 + 63.00 MB; see
 # profiles/tc_filter_uniform_n38400_d96_k20.md), valid only for the kernel's
 # device source it was measured on (sha256 prefix of tc_device.cuh followed by
 # tc_ptx.cuh); otherwise reported as null.
-FILTER_TRAFFIC_BYTES = 98.95e6
-FILTER_TRAFFIC_SRC = "2ab749aaa73c41b1"
+FILTER_TRAFFIC_BYTES = 99.51e6
+FILTER_TRAFFIC_SRC = "40568f59ef5e108d"
 FILTER_SOURCES = ("tc_device.cuh", "tc_ptx.cuh")
 
 CLOCK_HOLD_S = 0.3
