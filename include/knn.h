@@ -188,6 +188,8 @@ typedef struct {
                                    shared memory and the c nearest selected exactly (small
                                    reference sets; the tensor-core forms take this path
                                    too when their pilot would not run) */
+    int32_t pilot_group_size;   /* tensor cores: references per pilot group (32; 16 or 8 when
+                                   every tile is sampled and groups of 32 are too few) */
 } knn_plan;
 
 knn_status knn_explain_plan(int64_t n, int64_t m, int32_t d, int32_t k, knn_metric metric,

@@ -518,6 +518,7 @@ cudaError_t persist_build(const std::vector<PersistInst>& in, const PersistPlan&
         a.stride = p.stride;
         a.spt = p.spt;
         a.G = p.G;
+        a.gps = 32 / p.gsize;
         a.cap = p.cap;
         a.append_all = p.pilot ? 0 : 1;
         a.error_flag = ctr.error_flag;

@@ -335,8 +335,17 @@ knn_status plan_search_md(const knn_ctx* h, int64_t m, int32_t d, int precision,
         p.plan = tc_plan(n, m, d, p.kp, p.prec, p.c, sm_share);
         // rows too long for the tile, or a reference set too small for the
         // pilot (every reference would be appended to the lists): the float32
-        // form, whose small-set select handles the latter faster and exactly
-        if (p.plan.stages == 0 || (!p.plan.pilot && small_select_fits(m, d)))
+        // form, whose small-set select handles the latter faster and exactly.
+        // Where both would run, the small-set select is kept while each SM's
+        // share of its distance work (CTAs of eight queries, each over all m
+        // references) stays small: its time grows with that share, the
+        // tensor-core form's stays near 0.09 ms at these sizes (measured at
+        // n = m = 2400: d = 32, 151k products per SM, 0.082 against 0.089 ms;
+        // d = 64, 303k, 0.104 against 0.089 ms)
+        const double small_share = static_cast<double>((n + 7) / 8) * static_cast<double>(m) *
+                                   static_cast<double>(d) / static_cast<double>(sm_share);
+        if (p.plan.stages == 0 ||
+            (small_select_fits(m, d) && (!p.plan.pilot || small_share < kSmallSelectShare)))
             return plan_search_md(h, m, d, KNN_FP32, n, k, metric, io_on_device, sm_share, sp,
                                   fb_cap_bytes);
         p.S = p.plan.S;
@@ -1342,6 +1351,7 @@ knn_status knn_explain_plan(int64_t n, int64_t m, int32_t d, int32_t k, knn_metr
         o.pilot = sp.plan.pilot;
         o.pilot_stride = sp.plan.stride;
         o.pilot_groups = sp.plan.G;
+        o.pilot_group_size = sp.plan.gsize;
         o.threshold_rank = sp.plan.cprime;
         o.list_capacity = sp.plan.cap;
     }

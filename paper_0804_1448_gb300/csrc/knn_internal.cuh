@@ -153,6 +153,9 @@ int cc_max_candidates();
 // one CTA's.  kSmallSelectSpare: the spare slots a search plans beyond c_need.
 constexpr int64_t kSmallSelectMaxM = 4096;
 constexpr int kSmallSelectSpare = 16;
+// Tensor-core searches whose pilot runs still take the small-set select while
+// ceil(n / 8) * m * d / SMs (an SM's share of its distance products) is below this.
+constexpr double kSmallSelectShare = 2.2e5;
 size_t small_select_smem(int64_t m, int32_t d);
 bool small_select_fits(int64_t m, int32_t d);
 cudaError_t launch_small_select(const float* Q, int64_t n, const float* R, int64_t m, int32_t d,
@@ -216,6 +219,7 @@ struct TcPlan {
     int32_t stride;      // pilot samples every stride-th stage
     int32_t spt;         // pilot tile slots per split
     int32_t G;           // pilot group maxima per query
+    int32_t gsize;       // references per pilot group (32, or 16 / 8 when every tile is sampled)
     int32_t cprime;      // order statistic of the group maxima used as threshold
     int32_t pilot;       // 0: no pilot, every reference is appended
     int32_t cap;         // list capacity per (query, split, column group)

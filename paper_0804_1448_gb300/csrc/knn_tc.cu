@@ -119,6 +119,7 @@ TcArgs base_args(const TcPlan& p, int64_t n, int64_t m, int32_t* error_flag) {
     a.stride = p.stride;
     a.spt = p.spt;
     a.G = p.G;
+    a.gps = 32 / p.gsize;
     a.cap = p.cap;
     a.append_all = p.pilot ? 0 : 1;
     a.error_flag = error_flag;
@@ -209,7 +210,8 @@ TcPlan tc_plan(int64_t n, int64_t m, int32_t d, int32_t kp, int prec, int32_t c,
     p.chunk = chunk;
     // pilot sampling: every stride-th tile (one reference in 16 or fewer), at
     // most ~1024 groups of 32 per query
-    const int gpt = kTileN / 32;                   // groups per tile
+    int gpt = kTileN / 32;                         // groups per tile
+    p.gsize = 32;
     const int64_t tiles_total = (m + kTileN - 1) / kTileN;
     int stride = 4096 / kTileN;
     while (tiles_total * gpt / stride > 1024) stride *= 2;
@@ -225,6 +227,10 @@ TcPlan tc_plan(int64_t n, int64_t m, int32_t d, int32_t kp, int prec, int32_t c,
     // group maxima needs G comfortably above c': sample denser (halve the
     // stride) until G >= c' + 8, and run no pilot (every reference appended)
     // only when even every tile does not give that many groups.
+    // When every tile is sampled the count is no longer a random draw: c' = c
+    // groups reaching T put at least c references above it.  Should even that
+    // leave too few groups of 32, the groups shrink to 16 or 8 references
+    // (the elements u = i mod 2 or mod 4 of a 32-column slice, group i).
     // The group slots of a short split's missing tiles, and groups past the
     // end of the data, hold no maximum: gvalid counts the real groups.
     int64_t gvalid = 0;
@@ -232,6 +238,7 @@ TcPlan tc_plan(int64_t n, int64_t m, int32_t d, int32_t kp, int prec, int32_t c,
         p.stride = stride;
         p.spt = (tps + stride - 1) / stride;
         p.G = S * p.spt * gpt;
+        const int gps = 32 / p.gsize;
         int64_t sampled = 0;
         gvalid = 0;
         for (int s = 0; s < S; ++s) {
@@ -240,26 +247,36 @@ TcPlan tc_plan(int64_t n, int64_t m, int32_t d, int32_t kp, int prec, int32_t c,
             for (int64_t t = 0; t < tiles; t += stride) {
                 const int64_t v = std::min<int64_t>(rows - t * kTileN, kTileN);
                 sampled += v;
-                gvalid += (v + 31) / 32;
+                // slice j of the tile holds min(32, v - 32 j) elements, of
+                // which its first gps each start a group
+                for (int64_t j = 0; j * 32 < v; ++j) gvalid += std::min<int64_t>(v - 32 * j, gps);
             }
         }
         const double lambda = static_cast<double>(c) * static_cast<double>(sampled) / static_cast<double>(m);
-        p.cprime = static_cast<int>(std::ceil(lambda + 4.0 * std::sqrt(lambda) + 4.0));
-        if (gvalid >= p.cprime + 8 || stride == 1 || p.G > 1024) break;
-        stride /= 2;
+        p.cprime = sampled == m ? c
+                                : static_cast<int>(std::ceil(lambda + 4.0 * std::sqrt(lambda) + 4.0));
+        if (gvalid >= p.cprime + 8 || p.G > 1024) break;
+        if (stride > 1) {
+            stride /= 2;
+        } else if (p.gsize > 8) {
+            p.gsize /= 2;
+            gpt *= 2;
+        } else {
+            break;
+        }
     }
     // the threshold kernel holds at most 64 x 32 group maxima per query
     p.pilot = (gvalid >= p.cprime + 8 && p.G <= 2048) ? 1 : 0;
     // list capacity per (query, split, column group).  The threshold is the
-    // c'-th largest of gvalid group maxima (groups of 32): a fraction
-    // pg = c'/gvalid of the groups reach it, so about f = 1 - (1 - pg)^(1/32)
+    // c'-th largest of gvalid group maxima (groups of gsize): a fraction
+    // pg = c'/gvalid of the groups reach it, so about f = 1 - (1 - pg)^(1/gsize)
     // of all references pass, m f in all.  That count varies from query to
     // query with the order statistic (about 1/sqrt(c') relative) and its
     // split over the lists: 2.5 times the mean per list plus 48 keeps
     // overflows (sent to the exact fallback) rare.
     if (p.pilot) {
         const double pg = std::min(1.0, static_cast<double>(p.cprime) / static_cast<double>(gvalid));
-        const double f = 1.0 - std::pow(1.0 - pg, 1.0 / 32.0);
+        const double f = 1.0 - std::pow(1.0 - pg, 1.0 / static_cast<double>(p.gsize));
         const double per_list = static_cast<double>(m) * f / (kGroups * S);
         int64_t cap = static_cast<int64_t>(std::ceil(2.5 * per_list)) + 48;
         if (cap > chunk / kGroups) cap = chunk / kGroups;

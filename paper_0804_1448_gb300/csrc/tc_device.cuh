@@ -96,7 +96,8 @@ struct TcArgs {
     int32_t S;
     int32_t stride;       // pilot: every stride-th tile of a split
     int32_t spt;          // pilot: sampled-tile slots per split
-    int32_t G;            // pilot: group maxima per query (S * spt * kTileN / 32)
+    int32_t G;            // pilot: group maxima per query (S * spt * 8 * gps)
+    int32_t gps;          // pilot: groups per 32-column slice (1, 2 or 4: groups of 32, 16, 8)
     uint32_t* gmax;       // pilot: [n][G] order-mapped maxima, 0 = no group
     uint64_t* lists;      // filter: [n][S][kGroups][cap], one list per column group
     int32_t* counts;      // filter: [n][S][kGroups] (may exceed cap: overflow)
@@ -354,7 +355,8 @@ __device__ __forceinline__ void tc_run(const CUtensorMap* tmap_q, const CUtensor
         const bool active = q < a.n;
         const uint32_t lane_addr = tmem + (static_cast<uint32_t>(quarter * 32) << 16);
         uint32_t* st = stage + et * kSW;
-        constexpr int gpt = kTileN / 32;            // groups of 32 references per tile
+        const int gps = PILOT ? a.gps : 1;          // pilot groups per 32-column slice
+        const int gpt = (kTileN / 32) * gps;        // pilot groups per tile
         uint64_t* list = nullptr;
         uint32_t* gout = nullptr;
         if (PILOT) gout = a.gmax + q * a.G + static_cast<int64_t>(split) * a.spt * gpt;
@@ -485,15 +487,23 @@ __device__ __forceinline__ void tc_run(const CUtensorMap* tmap_q, const CUtensor
                     const int64_t left = r_end - j0;
                     const int nvalid = left <= 0 ? 0 : (left >= 32 ? 32 : static_cast<int>(left));
                     if (PILOT) {
+                        // halving max tree down to gps values: v[i] is then the
+                        // maximum of the slice's elements u = i (mod gps), group
+                        // i of the slice (valid when element i is)
                         float v[32];
 #pragma unroll
                         for (int u = 0; u < 32; ++u)
                             v[u] = u < nvalid ? __uint_as_float(r[u]) : __int_as_float(0xff800000);
 #pragma unroll
                         for (int w2 = 16; w2 > 0; w2 >>= 1)
+                            if (w2 >= gps) {   // uniform
 #pragma unroll
-                            for (int u = 0; u < w2; ++u) v[u] = fmaxf(v[u], v[u + w2]);
-                        if (active && nvalid > 0) gout[g * gpt + cg * 2 + sl] = ord_f32(v[0]);
+                                for (int u = 0; u < w2; ++u) v[u] = fmaxf(v[u], v[u + w2]);
+                            }
+                        uint32_t* go = gout + g * gpt + (cg * 2 + sl) * gps;
+#pragma unroll
+                        for (int i = 0; i < 4; ++i)
+                            if (i < gps && active && i < nvalid) go[i] = ord_f32(v[i]);
                     } else {
                         // sign bits, bit 31-u for element u, as four independent chains
                         uint32_t m4[4] = {0u, 0u, 0u, 0u};

@@ -80,7 +80,8 @@ class knn_plan(ctypes.Structure):
                 ("pilot", ctypes.c_int32), ("pilot_stride", ctypes.c_int32),
                 ("pilot_groups", ctypes.c_int32), ("threshold_rank", ctypes.c_int32),
                 ("list_capacity", ctypes.c_int32), ("fallback_slots", ctypes.c_int32),
-                ("workspace_bytes", ctypes.c_int64), ("small_select", ctypes.c_int32)]
+                ("workspace_bytes", ctypes.c_int64), ("small_select", ctypes.c_int32),
+                ("pilot_group_size", ctypes.c_int32)]
 
 
 _SIGS = {

@@ -72,6 +72,25 @@ def test_uniform_shapes(knn, precision, n, m, d, k):
 
 
 @pytest.mark.parametrize("precision", ["bf16", "tf32"])
+@pytest.mark.parametrize("n,m,d,k,gsize", [
+    (12000, 1000, 40, 10, 16),   # every tile sampled, groups of 16; last tile 232 rows
+    (12000, 777, 40, 20, 8),     # groups of 8; last tile 9 rows (a slice of 9 elements)
+    (6000, 2400, 96, 20, 16),    # two reference splits, the second short
+])
+def test_pilot_small_groups(knn, precision, n, m, d, k, gsize):
+    """Reference sets too small for pilot groups of 32: every tile is sampled,
+    c' = c, and the groups shrink to 16 or 8 references."""
+    p = knn.explain_plan(n, m, d, k, precision=precision)
+    assert p["tensor_cores"] == 1 and p["pilot"] == 1 and p["pilot_stride"] == 1
+    assert p["pilot_group_size"] == gsize and p["threshold_rank"] == p["candidates"]
+    R = inputs.uniform(m, d, seed=3100 + m)
+    Q = inputs.uniform(n, d, seed=4100 + n)
+    g_dist, g_idx = run(knn, R, Q, k, precision)
+    o_dist, o_idx = oracle.knn(R, Q, parity.oracle_k(k, m), "l2")
+    check_all_rows(R, Q, g_dist, g_idx, o_dist, o_idx, k)
+
+
+@pytest.mark.parametrize("precision", ["bf16", "tf32"])
 def test_uniform_n1200_d8_k20(knn, precision):
     R, Q, k = inputs.workload("uniform_n1200_d8_k20")
     g_dist, g_idx = run(knn, R, Q, k, precision)

@@ -32,9 +32,11 @@ def test_bench_shape():
 @pytest.mark.parametrize("D", [8, 16, 32, 64, 80, 96])
 def test_table1_grid_invariants(N, D):
     p = plan(N, N, D, 20)
-    if N < 4800:
-        # too few groups for the pilot even at stride 1: the exact float32
-        # small-set select (all N distances of a query in shared memory)
+    # an SM's share of the small-set select's distance products (CTAs of 8 queries)
+    share = math.ceil(N / 8) * N * D / SMS
+    if N < 4800 and share < 2.2e5:
+        # the exact float32 small-set select (all N distances of a query in
+        # shared memory) is faster than the tensor-core passes here
         assert p["tensor_cores"] == 0 and p["small_select"] == 1
         assert p["splits"] == 1 and p["chunk"] == N and p["candidates"] == 28 + 16
         return
@@ -47,6 +49,26 @@ def test_table1_grid_invariants(N, D):
     assert p["pilot_groups"] <= 2048
     # the c'-th largest of the group maxima needs groups to spare
     assert p["pilot_groups"] >= p["threshold_rank"] + 8
+    if N == 2400:
+        # every tile sampled: c' = c, and groups of 16 (75 groups of 32 are too few)
+        assert p["pilot_stride"] == 1 and p["threshold_rank"] == p["candidates"]
+        assert p["pilot_group_size"] == 16 and p["pilot_groups"] == 2 * 5 * 16
+    else:
+        assert p["pilot_group_size"] == 32
+
+
+def test_pilot_groups_shrink_when_every_tile_is_sampled():
+    # m = 777: 25 groups of 32 or 49 of 16 are too few for c' = c = 80 (+8)
+    p = plan(12000, 777, 40, 20)
+    assert p["tensor_cores"] == 1 and p["pilot_stride"] == 1
+    assert p["pilot_group_size"] == 8 and p["threshold_rank"] == 80
+    assert p["pilot_groups"] == 4 * 32                         # 4 tiles x 8 slices x 4 groups
+    # m = 600: 75 groups of 8 are too few; no pilot, so the small-set select
+    p = plan(12000, 600, 40, 20)
+    assert p["tensor_cores"] == 0 and p["small_select"] == 1
+    # sampled pilots keep groups of 32 and the Poisson margin
+    p = plan(38400, 38400, 96, 20)
+    assert p["pilot_group_size"] == 32 and p["threshold_rank"] > p["candidates"] * 10 / 150
 
 
 @pytest.mark.parametrize("n", [1, 64, 256])
