@@ -328,10 +328,8 @@ cudaError_t launch_tc_pilot(const TcPlan& p, const void* Q_lp, int64_t n, const 
     CUtensorMap mq, mr;
     if (!tc_make_map(&mq, Q_lp, n, kp, prec, kBlockM, 0) || !tc_make_map(&mr, R_lp, m, kp, prec, p.rb, p.kbs))
         return cudaErrorInvalidValue;
-    cudaError_t err = cudaMemsetAsync(gmax, 0, static_cast<size_t>(n) * p.G * 4, st);
-    if (err != cudaSuccess) return err;
     TcArgs a = base_args(p, n, m, error_flag);
-    a.gmax = gmax;
+    a.gmax = gmax;   // every slot of every row is written by the pilot
     if (launches) ++*launches;
     return dispatch<true>(p, prec, mq, mr, a, st);
 }

@@ -489,7 +489,8 @@ __device__ __forceinline__ void tc_run(const CUtensorMap* tmap_q, const CUtensor
                     if (PILOT) {
                         // halving max tree down to gps values: v[i] is then the
                         // maximum of the slice's elements u = i (mod gps), group
-                        // i of the slice (valid when element i is)
+                        // i of the slice (valid when element i is; an absent
+                        // group is written as 0, which no maximum takes)
                         float v[32];
 #pragma unroll
                         for (int u = 0; u < 32; ++u)
@@ -503,7 +504,7 @@ __device__ __forceinline__ void tc_run(const CUtensorMap* tmap_q, const CUtensor
                         uint32_t* go = gout + g * gpt + (cg * 2 + sl) * gps;
 #pragma unroll
                         for (int i = 0; i < 4; ++i)
-                            if (i < gps && active && i < nvalid) go[i] = ord_f32(v[i]);
+                            if (i < gps && active) go[i] = i < nvalid ? ord_f32(v[i]) : 0u;
                     } else {
                         // sign bits, bit 31-u for element u, as four independent chains
                         uint32_t m4[4] = {0u, 0u, 0u, 0u};
@@ -540,6 +541,12 @@ __device__ __forceinline__ void tc_run(const CUtensorMap* tmap_q, const CUtensor
             }
         }
         if (!PILOT && active) a.counts[(q * a.S + split) * kGroups + cg] = cnt;
+        // pilot: the group slots of tiles this split does not have (a short
+        // split) hold no maximum; every slot of the row is then written, so
+        // the buffer needs no clearing beforehand
+        if (PILOT && active)
+            for (int g = nt; g < a.spt; ++g)
+                for (int i = 0; i < 2 * gps; ++i) gout[g * gpt + cg * 2 * gps + i] = 0u;
     }
     tc_fence_before();
     __syncthreads();
