@@ -45,8 +45,8 @@ PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
 # profiles/tc_filter_uniform_n38400_d96_k20.md), valid only for the kernel's
 # device source it was measured on (sha256 prefix of tc_device.cuh followed by
 # tc_ptx.cuh); otherwise reported as null.
-FILTER_TRAFFIC_BYTES = 99.09e6
-FILTER_TRAFFIC_SRC = "eba92f62d836f85a"
+FILTER_TRAFFIC_BYTES = 99.23e6
+FILTER_TRAFFIC_SRC = "847a37a8c20ca9ba"
 FILTER_SOURCES = ("tc_device.cuh", "tc_ptx.cuh")
 
 CLOCK_HOLD_S = 0.3

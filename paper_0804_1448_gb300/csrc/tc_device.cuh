@@ -181,12 +181,14 @@ __device__ __forceinline__ uint32_t bfind31(uint32_t x) {
     return p & 31u;
 }
 
-// Store v to [addr] only when sel != 0 (a predicated 16-byte shared store).
-__device__ __forceinline__ void st_shared_if(uint32_t sel, uint32_t addr, uint32_t v0, uint32_t v1,
-                                             uint32_t v2, uint32_t v3) {
-    asm volatile("{\n .reg .pred p;\n setp.ne.b32 p, %0, 0;\n"
-                 " @p st.shared.v4.b32 [%1], {%2, %3, %4, %5};\n}"
-                 :: "r"(sel), "r"(addr), "r"(v0), "r"(v1), "r"(v2), "r"(v3) : "memory");
+// Store v to [addr] only when bits & sel != 0 (a predicated 16-byte shared
+// store; the predicate comes from the three-input logic operation itself).
+__device__ __forceinline__ void st_shared_if(uint32_t bits, uint32_t sel, uint32_t addr, uint32_t v0,
+                                             uint32_t v1, uint32_t v2, uint32_t v3) {
+    asm volatile("{\n .reg .pred p, t;\n .reg .b32 x;\n setp.eq.u32 t, 1, 1;\n"
+                 " lop3.and.b32 x|p, %0, %1, 0, 0xc0, t;\n"
+                 " @p st.shared.v4.b32 [%2], {%3, %4, %5, %6};\n}"
+                 :: "r"(bits), "r"(sel), "r"(addr), "r"(v0), "r"(v1), "r"(v2), "r"(v3) : "memory");
 }
 
 // MMAs of one 128-byte K block of one reference tile.  Fully unrolled over the
@@ -452,7 +454,7 @@ __device__ __forceinline__ void tc_run(const CUtensorMap* tmap_q, const CUtensor
                     // thread's staging words, which the appends read back by index
 #pragma unroll
                     for (int h = 0; h < 8; ++h)
-                        st_shared_if(hits & (0xf0000000u >> (4 * h)), st_addr + 16 * h,
+                        st_shared_if(hits, 0xf0000000u >> (4 * h), st_addr + 16 * h,
                                      r[4 * h], r[4 * h + 1], r[4 * h + 2], r[4 * h + 3]);
                     const float b3 = __uint_as_float(off3b);
                     const float* stf = reinterpret_cast<const float*>(st) + 31;
