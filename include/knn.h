@@ -126,7 +126,13 @@ knn_status knn_set_reference(knn_handle h, const float* R, int64_t m, int32_t d,
  *     `cuda_stream`; the call only enqueues work and returns (asynchronous).
  *   io_on_device = 0: host pointers; the call copies Q in, searches, copies
  *     the results out and returns when they are in place (synchronous).
- *     Pinned host memory makes the copies faster; pageable works too.
+ *     Pinned host memory makes the copies faster; pageable works too.  In
+ *     the tensor-core forms pinned Q and outputs are not copied: the kernels
+ *     read Q and write the results over the CPU-GPU link in place, and from
+ *     8192 queries on the search runs as two parts on two streams (the
+ *     handle's second stream joins back into cuda_stream), so that the
+ *     second part's queries cross the link while the first part computes.
+ *     Neither changes the result.
  * cuda_stream: a cudaStream_t, or NULL for the handle's own stream.
  * n = 0 is a no-op returning KNN_OK.
  * Errors: KNN_ERR_INVALID (null pointer with n > 0, n < 0, k < 1, k > m,

@@ -21,10 +21,16 @@ using namespace knn;
 namespace {
 
 constexpr int kMaxStages = 8;
+// A host-buffer search runs in up to kMaxParts parts of at least
+// kPartMinQueries queries each (four parts measured no faster than two at
+// n = 38400: 62.2 against 62.3-62.4 million queries/s end to end).
+constexpr int kMaxParts = 2;
+constexpr int64_t kPartMinQueries = 4096;
 
 // Device counters owned by a handle.
 struct Counters {
     int32_t fallback_count;                 // queued queries of the current search
+    int32_t fallback_part[kMaxParts - 1];   // the same, parts after the first of a host-buffer search
     int32_t error_flag;                     // set by a kernel whose bounded wait gave up
     unsigned long long recheck_total;       // re-checked near-tie candidates
     unsigned long long fallback_total;      // queries finished by the fallback
@@ -68,6 +74,11 @@ struct knn_ctx {
 
     Counters* counters = nullptr;  // device
     int32_t* flag_host = nullptr;  // pinned host word: the error flag as a host-buffer search ends
+    // host-buffer searches in parts: the side streams of parts after the
+    // first, and the events that order them (start; each part's query
+    // preparation done; each side part done)
+    cudaStream_t pipe_stream[kMaxParts - 1] = {};
+    cudaEvent_t pipe_start = nullptr, pipe_prep[kMaxParts - 1] = {}, pipe_done[kMaxParts - 1] = {};
     int64_t searches = 0;
     int64_t launches = 0;
 
@@ -420,7 +431,7 @@ struct RefView {
 knn_status enqueue_search(knn_ctx* h, const SearchPlan& sp, const RefView& rv, const float* Qd,
                           int64_t n, int32_t k, knn_metric metric, float* dd, int32_t* id,
                           unsigned char* ws, int32_t* fallback_count, cudaStream_t st, int* l,
-                          bool stages, float* Q_copy = nullptr) {
+                          bool stages, float* Q_copy = nullptr, cudaEvent_t prep_done = nullptr) {
     const int64_t m = rv.m;
     const int32_t d = rv.d;
     const int S = sp.S, c = sp.c;
@@ -444,6 +455,7 @@ knn_status enqueue_search(knn_ctx* h, const SearchPlan& sp, const RefView& rv, c
         KNN_CUDA(h, launch_prepare_query(Qd, n, d, rv.kp, prec, Ql, qs_prep, Q_copy, st, l));
         if (Q_copy) Qd = Q_copy;
         mark("prepare_q");
+        if (prep_done) KNN_CUDA(h, cudaEventRecord(prep_done, st));
         if (plan.pilot) {
             uint32_t* gmax = reinterpret_cast<uint32_t*>(ws + sp.off_gmax);
             KNN_CUDA(h, launch_tc_pilot(plan, Ql, n, rv.R_lp, m, rv.kp, prec, gmax, &ctr->error_flag,
@@ -613,6 +625,18 @@ knn_status enqueue_instance(knn_ctx* h, const knn_instance& x, const BatchPlan& 
     return enqueue_search(h, sp, rv, x.Q, x.n, x.k, static_cast<knn_metric>(x.metric), x.dist_out,
                           x.idx_out, ws + bp.base[i], reinterpret_cast<int32_t*>(ws + bp.fbc[i]),
                           st, l, false);
+}
+
+// The side streams and events of a host-buffer search run in parts.
+knn_status pipe_streams(knn_ctx* h) {
+    if (h->pipe_start) return KNN_OK;
+    for (int i = 0; i < kMaxParts - 1; ++i) {
+        KNN_CUDA(h, cudaStreamCreateWithFlags(&h->pipe_stream[i], cudaStreamNonBlocking));
+        KNN_CUDA(h, cudaEventCreateWithFlags(&h->pipe_prep[i], cudaEventDisableTiming));
+        KNN_CUDA(h, cudaEventCreateWithFlags(&h->pipe_done[i], cudaEventDisableTiming));
+    }
+    KNN_CUDA(h, cudaEventCreateWithFlags(&h->pipe_start, cudaEventDisableTiming));
+    return KNN_OK;
 }
 
 knn_status batch_streams(knn_ctx* h) {
@@ -890,6 +914,15 @@ knn_status knn_destroy(knn_handle h) {
         if (h->join_ev[b]) cudaEventDestroy(h->join_ev[b]);
     }
     if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
+    for (int i = 0; i < kMaxParts - 1; ++i) {
+        if (h->pipe_stream[i]) {
+            cudaStreamSynchronize(h->pipe_stream[i]);
+            cudaStreamDestroy(h->pipe_stream[i]);
+        }
+        if (h->pipe_prep[i]) cudaEventDestroy(h->pipe_prep[i]);
+        if (h->pipe_done[i]) cudaEventDestroy(h->pipe_done[i]);
+    }
+    if (h->pipe_start) cudaEventDestroy(h->pipe_start);
     if (h->fork_ev) cudaEventDestroy(h->fork_ev);
     if (h->t_ev[0]) cudaEventDestroy(h->t_ev[0]);
     if (h->t_ev[1]) cudaEventDestroy(h->t_ev[1]);
@@ -1074,9 +1107,61 @@ knn_status knn_search(knn_handle h, const float* Q, int64_t n, int32_t d, int32_
         stage(h, st, "whiten_q");
     }
     RefView rv{rs.R, rs.m, rs.d, rs.R_lp, rs.kp, rs.rmax2};
-    s = enqueue_search(h, sp, rv, Qd, n, k, metric, dd, id, ws, &ctr->fallback_count, st, &l, true,
-                       q_copy);
-    if (s != KNN_OK) return s;
+    // Queries and outputs both in pinned host memory, read and written in
+    // place: the link moves the queries at a fraction of the rate the kernels
+    // use them, so a large search runs in parts (whole 128-query tiles), each
+    // on its own stream, each part's query preparation starting when the one
+    // before it ends.  The link then carries a part's queries while the parts
+    // before it compute.  Only when the parts' workspaces fit the one this
+    // search already has, and no stage profiling is on.
+    int parts = 1;
+    SearchPlan pp[kMaxParts];
+    size_t poff[kMaxParts] = {};
+    int64_t pb[kMaxParts + 1] = {};
+    if (q_copy && out_direct && !h->profiling) {
+        for (int np = static_cast<int>(std::min<int64_t>(kMaxParts, n / kPartMinQueries)); np > 1;
+             np = np > 2 ? 2 : 1) {
+            bool ok = true;
+            size_t total = 0;
+            for (int j = 0; j <= np; ++j) pb[j] = j == np ? n : (n * j / np + 127) / 128 * 128;
+            for (int j = 0; j < np && ok; ++j) {
+                ok = plan_search(h, pb[j + 1] - pb[j], k, metric, 0, &pp[j]) == KNN_OK && pp[j].tensor;
+                poff[j] = total;
+                total += (pp[j].bytes + 255) / 256 * 256;
+            }
+            if (ok && total <= h->ws_bytes) {
+                parts = np;
+                break;
+            }
+        }
+    }
+    if (parts > 1) {
+        s = pipe_streams(h);
+        if (s != KNN_OK) return s;
+        KNN_CUDA(h, cudaEventRecord(h->pipe_start, st));
+        for (int j = 0; j < parts; ++j) {
+            cudaStream_t sj = j == 0 ? st : h->pipe_stream[j - 1];
+            if (j > 0) {
+                KNN_CUDA(h, cudaStreamWaitEvent(sj, h->pipe_start, 0));
+                KNN_CUDA(h, cudaStreamWaitEvent(sj, h->pipe_prep[j - 1], 0));
+            }
+            unsigned char* wj = ws + poff[j];
+            int32_t* fc = j == 0 ? &ctr->fallback_count : &ctr->fallback_part[j - 1];
+            s = enqueue_search(h, pp[j], rv, Q + pb[j] * d, pb[j + 1] - pb[j], k, metric,
+                               dist_out + pb[j] * k, idx_out + pb[j] * k, wj, fc, sj, &l, false,
+                               reinterpret_cast<float*>(wj + pp[j].off_q),
+                               j + 1 < parts ? h->pipe_prep[j] : nullptr);
+            if (s != KNN_OK) return s;
+        }
+        for (int j = 1; j < parts; ++j) {
+            KNN_CUDA(h, cudaEventRecord(h->pipe_done[j - 1], h->pipe_stream[j - 1]));
+            KNN_CUDA(h, cudaStreamWaitEvent(st, h->pipe_done[j - 1], 0));
+        }
+    } else {
+        s = enqueue_search(h, sp, rv, Qd, n, k, metric, dd, id, ws, &ctr->fallback_count, st, &l,
+                           true, q_copy);
+        if (s != KNN_OK) return s;
+    }
     h->launches += l;
     h->searches += 1;
 

@@ -223,6 +223,34 @@ def test_pinned_host_buffers_equal_device_buffers(knn, precision):
     ix.close()
 
 
+@pytest.mark.parametrize("precision", ["bf16", "tf32"])
+@pytest.mark.parametrize("n", [12_001, 20_001])   # ragged second halves
+def test_pinned_host_search_in_parts(knn, precision, n):
+    """From 8192 queries on, a search whose queries and outputs are in pinned
+    host memory runs in two parts, each on its own stream, the second part's
+    queries crossing the link while the first part computes.  Its result is the device-buffer search's, bit for bit,
+    and the oracle's under the parity rule."""
+    import torch
+    m, d, k = 5_000, 64, 16
+    R = inputs.uniform(m, d, seed=3711)
+    Q = inputs.uniform(n, d, seed=3712)
+    ix = knn.Index(0, precision)
+    ix.set_reference(torch.from_numpy(R).cuda())
+    d_dev, i_dev = ix.search(torch.from_numpy(Q).cuda(), k, "l2")
+    ix.sync()
+    Qh = torch.from_numpy(Q).pin_memory()
+    dh = torch.empty((n, k), dtype=torch.float32).pin_memory()
+    ih = torch.empty((n, k), dtype=torch.int32).pin_memory()
+    for _ in range(2):   # the second call reuses the side stream and the workspace
+        dh.fill_(-1.0)
+        ih.fill_(-1)
+        ix.search_into(Qh, k, dh, ih, "l2")
+        assert torch.equal(dh, d_dev.cpu()) and torch.equal(ih, i_dev.cpu())
+    ix.close()
+    o_dist, o_idx = oracle.knn(R, Q, parity.oracle_k(k, m), "l2")
+    check_all_rows(R, Q, dh.numpy(), ih.numpy(), o_dist, o_idx, k)
+
+
 # ------------------------------------------------- serving k range, large pools
 
 @pytest.fixture(scope="module")
