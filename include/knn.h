@@ -276,8 +276,8 @@ knn_status knn_search_self(knn_handle h, int32_t k, knn_metric metric, float* di
                            int32_t* idx_out, void* cuda_stream);
 
 /*
- * The float32 search of knn_search (distance from coordinate differences,
- * float64 re-check of near ties, exact fallback) for callers that cannot
+ * The float32 search of knn_search (returned distances from coordinate
+ * differences, float64 re-check of near ties, exact fallback) for callers that cannot
  * allocate device memory when they search: frameworks that hand out every
  * device allocation from their own pool (and account for it), and
  * latency-critical paths that cannot take the device-wide synchronisation of

@@ -7,8 +7,9 @@
 // finalize (one warp per query):
 //   1. candidates: the S*c keys of the select stage, or the tensor-core hit
 //      lists cut to (at least) the best c by their low-precision keys; then the
-//      exact float32 distance of every candidate (differences, as the CUDA-core
-//      select kernel computes them): the "re-rank";
+//      exact float32 distance of every candidate from coordinate differences
+//      (the select stages rank low-precision scores or, for the Euclidean
+//      CUDA-core select, lower bounds from the expanded form): the "re-rank";
 //   2. ascending prefix by (distance, index) -- step 2 of the brute-force
 //      algorithm of Sec. 2.1, restricted to the candidates: the first k, and
 //      the run of near-equal distances that crosses position k-1;

@@ -13,10 +13,21 @@
 // so the serial part of the selection shrinks to the rare insertions.  Only
 // the c survivors per (query, split) are written out.
 //
-// Distances are formed from coordinate differences in float32, coordinate 0
-// first: Euclidean sum_t fma(q_t - r_t, q_t - r_t, acc) (the squared
-// distance), Manhattan sum_t |q_t - r_t|.  Nothing is expanded, so a query
-// that equals a reference gets exactly 0.
+// Manhattan and Chebyshev distances are formed from coordinate differences in
+// float32, coordinate 0 first (sum_t |q_t - r_t|, max_t |q_t - r_t|).  The
+// Euclidean one is expanded, ||q - r||^2 = ||q||^2 + ||r||^2 - 2 q.r: one
+// fused multiply-add per coordinate for the product, the squared norms summed
+// from the same staged coordinates.  What the selection ranks is a LOWER BOUND
+// of the exact squared distance, L = (1 - g) (||q||^2 + ||r||^2) - 2 q.r with
+// g = 4 (d + 3) 2^-24, clamped at 0: each norm and the product carry at most
+// gamma_d = d u / (1 - d u) relative error over the sums of their terms
+// (u = 2^-24; fused multiply-adds in any order), |q.r| summed termwise is at
+// most (||q||^2 + ||r||^2) / 2, and the last three roundings add 3 u of the
+// same, so the float32 L falls short of ||q - r||^2 by at least
+// (g - 2 gamma_d - 3 u) (||q||^2 + ||r||^2) >= 0.  The finalize re-ranks the
+// kept candidates with exact float32 differences; a reference a split leaves
+// out has L >= the split's largest kept L, so the finalize's completeness test
+// on that largest key holds for the exact distances as well.
 #include "knn_internal.cuh"
 
 namespace knn {
@@ -69,9 +80,12 @@ constexpr size_t cc_union_bytes() {
                ? cc_stage_bytes<ROWS>()
                : sizeof(float) * ROWS * cc_dst<ROWS>();
 }
+// ... then the squared norms of the CTA's queries and of the current reference
+// tile (Euclidean).
 template <int ROWS>
 constexpr size_t cc_smem_bytes(int c) {
-    return cc_union_bytes<ROWS>() + sizeof(uint64_t) * static_cast<size_t>(c) * ROWS;
+    return cc_union_bytes<ROWS>() + sizeof(uint64_t) * static_cast<size_t>(c) * ROWS +
+           sizeof(float) * (ROWS + kTM);
 }
 
 // Max-heap (largest key at slot 0) of c keys, slot-major with stride ROWS.
@@ -104,31 +118,13 @@ __device__ __forceinline__ void heapify(uint64_t* h, int c) {
     for (int i = c / 2 - 1; i >= 0; --i) heap_sift_down<ROWS>(h, c, i, h[i * ROWS]);
 }
 
-// Two float32 lanes: (a, a) - (b0, b1), the difference of one query
-// coordinate and the same coordinate of two references, rounded per lane.
-__device__ __forceinline__ uint64_t sub_pair(float a, float b0, float b1) {
+// Two float32 lanes: acc + (a, a) * (b0, b1), one query coordinate times the
+// same coordinate of two references, one rounding per lane.
+__device__ __forceinline__ uint64_t dot_pair(float a, float b0, float b1, uint64_t acc) {
     uint64_t r;
     asm("{\n .reg .b64 x, y;\n mov.b64 x, {%1, %1};\n mov.b64 y, {%2, %3};\n"
-        " sub.rn.f32x2 %0, x, y;\n}"
-        : "=l"(r) : "f"(a), "f"(b0), "f"(b1));
-    return r;
-}
-// acc + diff * diff per lane, one rounding (the fmaf of the scalar form).
-__device__ __forceinline__ uint64_t sqacc_pair(uint64_t diff, uint64_t acc) {
-    uint64_t r;
-    asm("fma.rn.f32x2 %0, %1, %1, %2;" : "=l"(r) : "l"(diff), "l"(acc));
-    return r;
-}
-// The same as sqacc_pair, as two one-lane fmas (the same rounding per lane).
-// One column pair of the micro-tile takes this form: the one-lane fmas can run
-// beside the two-lane instructions, which all share one pipe (measured: 11.18
-// against 11.52 ms at n = m = 38400, d = 96, bit-identical outputs; two pairs
-// or the subtractions in this form were slower).
-__device__ __forceinline__ uint64_t sqacc_lanes(uint64_t diff, uint64_t acc) {
-    uint64_t r;
-    asm("{\n .reg .f32 d0, d1, a0, a1;\n mov.b64 {d0, d1}, %1;\n mov.b64 {a0, a1}, %2;\n"
-        " fma.rn.f32 a0, d0, d0, a0;\n fma.rn.f32 a1, d1, d1, a1;\n mov.b64 %0, {a0, a1};\n}"
-        : "=l"(r) : "l"(diff), "l"(acc));
+        " fma.rn.f32x2 %0, x, y, %4;\n}"
+        : "=l"(r) : "f"(a), "f"(b0), "f"(b1), "l"(acc));
     return r;
 }
 __device__ __forceinline__ float pair_lo(uint64_t v) { return __uint_as_float(static_cast<uint32_t>(v)); }
@@ -142,8 +138,9 @@ __device__ __forceinline__ float pair_hi(uint64_t v) { return __uint_as_float(st
 // and one barrier per step separates the writes of a buffer from the reads of
 // the step before.  A finished tile's distances take the buffers' place until
 // the selection has consumed them (two more barriers per tile).
-// Euclidean sums run as two-lane float32 instructions (sub, fma): per lane
-// the same operations, in the same order, as the scalar form.
+// Euclidean products run as two-lane float32 fused multiply-adds; the
+// threads below kTM (below ROWS, in a CTA's first tile) also sum the squares
+// of reference (query) tid's staged coordinates, its squared norm.
 template <int METRIC, int ROWS>
 __global__ void __launch_bounds__(kThreads, CCShape<ROWS>::MINB)
 cc_select_kernel(const float* __restrict__ Q, int64_t n, const float* __restrict__ R,
@@ -167,6 +164,10 @@ cc_select_kernel(const float* __restrict__ Q, int64_t n, const float* __restrict
     float* Rs = Qs + 2 * kDK * QST;                            // [2][kDK][RST]
     float* Dt = reinterpret_cast<float*>(smem_raw);            // [ROWS][DST], over the stages
     uint64_t* heap = reinterpret_cast<uint64_t*>(smem_raw + cc_union_bytes<ROWS>());  // [c][ROWS]
+    float* nqs = reinterpret_cast<float*>(heap + static_cast<size_t>(cand.c) * ROWS);   // [ROWS]
+    float* nrs = nqs + ROWS;                                                             // [kTM]
+    float nq_acc = 0.f, nr_acc = 0.f;   // squared norm of query / reference tid (Euclidean)
+    const float g1 = 1.f - 4.f * static_cast<float>(d + 3) * 5.9604644775390625e-8f;   // 1 - g
 
     const int tid = threadIdx.x;
     const int ty = tid / S::TX, tx = tid % S::TX;
@@ -241,6 +242,16 @@ cc_select_kernel(const float* __restrict__ Q, int64_t n, const float* __restrict
         }
         __syncthreads();
         if (h + 1 < steps) fetch(h + 1);
+        if constexpr (METRIC == kL2) {
+            if (tid < kTM) {
+#pragma unroll
+                for (int t = 0; t < kDK; ++t) nr_acc = fmaf(rs[t * RST + tid], rs[t * RST + tid], nr_acc);
+            }
+            if (h < stages && tid < ROWS) {
+#pragma unroll
+                for (int t = 0; t < kDK; ++t) nq_acc = fmaf(qs[t * QST + tid], qs[t * QST + tid], nq_acc);
+            }
+        }
 #pragma unroll 4
         for (int t = 0; t < kDK; ++t) {
             float qv[S::RR], rv[S::CN];
@@ -266,10 +277,7 @@ cc_select_kernel(const float* __restrict__ Q, int64_t n, const float* __restrict
                 for (int i = 0; i < S::RR; ++i)
 #pragma unroll
                     for (int j = 0; j < CP; ++j)
-                    {
-                        const uint64_t df = sub_pair(qv[i], rv[2 * j], rv[2 * j + 1]);
-                        acc2[i][j] = j == CP - 1 ? sqacc_lanes(df, acc2[i][j]) : sqacc_pair(df, acc2[i][j]);
-                    }
+                        acc2[i][j] = dot_pair(qv[i], rv[2 * j], rv[2 * j + 1], acc2[i][j]);
             } else {
 #pragma unroll
                 for (int i = 0; i < S::RR; ++i)
@@ -286,21 +294,38 @@ cc_select_kernel(const float* __restrict__ Q, int64_t n, const float* __restrict
         // a reference tile is complete: its distances -> shared memory, over
         // the stage buffers once every thread is done reading them
         const int64_t tbase = r_begin + static_cast<int64_t>(h / stages) * kTM;
+        if constexpr (METRIC == kL2) {
+            if (tid < kTM) {
+                nrs[tid] = nr_acc;
+                nr_acc = 0.f;
+            }
+            if (h == stages - 1 && tid < ROWS) nqs[tid] = nq_acc;
+        }
         __syncthreads();
+        // the lower bound of the squared distance from the product and the norms
+        auto lower = [g1](float nq, float nr, float dot) {
+            return fmaxf(0.f, fmaf(-2.f, dot, g1 * (nq + nr)));
+        };
 #pragma unroll
         for (int i = 0; i < S::RR; ++i) {
             float* drow = Dt + (ty * S::RR + i) * DST;
+            const float nq = METRIC == kL2 ? nqs[ty * S::RR + i] : 0.f;
 #pragma unroll
             for (int g = 0; g < S::CN / S::G; ++g) {
                 const int col = g * (S::TX * S::G) + tx * S::G;
                 if constexpr (METRIC == kL2) {
                     const uint64_t p0 = acc2[i][g * S::G / 2];
                     const uint64_t p1 = acc2[i][(g * S::G / 2 + 1) % CP];
-                    if constexpr (S::G == 4)
+                    if constexpr (S::G == 4) {
+                        const float4 nr = *reinterpret_cast<const float4*>(nrs + col);
                         *reinterpret_cast<float4*>(drow + col) =
-                            make_float4(pair_lo(p0), pair_hi(p0), pair_lo(p1), pair_hi(p1));
-                    else
-                        *reinterpret_cast<float2*>(drow + col) = make_float2(pair_lo(p0), pair_hi(p0));
+                            make_float4(lower(nq, nr.x, pair_lo(p0)), lower(nq, nr.y, pair_hi(p0)),
+                                        lower(nq, nr.z, pair_lo(p1)), lower(nq, nr.w, pair_hi(p1)));
+                    } else {
+                        const float2 nr = *reinterpret_cast<const float2*>(nrs + col);
+                        *reinterpret_cast<float2*>(drow + col) =
+                            make_float2(lower(nq, nr.x, pair_lo(p0)), lower(nq, nr.y, pair_hi(p0)));
+                    }
                 } else {
                     if constexpr (S::G == 4)
                         *reinterpret_cast<float4*>(drow + col) =
