@@ -17,14 +17,18 @@
 // float32, coordinate 0 first (sum_t |q_t - r_t|, max_t |q_t - r_t|).  The
 // Euclidean one is expanded, ||q - r||^2 = ||q||^2 + ||r||^2 - 2 q.r: one
 // fused multiply-add per coordinate for the product, the squared norms summed
-// from the same staged coordinates.  What the selection ranks is a LOWER BOUND
-// of the exact squared distance, L = (1 - g) (||q||^2 + ||r||^2) - 2 q.r with
-// g = 4 (d + 3) 2^-24, clamped at 0: each norm and the product carry at most
-// gamma_d = d u / (1 - d u) relative error over the sums of their terms
-// (u = 2^-24; fused multiply-adds in any order), |q.r| summed termwise is at
-// most (||q||^2 + ||r||^2) / 2, and the last three roundings add 3 u of the
-// same, so the float32 L falls short of ||q - r||^2 by at least
-// (g - 2 gamma_d - 3 u) (||q||^2 + ||r||^2) >= 0.  The finalize re-ranks the
+// from the same staged coordinates, which are taken relative to a centre c
+// (the first reference of the CTA's split): q' = fl(q - c), r' = fl(r - c).
+// What the selection ranks is a LOWER BOUND of the exact squared distance,
+// L = (1 - g) (||q'||^2 + ||r'||^2) - 2 q'.r' with g = 4 (d + 6) 2^-24, clamped
+// at 0: each norm and the product carry at most gamma_d = d u / (1 - d u)
+// relative error over the sums of their terms (u = 2^-24; fused
+// multiply-adds in any order), |q'.r'| summed termwise is at most
+// (||q'||^2 + ||r'||^2) / 2, the last three roundings add 3 u of the same, and
+// the rounding of the centred coordinates moves the distance by at most
+// (4 u + O(u^2)) (||q'||^2 + ||r'||^2) (||q - r|| >= ||q' - r'|| - u (||q'|| + ||r'||)
+// to first order), so the float32 L falls short of ||q - r||^2 by at least
+// (g - 2 gamma_d - 7 u - O(u^2)) (||q'||^2 + ||r'||^2) >= 0.  The finalize re-ranks the
 // kept candidates with exact float32 differences; a reference a split leaves
 // out has L >= the split's largest kept L, so the finalize's completeness test
 // on that largest key holds for the exact distances as well.
@@ -167,7 +171,7 @@ cc_select_kernel(const float* __restrict__ Q, int64_t n, const float* __restrict
     float* nqs = reinterpret_cast<float*>(heap + static_cast<size_t>(cand.c) * ROWS);   // [ROWS]
     float* nrs = nqs + ROWS;                                                             // [kTM]
     float nq_acc = 0.f, nr_acc = 0.f;   // squared norm of query / reference tid (Euclidean)
-    const float g1 = 1.f - 4.f * static_cast<float>(d + 3) * 5.9604644775390625e-8f;   // 1 - g
+    const float g1 = 1.f - 4.f * static_cast<float>(d + 6) * 5.9604644775390625e-8f;   // 1 - g
 
     const int tid = threadIdx.x;
     const int ty = tid / S::TX, tx = tid % S::TX;
@@ -197,9 +201,21 @@ cc_select_kernel(const float* __restrict__ Q, int64_t n, const float* __restrict
     int fill = 0;
 
     float pq[QPT], pr[RPT];
+    // Euclidean: coordinates are staged relative to the split's first
+    // reference (distances do not change; the norms, and with them the
+    // slack of the lower bound, become those of the data's spread rather than
+    // of its offset from the origin).  A thread's elements of a step all have
+    // coordinate tid % kDK (kThreads is a multiple of kDK): one centre value,
+    // loaded with them and taken off as they are stored to shared memory (so
+    // the loads stay in flight during the step before).  Rows past the data
+    // then hold -c instead of 0: their distances are masked anyway.
+    const float* cen = R + (r_begin < m ? r_begin : 0) * static_cast<int64_t>(d);
+    float pcv = 0.f;
     auto fetch = [&](int h) {
         const int64_t tbase = r_begin + static_cast<int64_t>(h / stages) * kTM;
         const int dbase = (h % stages) * kDK;
+        const int ct = dbase + tid % kDK;
+        pcv = (METRIC == kL2 && ct < d) ? cen[ct] : 0.f;
 #pragma unroll
         for (int u = 0; u < QPT; ++u) {
             const int e = tid + u * kThreads, r = e / kDK, t = e % kDK;
@@ -233,12 +249,12 @@ cc_select_kernel(const float* __restrict__ Q, int64_t n, const float* __restrict
 #pragma unroll
         for (int u = 0; u < QPT; ++u) {
             const int e = tid + u * kThreads;
-            qs[(e % kDK) * QST + e / kDK] = pq[u];
+            qs[(e % kDK) * QST + e / kDK] = METRIC == kL2 ? pq[u] - pcv : pq[u];
         }
 #pragma unroll
         for (int u = 0; u < RPT; ++u) {
             const int e = tid + u * kThreads;
-            rs[(e % kDK) * RST + e / kDK] = pr[u];
+            rs[(e % kDK) * RST + e / kDK] = METRIC == kL2 ? pr[u] - pcv : pr[u];
         }
         __syncthreads();
         if (h + 1 < steps) fetch(h + 1);

@@ -150,6 +150,22 @@ def test_near_tie_ladder_exact_order(knn, metric, d):
     assert st["recheck_entries"] > 0
 
 
+@pytest.mark.parametrize("offset", [0.0, 1000.0])
+def test_expanded_euclidean_far_from_the_origin(knn, offset):
+    """The float32 Euclidean select (m > 4096) ranks lower bounds of the
+    expanded distance, with coordinates taken relative to a reference of the
+    split: a point cloud translated far from the origin (coordinates near
+    1000, spread 1) keeps the bound's slack at the scale of the spread, so no
+    query needs the exact fallback, and the result is the oracle's."""
+    R = inputs.uniform(6000, 32, seed=881) + np.float32(offset)
+    Q = inputs.uniform(300, 32, seed=882) + np.float32(offset)
+    k = 20
+    g_dist, g_idx, st = run_case(knn, R, Q, k, "l2")
+    o_dist, o_idx = oracle.knn(R, Q, parity.oracle_k(k, R.shape[0]), "l2")
+    parity.compare(g_dist, g_idx, o_dist, o_idx, k, R.shape[0])
+    assert st["fallback_queries"] == 0
+
+
 def test_all_identical_points_use_exact_fallback(knn):
     R = np.full((2000, 5), 0.125, dtype=np.float32)
     Q = np.array([[0.125] * 5, [0.5] * 5], dtype=np.float32)
